@@ -10,7 +10,10 @@ state its constants.  Reading used here (the usual heuristic OC fixed point):
 
 with lam chosen by bisection so that V(lam) = V_max: l1 = 0, l2 = 1 doubled (at most 100
 times) until V(l2) <= V_max, then halving until (l2 - l1)/(l1 + l2) <= tol; the update is
-evaluated at the final midpoint.
+evaluated at the final midpoint.  The multiplier is confined to [2^-100, 2^100]: if the
+volume bound cannot bind (V(lam) <= V_max even as lam -> 0, every entry at its upper move
+limit) the halving stops once l2 <= 2^-100; if it cannot be met (V(lam) > V_max at 2^100)
+the result sits at the lower move limits.
 """
 from __future__ import annotations
 
@@ -38,7 +41,7 @@ def oc_update(z, dcdz, dvdz, vmax, move=0.2, eta=0.5, tol=1e-10, max_doublings=1
     while vol(l2) > vmax and n < max_doublings:
         l2 *= 2.0
         n += 1
-    while (l2 - l1) / (l1 + l2) > tol:
+    while (l2 - l1) / (l1 + l2) > tol and l2 > 2.0 ** -100:
         lmid = 0.5 * (l1 + l2)
         if vol(lmid) > vmax:
             l1 = lmid

@@ -65,3 +65,16 @@ def test_zero_or_positive_sensitivity_goes_to_lower_bound():
     znew, _, _ = oc.oc_update(z, dc, w, 1.6, 0.2)
     assert znew[0] == 0.3 and znew[1] == 0.3
     assert np.isclose(znew.sum(), 1.6, rtol=1e-9)
+
+
+def test_inactive_volume_bound_gives_upper_bounds():
+    """If every entry at its upper move limit still stays below V_max, the multiplier runs
+    to its floor 2^-100 and the update is min(1, z + move) (zero sensitivity excepted)."""
+    z = np.array([0.25, 0.6, 0.9])
+    dc = np.array([-0.4, -1.0, -2.0])
+    w = np.ones(3)
+    znew, lam, _ = oc.oc_update(z, dc, w, 2.9, 0.2)
+    assert lam <= 2.0 ** -100
+    assert np.allclose(znew, np.minimum(1.0, z + 0.2), rtol=0, atol=1e-15)
+    znew1, _, _ = oc.oc_update(z[:1], dc[:1], w[:1], 0.5, 0.2)
+    assert np.isclose(znew1[0], 0.45)
