@@ -1,0 +1,201 @@
+/*
+ * tomo.h -- C ABI of the exact-gradient path of SIMP compliance minimisation on a
+ * structured hex8 voxel grid, built for NVIDIA GB300 (sm_103a).
+ *
+ * The problem (Eq. 4, Section III-D of "Speeding up Computational Morphogenesis with Online
+ * Neural Synthetic Gradients"): minimise the compliance c = f^T u(z) subject to
+ * v^T P z <= V_max and 0 <= z_i <= 1, where u(z) solves K(P z) u = f (the state equation
+ * r = K u - f = 0), P is the density filter and K(rho) = sum_e h E_e(rho_e) K0 with the
+ * modified SIMP modulus E_e = Emin + rho_e^p (E0 - Emin).  Its gradient is Eq. 5,
+ * g_i = -u^T (dK/dz_i) u, and the volume gradient is P^T v (Section III-D).  The design is
+ * updated by the optimality-criteria (OC) method (Section III-D, Algorithm 1).
+ *
+ * Layout (all arrays, host or device):
+ *   elements  e = i + nx*(j + ny*k), 0 <= i < nx, 0 <= j < ny, 0 <= k < nz  (x fastest)
+ *   nodes     n = i + (nx+1)*(j + (ny+1)*k)
+ *   nodal vectors are structure-of-arrays: component c (0=x, 1=y, 2=z) of node n at
+ *   index c*N_n + n, N_n = (nx+1)(ny+1)(nz+1).
+ *
+ * Ownership: the caller owns every array passed in or out; the library copies the
+ * descriptor's host arrays at creation and owns its internal state (multigrid hierarchy,
+ * scratch vectors, constants) until tomo_destroy_grid.
+ *
+ * Pointers: every array argument may be a device pointer (cudaMalloc / torch tensor on
+ * the grid's device) or a host pointer (pageable or pinned).  Host arrays are staged
+ * through internal device buffers; the call then synchronises the grid's stream before it
+ * returns.  With device pointers all work is queued on the grid's stream and the call
+ * returns without waiting, except where a host scalar is written (compliance, change,
+ * solve info), which waits for the stream.
+ *
+ * Precision: a grid is created in one precision.  TOMO_FP64 grids take the *_d entry
+ * points (double arrays) and compute everything in FP64.  TOMO_FP32 grids take the float
+ * entry points: matrix-free products and multigrid smoothing in FP32, the CG iterate kept
+ * as an unevaluated float pair (about 48 significant bits), inner products, residual
+ * replacement, the compliance and the OC volume sums in FP64.  Calling an entry point of the
+ * other precision returns TOMO_EINVAL.
+ *
+ * Errors: every call returns a tomo_status.  Nothing aborts or traps; after an error the
+ * handle stays valid and tomo_last_error() describes the most recent failure on it.
+ * Calls on one handle are not thread-safe; distinct handles are independent.
+ */
+#ifndef TOMO_H
+#define TOMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tomo_grid tomo_grid; /* opaque, owned by the library */
+
+typedef enum {
+  TOMO_OK = 0,
+  TOMO_EINVAL = 1,   /* bad argument, size, layout or precision */
+  TOMO_ENOMEM = 2,   /* device or host allocation failed */
+  TOMO_ENOCONV = 3,  /* CG stopped at maxit or broke down (p^T A p <= 0) */
+  TOMO_ENAN = 4,     /* a NaN/Inf appeared in the iteration */
+  TOMO_ETIMEOUT = 5, /* a bounded device wait ran out */
+  TOMO_ECUDA = 6,    /* a CUDA runtime call failed (message in tomo_last_error) */
+  TOMO_EBUSY = 7     /* the handle is in use by an unfinished call */
+} tomo_status;
+
+enum { TOMO_FP64 = 0, TOMO_FP32 = 1 };
+enum { TOMO_PRECOND_MG = 0, TOMO_PRECOND_JACOBI = 1 };
+
+typedef struct {
+  int32_t iters;       /* CG iterations taken */
+  double rel_res;      /* ||r||_2 / ||f||_2 of the recursively updated residual at exit */
+  int32_t status;      /* tomo_status of the solve */
+  int32_t mg_levels;   /* multigrid levels used (1 for Jacobi) */
+} tomo_solve_info;
+
+typedef struct {
+  int32_t nx, ny, nz;   /* elements per axis, each >= 1 */
+  double h;             /* element edge length (> 0); K_e = h E_e K0, v_e = h^3 */
+  double E0, Emin;      /* solid and void moduli, E0 > Emin >= 0 */
+  double nu;            /* Poisson ratio, -1 < nu < 0.5 */
+  double penal;         /* SIMP exponent p >= 1 */
+  double rmin;          /* filter radius in element units (cone weights rmin - dist) */
+  const uint8_t* fixed_dof; /* host, 3*N_n, SoA; nonzero = displacement fixed to 0 */
+  const double* f;      /* host, 3*N_n, SoA load vector */
+  int32_t precision;    /* TOMO_FP64 | TOMO_FP32 */
+  int32_t precond;      /* TOMO_PRECOND_MG (default) | TOMO_PRECOND_JACOBI */
+  double rtol;          /* CG stop: ||r|| <= rtol ||f||; <= 0 selects 1e-6 */
+  int32_t maxit;        /* CG iteration cap; <= 0 selects 2000 */
+  int32_t mg_levels;    /* multigrid levels; <= 0 coarsens until the coarsest grid is small */
+  int32_t smoother_degree; /* Chebyshev degree per pre/post smoothing; <= 0 selects 2 */
+  double cheb_ratio;    /* smoothing interval [lmax/ratio, lmax] of D^-1 K; <= 1 selects 10 */
+  int32_t rr_every;     /* residual replacement r = f - K x (evaluated in FP64) every rr_every
+                           iterations; 0 selects 50, < 0 off */
+  void* stream;         /* cudaStream_t for all work on this grid; NULL = legacy default */
+} tomo_grid_desc;
+
+/* Fill *desc with defaults (no arrays, FP32, MG, rtol 1e-6, maxit 2000, auto levels,
+ * degree 2, residual replacement every 50 iterations, E0=1, Emin=1e-9, nu=0.3, p=3,
+ * rmin=1.5, h=1). */
+void tomo_default_desc(tomo_grid_desc* desc);
+
+/* Validate the descriptor, copy its host arrays, build K0 (Section III-D, hex8, E = 1,
+ * unit cube), the filter weights, the multigrid hierarchy and all scratch on the current
+ * CUDA device.  *out receives the handle.  TOMO_EINVAL on bad sizes or parameters,
+ * TOMO_ENOMEM if device memory runs out. */
+tomo_status tomo_create_grid(const tomo_grid_desc* desc, tomo_grid** out);
+
+/* Synchronise the grid's stream and release everything the handle owns. NULL is a no-op. */
+tomo_status tomo_destroy_grid(tomo_grid* grid);
+
+/* Rebind the grid to another stream (cudaStream_t); later calls queue there. */
+tomo_status tomo_set_stream(tomo_grid* grid, void* stream);
+
+/* Density filter of Eq. 4 (Section III-D): transpose = 0 computes out = P in = (H in)/Hs,
+ * transpose != 0 computes out = P^T in = H (in/Hs).  H_ij = max(0, rmin - |x_i - x_j|)
+ * over element centroids, Hs = H 1 truncated at the domain boundary.  in/out: N_el
+ * element arrays; they must not overlap. */
+tomo_status tomo_filter(tomo_grid* grid, const float* in, float* out, int transpose);
+tomo_status tomo_filter_d(tomo_grid* grid, const double* in, double* out, int transpose);
+
+/* y = K(rho) x on the free DOFs (fixed rows and the fixed entries of x are zero), with
+ * K(rho) = sum_e h E_e K0 and E_e = Emin + rho_e^p (E0 - Emin) (state equation of Eq. 4).
+ * rho: N_el physical densities in [0,1]; x, y: 3*N_n nodal vectors (SoA), no overlap. */
+tomo_status tomo_apply_stiffness(tomo_grid* grid, const float* rho, const float* x, float* y);
+tomo_status tomo_apply_stiffness_d(tomo_grid* grid, const double* rho, const double* x, double* y);
+
+/* Residual of the state equation of Eq. 4: r = f - K(rho) u on the free DOFs (0 on fixed
+ * DOFs).  FP32 grids take u as the unevaluated pair u + u_lo (u_lo may be NULL), the form
+ * in which the solver keeps its iterate.  rho: N_el; u, u_lo, r: 3*N_n. */
+tomo_status tomo_residual(tomo_grid* grid, const float* rho, const float* u, const float* u_lo,
+                          float* r);
+tomo_status tomo_residual_d(tomo_grid* grid, const double* rho, const double* u, double* r);
+
+/* Solve K(rho) u = f (state equation of Eq. 4, Section III-D) by CG preconditioned with a
+ * geometric-multigrid V-cycle (or Jacobi), to ||r|| <= rtol ||f||.  rho: N_el physical
+ * densities.  u: 3*N_n; on entry a warm start (fixed entries ignored), on exit the
+ * solution.  info (may be NULL) receives iterations, residual and status.  Returns
+ * TOMO_ENOCONV if maxit was reached, TOMO_ENAN on a NaN.  u holds the last iterate in
+ * both cases. */
+tomo_status tomo_solve(tomo_grid* grid, const float* rho, float* u, tomo_solve_info* info);
+tomo_status tomo_solve_d(tomo_grid* grid, const double* rho, double* u, tomo_solve_info* info);
+
+/* Compliance and its sensitivity (Eq. 4 objective, Eq. 5 with the SIMP chain rule):
+ * *compliance = f^T u (host or device double), and
+ * dc[e] = -p rho_e^(p-1) (E0 - Emin) h u_e^T K0 u_e  (derivative w.r.t. rho_e).
+ * rho: N_el, u: 3*N_n, dc: N_el.  compliance or dc may be NULL to skip them. */
+tomo_status tomo_sensitivity(tomo_grid* grid, const float* rho, const float* u,
+                             double* compliance, float* dc);
+tomo_status tomo_sensitivity_d(tomo_grid* grid, const double* rho, const double* u,
+                               double* compliance, double* dc);
+
+/* One optimality-criteria update (Section III-D): with B_e = max(-dcdz_e, 0)/(lam dvdz_e),
+ * z_new = clamp(z sqrt(B_e), max(0, z - move), min(1, z + move)), lam chosen so that
+ * sum_e dvdz_e z_new_e = volfrac * N_el * h^3 (the filtered volume v^T P z_new of Eq. 4),
+ * located to a relative bracket width of 1e-10 (at most 2^100).  *change (host or device
+ * double, may be NULL) = max_e |z_new_e - z_e|.  All arrays N_el; z_new must not overlap
+ * the inputs. */
+tomo_status tomo_oc_step(tomo_grid* grid, const float* z, const float* dcdz, const float* dvdz,
+                         double volfrac, double move, float* z_new, double* change);
+tomo_status tomo_oc_step_d(tomo_grid* grid, const double* z, const double* dcdz,
+                           const double* dvdz, double volfrac, double move, double* z_new,
+                           double* change);
+
+/* One exact-gradient evaluation (Algorithm 1, exact branch; Eq. 4-5): rho = P z,
+ * E = Emin + rho^p (E0 - Emin), solve K u = f from a zero start, *compliance = f^T u,
+ * dcdz = P^T dc/drho, dvdz = P^T v.  z, dcdz, dvdz: N_el.  dvdz may be NULL (then it is not
+ * computed).  The solution u stays inside the handle (tomo_get_displacement). */
+tomo_status tomo_gradient(tomo_grid* grid, const float* z, double* compliance, float* dcdz,
+                          float* dvdz, tomo_solve_info* info);
+tomo_status tomo_gradient_d(tomo_grid* grid, const double* z, double* compliance,
+                            double* dcdz, double* dvdz, tomo_solve_info* info);
+
+/* Copy the displacement of the last tomo_gradient / tomo_solve on this grid to u
+ * (3*N_n, host or device). */
+tomo_status tomo_get_displacement(tomo_grid* grid, float* u);
+tomo_status tomo_get_displacement_d(tomo_grid* grid, double* u);
+
+/* Grid counts: n_el, n_nodes, number of multigrid levels; any pointer may be NULL. */
+tomo_status tomo_get_counts(const tomo_grid* grid, int64_t* n_el, int64_t* n_nodes,
+                            int32_t* mg_levels);
+
+/* Number of kernels this grid has launched since creation (kernels of the device-side CG
+ * loop counted once per executed iteration). */
+tomo_status tomo_get_launch_count(const tomo_grid* grid, int64_t* launches);
+
+/* Kernel timing for roofline reports.  When enabled, the library brackets every launch
+ * of the fine-level matrix-free kernels (products and smoother steps) with CUDA events
+ * on the grid's stream and accumulates their count, total milliseconds and algorithmic
+ * DRAM bytes (inputs read once plus outputs written once).  tomo_profile_read waits for
+ * the stream, returns the totals since the last reset and resets them. */
+tomo_status tomo_profile_enable(tomo_grid* grid, int enable);
+tomo_status tomo_profile_read(tomo_grid* grid, int64_t* launches, double* total_ms,
+                              double* algorithmic_bytes);
+
+/* Description of the most recent error on grid (or of the last failed tomo_create_grid
+ * in this thread when grid is NULL).  Never NULL; valid until the next call on grid. */
+const char* tomo_last_error(const tomo_grid* grid);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOMO_H */

@@ -1,0 +1,1251 @@
+// C ABI of the tomo library: grid handle, multigrid hierarchy, preconditioned CG driver and
+// the exact-gradient evaluation (Algorithm 1, exact branch; Eq. 4-5, Section III-D).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "host.h"
+
+using namespace tomo;
+
+namespace tomo {
+thread_local std::string g_create_err;
+thread_local std::string* g_cur_err = nullptr;
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e),
+           what, file, line);
+  if (g_cur_err) *g_cur_err = buf;
+  return TOMO_ECUDA;
+}
+}  // namespace tomo
+
+namespace {
+
+tomo_status fail(tomo_grid* G, tomo_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (G) G->err = buf;
+  else g_create_err = buf;
+  return st;
+}
+
+#define CK(...)                                                        \
+  do {                                                                 \
+    cudaError_t _e = (__VA_ARGS__);                                    \
+    if (_e != cudaSuccess) {                                           \
+      return fail(G, _e == cudaErrorMemoryAllocation ? TOMO_ENOMEM : TOMO_ECUDA, \
+                  "CUDA error %d (%s) in %s (%s:%d)", (int)_e,         \
+                  cudaGetErrorString(_e), #__VA_ARGS__, __FILE__, __LINE__); \
+    }                                                                  \
+  } while (0)
+
+#define TRY(...)                           \
+  do {                                     \
+    tomo_status _s = (__VA_ARGS__);        \
+    if (_s != TOMO_OK) return _s;          \
+  } while (0)
+
+template <typename T>
+ElemConst<T> elem_const(const tomo_grid* G) {
+  ElemConst<T> c;
+  for (int k = 0; k < 8; ++k)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) c.blk[k][a][b] = (T)G->blk[k][a][b];
+  c.k0diag = (T)G->k0diag;
+  return c;
+}
+
+template <typename T>
+DenseK0<T> dense_k0(const tomo_grid* G) {
+  DenseK0<T> d;
+  for (int q = 0; q < 576; ++q) d.k[q] = (T)G->K0[q];
+  return d;
+}
+
+tomo_status dalloc(tomo_grid* G, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  CK(cudaMalloc(p, bytes));
+  return TOMO_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array; host arrays are copied into staging slot `slot`.
+tomo_status stage_in(tomo_grid* G, const void* p, size_t bytes, int slot, const void** out,
+                     bool* host) {
+  *host = !is_device_ptr(p);
+  if (!*host) {
+    *out = p;
+    return TOMO_OK;
+  }
+  if ((int)G->stage.size() <= slot) {
+    G->stage.resize(slot + 1, nullptr);
+    G->stage_size.resize(slot + 1, 0);
+  }
+  if (G->stage_size[slot] < bytes) {
+    if (G->stage[slot]) cudaFree(G->stage[slot]);
+    G->stage[slot] = nullptr;
+    G->stage_size[slot] = 0;
+    TRY(dalloc(G, &G->stage[slot], bytes));
+    G->stage_size[slot] = bytes;
+  }
+  if (p) CK(cudaMemcpyAsync(G->stage[slot], p, bytes, cudaMemcpyHostToDevice, G->stream));
+  *out = G->stage[slot];
+  return TOMO_OK;
+}
+
+tomo_status stage_out(tomo_grid* G, void* p, size_t bytes, int slot, void** out, bool* host) {
+  const void* o;
+  *host = !is_device_ptr(p);
+  if (!*host) {
+    *out = p;
+    return TOMO_OK;
+  }
+  if ((int)G->stage.size() <= slot) {
+    G->stage.resize(slot + 1, nullptr);
+    G->stage_size.resize(slot + 1, 0);
+  }
+  if (G->stage_size[slot] < bytes) {
+    if (G->stage[slot]) cudaFree(G->stage[slot]);
+    G->stage[slot] = nullptr;
+    G->stage_size[slot] = 0;
+    TRY(dalloc(G, &G->stage[slot], bytes));
+    G->stage_size[slot] = bytes;
+  }
+  o = G->stage[slot];
+  *out = const_cast<void*>(o);
+  return TOMO_OK;
+}
+
+tomo_status copy_back(tomo_grid* G, void* host, const void* dev, size_t bytes, bool is_host) {
+  if (!is_host) return TOMO_OK;
+  CK(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, G->stream));
+  return TOMO_OK;
+}
+
+tomo_status sync(tomo_grid* G) {
+  CK(cudaStreamSynchronize(G->stream));
+  return TOMO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Profiling of fine-level matrix-free launches
+// ---------------------------------------------------------------------------------------
+tomo_status prof_begin(tomo_grid* G, cudaEvent_t* e0) {
+  if (!G->prof) return TOMO_OK;
+  if (G->ev_used + 2 > G->ev.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      G->ev.push_back(e);
+    }
+  }
+  *e0 = G->ev[G->ev_used];
+  CK(cudaEventRecord(*e0, G->stream));
+  return TOMO_OK;
+}
+
+tomo_status prof_end(tomo_grid* G, double bytes) {
+  if (!G->prof) return TOMO_OK;
+  CK(cudaEventRecord(G->ev[G->ev_used + 1], G->stream));
+  G->ev_used += 2;
+  G->prof_launches += 1;
+  G->prof_bytes += bytes;
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status march(tomo_grid* G, int level, int mode, MarchArgs<T> a, const T* s_override = nullptr) {
+  const bool prof = G->prof && level == 0;
+  cudaEvent_t e0;
+  if (prof) TRY(prof_begin(G, &e0));
+  a.g = G->L[level].g;
+  a.s = s_override ? s_override : (const T*)G->L[level].s;
+  a.mask = G->L[level].mask;
+  a.partials = G->partials;
+  a.counter = G->counter;
+  int ctas = 0;
+  CK(launch_march<T>(G->stream, mode, a, elem_const<T>(G), G->num_sms, &ctas));
+  G->launches += 1;
+  if (prof) {
+    const double nv = 3.0 * a.g.nn * sizeof(T);
+    double bytes = nv + a.g.nel * (double)sizeof(T) + a.g.nn;  // x, s, mask
+    if (a.xlo) bytes += nv;
+    if (mode == M_APPLY) bytes += nv;                  // y
+    else if (mode == M_RESID) bytes += 2 * nv;         // b, y
+    else bytes += (a.c1 != T(0) ? 3 : 2) * nv;         // b, (xprev), x_new
+    TRY(prof_end(G, bytes));
+  }
+  return TOMO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Multigrid hierarchy
+// ---------------------------------------------------------------------------------------
+template <typename T>
+tomo_status setup_levels(tomo_grid* G) {
+  if (G->s64) {
+    CK(launch_convert<double, T>(G->stream, G->g.nel, (const T*)G->L[0].s, nullptr, G->s64));
+    G->launches += 1;
+  }
+  for (size_t l = 1; l < G->L.size(); ++l) {
+    CK(launch_coarsen_s<T>(G->stream, G->L[l - 1].g, G->L[l].g, (const T*)G->L[l - 1].s,
+                           (T*)G->L[l].s));
+    G->launches += 1;
+  }
+  if (G->L.size() > 1) {
+    auto& C = G->L.back();
+    CK(launch_coarse_factor<T>(G->stream, C.g, (const T*)C.s, C.mask, dense_k0<T>(G),
+                               (T*)G->coarseA, (T*)G->coarseD, &G->sc->status));
+    G->launches += 1;
+  }
+  return TOMO_OK;
+}
+
+struct Cheb {
+  double theta, delta, sigma;
+};
+
+Cheb cheb(const tomo_grid* G) {
+  const double hi = G->lam_hi, lo = hi / G->cheb_ratio;
+  Cheb c;
+  c.theta = 0.5 * (hi + lo);
+  c.delta = 0.5 * (hi - lo);
+  c.sigma = c.theta / c.delta;
+  return c;
+}
+
+// Chebyshev smoothing of K_l x = b on [lam_hi/ratio, lam_hi] of D^-1 K, degree K steps.
+// zero_start: x_0 = 0 (first step needs no product).  On return *X holds the result.
+template <typename T>
+tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_start, bool dot,
+                   const int* skip) {
+  const Cheb cb = cheb(G);
+  const int K = G->d.smoother_degree;
+  const T k0d = (T)G->k0diag;
+  auto& Lv = G->L[l];
+  double rho_prev = 1.0 / cb.sigma;
+  for (int s = 0; s < K; ++s) {
+    const bool last = (s == K - 1);
+    double c1, c2;
+    if (s == 0) {
+      c1 = 0.0;
+      c2 = 1.0 / cb.theta;
+    } else {
+      const double rho = 1.0 / (2.0 * cb.sigma - rho_prev);
+      c1 = rho * rho_prev;
+      c2 = 2.0 * rho / cb.delta;
+      rho_prev = rho;
+    }
+    const int dk = (dot && last) ? 2 : 0;
+    if (s == 0 && zero_start) {
+      CK(launch_jacobi<T>(G->stream, Lv.g, (const T*)Lv.s, Lv.mask, b, (T)c2, k0d, *X, *Y,
+                          G->partials, G->counter, G->sc, dk, skip));
+      G->launches += 1;
+      // X = x1, Y = x0 = 0: the recurrence continues with (x = X, xprev = Y)
+      continue;
+    }
+    MarchArgs<T> a{};
+    a.x = *X;
+    a.b = b;
+    a.xprev = *Y;
+    a.c1 = (T)c1;
+    a.c2 = (T)c2;
+    a.sc = G->sc;
+    a.dot_kind = dk;
+    a.skip = skip;
+    TRY(march<T>(G, l, M_CHEB, a));
+    std::swap(*X, *Y);
+  }
+  return TOMO_OK;
+}
+
+// z = V-cycle(b) on level l; *out receives the buffer holding z.
+template <typename T>
+tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int* skip) {
+  auto& Lv = G->L[l];
+  const int nl = (int)G->L.size();
+  if (l == nl - 1) {
+    CK(launch_coarse_apply<T>(G->stream, G->coarse_n, (const T*)G->coarseA,
+                              (const T*)G->coarseD, b, (T*)Lv.x, skip));
+    G->launches += 1;
+    *out = (T*)Lv.x;
+    return TOMO_OK;
+  }
+  T* X = (T*)Lv.x;
+  T* Y = (T*)Lv.xp;
+  TRY(smooth<T>(G, l, b, &X, &Y, true, false, skip));
+  {
+    MarchArgs<T> a{};
+    a.x = X;
+    a.b = b;
+    a.y = (T*)Lv.t;
+    a.skip = skip;
+    TRY(march<T>(G, l, M_RESID, a));
+  }
+  auto& Lc = G->L[l + 1];
+  CK(launch_restrict<T>(G->stream, Lv.g, Lc.g, (const T*)Lv.t, (T*)Lc.b, Lc.mask, skip));
+  G->launches += 1;
+  T* zc = nullptr;
+  TRY(vcycle<T>(G, l + 1, (const T*)Lc.b, &zc, false, skip));
+  CK(launch_prolong_add<T>(G->stream, Lv.g, Lc.g, zc, X, Lv.mask, skip));
+  G->launches += 1;
+  TRY(smooth<T>(G, l, b, &X, &Y, false, dot, skip));
+  *out = X;
+  return TOMO_OK;
+}
+
+// z = M r with rz/beta from the fused dot
+template <typename T>
+tomo_status precond(tomo_grid* G, const T* r, T** z) {
+  const int* skip = &G->sc->done;
+  if (G->d.precond == TOMO_PRECOND_JACOBI) {
+    auto& L0 = G->L[0];
+    CK(launch_jacobi<T>(G->stream, L0.g, (const T*)L0.s, L0.mask, r, T(1), (T)G->k0diag,
+                        (T*)L0.x, nullptr, G->partials, G->counter, G->sc, 2, skip));
+    G->launches += 1;
+    *z = (T*)L0.x;
+    return TOMO_OK;
+  }
+  return vcycle<T>(G, 0, r, z, true, skip);
+}
+
+// One PCG iteration: q = A p (alpha), x/r update (convergence test), residual replacement
+// when it % rr_every == 0 (decided on the device), z = M r (beta), p = z + beta p.  Every
+// kernel returns at once when the device flag sc->done is set.
+template <typename T>
+tomo_status enqueue_iteration(tomo_grid* G) {
+  const int n = 3 * G->g.nn;
+  T* r = (T*)G->r;
+  T* p = (T*)G->p;
+  T* q = (T*)G->q;
+  T* xhi = (T*)G->xhi;
+  T* xlo = G->prec == TOMO_FP32 ? (T*)G->xlo : nullptr;
+  MarchArgs<T> a{};
+  a.x = p;
+  a.y = q;
+  a.sc = G->sc;
+  a.dot_kind = 1;
+  a.skip = &G->sc->done;
+  TRY(march<T>(G, 0, M_APPLY, a));
+  CK(launch_cg_xr<T>(G->stream, n, xhi, xlo, r, p, q, G->partials, G->counter, G->sc));
+  G->launches += 1;
+  if (G->d.rr_every > 0) {
+    // residual replacement r = f - K x on iterations it % rr_every == 0 (device gate), in
+    // FP64 for both precisions
+    if constexpr (sizeof(T) == 8) {
+      MarchArgs<T> rr{};
+      rr.x = xhi;
+      rr.b = (const T*)G->f64;
+      rr.y = r;
+      rr.skip = &G->sc->done;
+      rr.gate = G->sc;
+      TRY(march<T>(G, 0, M_RESID, rr));
+    } else {
+      CK(launch_convert<double, float>(G->stream, n, xhi, xlo, G->x64, G->sc));
+      G->launches += 1;
+      MarchArgs<double> rr{};
+      rr.x = G->x64;
+      rr.b = G->f64;
+      rr.y = G->r64;
+      rr.skip = &G->sc->done;
+      rr.gate = G->sc;
+      TRY(march<double>(G, 0, M_RESID, rr, G->s64));
+      CK(launch_convert<float, double>(G->stream, n, G->r64, nullptr, r, G->sc));
+      G->launches += 1;
+    }
+  }
+  T* z = nullptr;
+  TRY(precond<T>(G, r, &z));
+  CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
+  G->launches += 1;
+  return TOMO_OK;
+}
+
+// Capture one iteration into the body of a conditional-while graph node; the body ends
+// with a kernel that clears the condition once CG has stopped.
+template <typename T>
+tomo_status build_loop_graph(tomo_grid* G) {
+  if (!G->cap_stream) CK(cudaStreamCreateWithFlags(&G->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    CK(e);
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t saved = G->stream;
+  G->stream = G->cap_stream;
+  e = cudaStreamBeginCaptureToGraph(G->stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  tomo_status st = TOMO_OK;
+  const int64_t before = G->launches;
+  if (e == cudaSuccess) {
+    st = enqueue_iteration<T>(G);
+    if (st == TOMO_OK) {
+      cudaError_t e2 = launch_loop_cond(G->stream, h, G->sc);
+      G->launches += 1;
+      if (e2 != cudaSuccess) st = fail(G, TOMO_ECUDA, "loop control launch failed: %s",
+                                       cudaGetErrorString(e2));
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(G->stream, &captured);
+    if (st == TOMO_OK && e3 != cudaSuccess) e = e3;
+  }
+  G->stream = saved;
+  G->iter_launches = G->launches - before;  // captured, not executed
+  G->launches = before;
+  if (e != cudaSuccess || st != TOMO_OK) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != TOMO_OK) return st;
+    CK(e);
+  }
+  e = cudaGraphInstantiate(&G->loop_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  return TOMO_OK;
+}
+
+// Preconditioned CG on K(s_0) x = f.  x (xhi [+ xlo]) holds the start on entry (warm) or is
+// zeroed (cold).  The iteration loop runs on the device (conditional-while graph); with
+// profiling enabled it is issued from the host in batches instead, so that every launch
+// can be bracketed by events.
+template <typename T>
+tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
+  const Geom g = G->g;
+  const int n = 3 * g.nn;
+  T* r = (T*)G->r;
+  T* p = (T*)G->p;
+  T* xhi = (T*)G->xhi;
+  T* xlo = G->prec == TOMO_FP32 ? (T*)G->xlo : nullptr;
+  const double ff = G->ff;
+  const double rtol = G->d.rtol;
+  CgScalars h{};
+  h.ff = ff;
+  h.tol2 = rtol * rtol * ff;
+  h.maxit = G->d.maxit;
+  h.rr_every = G->d.rr_every > 0 ? G->d.rr_every : 0;
+  *G->h_sc = h;
+  CK(cudaMemcpyAsync(G->sc, G->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, G->stream));
+  if (ff == 0.0) {
+    CK(cudaMemsetAsync(xhi, 0, sizeof(T) * n, G->stream));
+    if (xlo) CK(cudaMemsetAsync(xlo, 0, sizeof(T) * n, G->stream));
+    TRY(sync(G));
+    if (info) {
+      info->iters = 0;
+      info->rel_res = 0.0;
+      info->status = TOMO_OK;
+      info->mg_levels = (int)G->L.size();
+    }
+    G->have_solution = true;
+    return TOMO_OK;
+  }
+  if (warm) {
+    MarchArgs<T> a{};
+    a.x = xhi;
+    a.xlo = xlo;
+    a.b = (const T*)G->f_T;
+    a.y = r;
+    TRY(march<T>(G, 0, M_RESID, a));
+  } else {
+    CK(cudaMemsetAsync(xhi, 0, sizeof(T) * n, G->stream));
+    if (xlo) CK(cudaMemsetAsync(xlo, 0, sizeof(T) * n, G->stream));
+    CK(launch_mask_copy<T>(G->stream, g, (const T*)G->f_T, G->L[0].mask, r));
+    G->launches += 1;
+  }
+  CK(cudaMemsetAsync(p, 0, sizeof(T) * n, G->stream));
+  T* z = nullptr;
+  TRY(precond<T>(G, r, &z));
+  CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
+  G->launches += 1;
+  if (G->use_graph && !G->prof) {
+    if (!G->loop_exec) TRY(build_loop_graph<T>(G));
+    CK(cudaGraphLaunch(G->loop_exec, G->stream));
+    CK(cudaMemcpyAsync(G->h_sc, G->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, G->stream));
+    TRY(sync(G));
+    G->launches += (int64_t)G->h_sc->loops * G->iter_launches;
+  } else {
+    const int batch = 4;
+    int it = 0;
+    bool done = false;
+    while (!done) {
+      for (int b2 = 0; b2 < batch; ++b2, ++it) TRY(enqueue_iteration<T>(G));
+      CK(cudaMemcpyAsync(G->h_sc, G->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, G->stream));
+      TRY(sync(G));
+      done = G->h_sc->done != 0;
+      if (it > G->d.maxit + batch) done = true;
+    }
+  }
+  const CgScalars& hs = *G->h_sc;
+  tomo_status st = TOMO_OK;
+  if (hs.status & DEV_NAN) st = TOMO_ENAN;
+  else if (hs.status & DEV_BREAKDOWN) st = TOMO_ENOCONV;
+  else if (hs.rr > hs.tol2) st = TOMO_ENOCONV;
+  if (info) {
+    info->iters = hs.it;
+    info->rel_res = std::sqrt(std::max(hs.rr, 0.0) / ff);
+    info->status = st;
+    info->mg_levels = (int)G->L.size();
+  }
+  G->have_solution = true;
+  if (st == TOMO_ENAN) return fail(G, st, "NaN/Inf in the CG iteration at iteration %d", hs.it);
+  if (st == TOMO_ENOCONV)
+    return fail(G, st, "CG stopped after %d iterations at relative residual %.3e%s", hs.it,
+                std::sqrt(std::max(hs.rr, 0.0) / ff),
+                (hs.status & DEV_BREAKDOWN) ? " (breakdown)" : "");
+  return TOMO_OK;
+}
+
+// dV/dz = P^T v with v_e = h^3 (Section III-D), written to out.
+template <typename T>
+tomo_status volume_gradient(tomo_grid* G, T* out) {
+  const int ne = G->g.nel;
+  if (!G->dvdz_ready) {
+    std::vector<T> v(ne, (T)(G->d.h * G->d.h * G->d.h));
+    CK(cudaMemcpy(G->dvdz, v.data(), sizeof(T) * ne, cudaMemcpyHostToDevice));
+    G->dvdz_ready = true;  // G->dvdz holds the constant element volumes
+  }
+  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                      (const T*)G->dvdz, (const T*)G->Hs, out, 1, 0, T(0), T(0), T(0), T(0),
+                      nullptr));
+  G->launches += 1;
+  return TOMO_OK;
+}
+
+template <typename T>
+T* x_lo(tomo_grid* G) {
+  return G->prec == TOMO_FP32 ? (T*)G->xlo : nullptr;
+}
+
+tomo_status check_prec(tomo_grid* G, bool want64) {
+  if (!G) return TOMO_EINVAL;
+  if ((G->prec == TOMO_FP64) != want64)
+    return fail(G, TOMO_EINVAL, "entry point precision does not match the grid (%s grid)",
+                G->prec == TOMO_FP64 ? "FP64" : "FP32");
+  return TOMO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Entry point bodies
+// ---------------------------------------------------------------------------------------
+template <typename T>
+tomo_status do_filter(tomo_grid* G, const T* in, T* out, int transpose) {
+  if (!in || !out) return fail(G, TOMO_EINVAL, "null array");
+  const size_t bytes = sizeof(T) * (size_t)G->g.nel;
+  const void* din;
+  void* dout;
+  bool hin, hout;
+  TRY(stage_in(G, in, bytes, 0, &din, &hin));
+  TRY(stage_out(G, out, bytes, 1, &dout, &hout));
+  if (din == dout) return fail(G, TOMO_EINVAL, "in and out overlap");
+  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps, (const T*)din,
+                      (const T*)G->Hs, (T*)dout, transpose ? 1 : 0, 0, T(0), T(0), T(0), T(0),
+                      nullptr));
+  G->launches += 1;
+  TRY(copy_back(G, out, dout, bytes, hout));
+  if (hin || hout) TRY(sync(G));
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_apply(tomo_grid* G, const T* rho, const T* x, T* y) {
+  if (!rho || !x || !y) return fail(G, TOMO_EINVAL, "null array");
+  const size_t be = sizeof(T) * (size_t)G->g.nel, bn = sizeof(T) * 3 * (size_t)G->g.nn;
+  const void *drho, *dx;
+  void* dy;
+  bool h1, h2, h3;
+  TRY(stage_in(G, rho, be, 0, &drho, &h1));
+  TRY(stage_in(G, x, bn, 2, &dx, &h2));
+  TRY(stage_out(G, y, bn, 3, &dy, &h3));
+  if (dx == dy) return fail(G, TOMO_EINVAL, "x and y overlap");
+  const tomo_grid_desc& d = G->d;
+  CK(launch_material<T>(G->stream, G->g.nel, (const T*)drho, (T)d.E0, (T)d.Emin, (T)d.penal,
+                        (T)d.h, (T*)G->L[0].s));
+  G->launches += 1;
+  // the product sees masked input: fixed entries of x are ignored
+  T* xm = (T*)G->q;
+  CK(launch_mask_copy<T>(G->stream, G->g, (const T*)dx, G->L[0].mask, xm));
+  G->launches += 1;
+  MarchArgs<T> a{};
+  a.x = xm;
+  a.y = (T*)dy;
+  TRY(march<T>(G, 0, M_APPLY, a));
+  TRY(copy_back(G, y, dy, bn, h3));
+  if (h1 || h2 || h3) TRY(sync(G));
+  return TOMO_OK;
+}
+
+// r = f - K(rho) (u + ulo) on the free DOFs, by the product kernel's residual mode with the
+// pair input (FP32 grids) or plain input (FP64 grids).
+template <typename T>
+tomo_status do_residual(tomo_grid* G, const T* rho, const T* u, const T* ulo, T* r) {
+  if (!rho || !u || !r) return fail(G, TOMO_EINVAL, "null array");
+  if (ulo && G->prec == TOMO_FP64) return fail(G, TOMO_EINVAL, "u_lo is for FP32 grids");
+  const size_t be = sizeof(T) * (size_t)G->g.nel, bn = sizeof(T) * 3 * (size_t)G->g.nn;
+  const void *drho, *du, *dul = nullptr;
+  void* dr;
+  bool h1, h2, h3 = false, h4;
+  TRY(stage_in(G, rho, be, 0, &drho, &h1));
+  TRY(stage_in(G, u, bn, 2, &du, &h2));
+  if (ulo) TRY(stage_in(G, ulo, bn, 6, &dul, &h3));
+  TRY(stage_out(G, r, bn, 3, &dr, &h4));
+  const tomo_grid_desc& d = G->d;
+  CK(launch_material<T>(G->stream, G->g.nel, (const T*)drho, (T)d.E0, (T)d.Emin, (T)d.penal,
+                        (T)d.h, (T*)G->L[0].s));
+  G->launches += 1;
+  // masked copies: fixed entries of u are ignored
+  T* xm = (T*)G->q;
+  T* xl = (T*)G->p;
+  CK(launch_mask_copy<T>(G->stream, G->g, (const T*)du, G->L[0].mask, xm));
+  G->launches += 1;
+  if (dul) {
+    CK(launch_mask_copy<T>(G->stream, G->g, (const T*)dul, G->L[0].mask, xl));
+    G->launches += 1;
+  }
+  MarchArgs<T> a{};
+  a.x = xm;
+  a.xlo = dul ? xl : nullptr;
+  a.b = (const T*)G->f_T;
+  a.y = (T*)dr;
+  TRY(march<T>(G, 0, M_RESID, a));
+  TRY(copy_back(G, r, dr, bn, h4));
+  if (h1 || h2 || h3 || h4) TRY(sync(G));
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_solve(tomo_grid* G, const T* rho, T* u, tomo_solve_info* info) {
+  if (!rho || !u) return fail(G, TOMO_EINVAL, "null array");
+  const size_t be = sizeof(T) * (size_t)G->g.nel, bn = sizeof(T) * 3 * (size_t)G->g.nn;
+  const void *drho, *du;
+  bool h1, h2;
+  TRY(stage_in(G, rho, be, 0, &drho, &h1));
+  TRY(stage_in(G, u, bn, 2, &du, &h2));
+  const tomo_grid_desc& d = G->d;
+  CK(launch_material<T>(G->stream, G->g.nel, (const T*)drho, (T)d.E0, (T)d.Emin, (T)d.penal,
+                        (T)d.h, (T*)G->L[0].s));
+  G->launches += 1;
+  TRY(setup_levels<T>(G));
+  CK(launch_mask_copy<T>(G->stream, G->g, (const T*)du, G->L[0].mask, (T*)G->xhi));
+  G->launches += 1;
+  if (x_lo<T>(G)) CK(cudaMemsetAsync(G->xlo, 0, bn, G->stream));
+  tomo_status st = pcg<T>(G, true, info);
+  if (st != TOMO_OK && st != TOMO_ENOCONV && st != TOMO_ENAN) return st;
+  // u = x (pair summed)
+  void* dout;
+  bool hout;
+  TRY(stage_out(G, u, bn, 3, &dout, &hout));
+  CK(launch_convert<T, T>(G->stream, 3 * G->g.nn, (const T*)G->xhi, (const T*)x_lo<T>(G),
+                          (T*)dout));
+  G->launches += 1;
+  TRY(copy_back(G, u, dout, bn, hout));
+  TRY(sync(G));
+  return st;
+}
+
+template <typename T>
+tomo_status compliance_and_sens(tomo_grid* G, const T* drho, const T* du, const T* dulo,
+                                double* compliance, T* ddc) {
+  const tomo_grid_desc& d = G->d;
+  if (compliance) {
+    CK(launch_dot<double, T>(G->stream, 3 * G->g.nn, G->f64, du, dulo, G->partials, G->counter,
+                             G->dscal));
+    G->launches += 1;
+  }
+  if (ddc) {
+    CK(launch_sensitivity<T>(G->stream, G->g, drho, du, dulo, elem_const<T>(G), (T)d.penal,
+                             (T)d.E0, (T)d.Emin, (T)d.h, ddc));
+    G->launches += 1;
+  }
+  return TOMO_OK;
+}
+
+tomo_status write_scalar(tomo_grid* G, double* dst, const double* dev_src) {
+  if (!dst) return TOMO_OK;
+  if (is_device_ptr(dst)) {
+    CK(cudaMemcpyAsync(dst, dev_src, sizeof(double), cudaMemcpyDeviceToDevice, G->stream));
+    return TOMO_OK;
+  }
+  CK(cudaMemcpyAsync(G->h_scal, dev_src, sizeof(double), cudaMemcpyDeviceToHost, G->stream));
+  TRY(sync(G));
+  *dst = *G->h_scal;
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_sensitivity(tomo_grid* G, const T* rho, const T* u, double* compliance, T* dc) {
+  if (!rho || !u) return fail(G, TOMO_EINVAL, "null array");
+  const size_t be = sizeof(T) * (size_t)G->g.nel, bn = sizeof(T) * 3 * (size_t)G->g.nn;
+  const void *drho, *du;
+  void* ddc = nullptr;
+  bool h1, h2, h3 = false;
+  TRY(stage_in(G, rho, be, 0, &drho, &h1));
+  TRY(stage_in(G, u, bn, 2, &du, &h2));
+  if (dc) TRY(stage_out(G, dc, be, 1, &ddc, &h3));
+  TRY(compliance_and_sens<T>(G, (const T*)drho, (const T*)du, nullptr, compliance, (T*)ddc));
+  if (dc) TRY(copy_back(G, dc, ddc, be, h3));
+  TRY(write_scalar(G, compliance, G->dscal));
+  if (h1 || h2 || h3) TRY(sync(G));
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_oc(tomo_grid* G, const T* z, const T* dcdz, const T* dvdz, double volfrac,
+                  double move, T* znew, double* change) {
+  if (!z || !dcdz || !dvdz || !znew) return fail(G, TOMO_EINVAL, "null array");
+  if (!(volfrac > 0.0 && volfrac <= 1.0) || !(move > 0.0))
+    return fail(G, TOMO_EINVAL, "volfrac must be in (0,1] and move > 0");
+  const size_t be = sizeof(T) * (size_t)G->g.nel;
+  const void *dz, *ddc, *dw;
+  void* dzn;
+  bool h1, h2, h3, h4;
+  TRY(stage_in(G, z, be, 0, &dz, &h1));
+  TRY(stage_in(G, dcdz, be, 1, &ddc, &h2));
+  TRY(stage_in(G, dvdz, be, 4, &dw, &h3));
+  TRY(stage_out(G, znew, be, 5, &dzn, &h4));
+  if (dzn == dz || dzn == ddc || dzn == dw) return fail(G, TOMO_EINVAL, "z_new overlaps an input");
+  const double vmax = volfrac * (double)G->g.nel * G->d.h * G->d.h * G->d.h;
+  CK(launch_oc<T>(G->stream, G->g.nel, (const T*)dz, (const T*)ddc, (const T*)dw, vmax, move,
+                  (T*)dzn, G->partials, G->counter, G->dscal + 2, G->dscal + 1,
+                  oc_max_blocks(G->g.nel)));
+  G->launches += (sizeof(T) == 8) ? 11 : 10;
+  TRY(copy_back(G, znew, dzn, be, h4));
+  TRY(write_scalar(G, change, G->dscal + 1));
+  if (h1 || h2 || h3 || h4) TRY(sync(G));
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T* dvdz,
+                        tomo_solve_info* info) {
+  if (!z || !dcdz) return fail(G, TOMO_EINVAL, "null array");
+  const size_t be = sizeof(T) * (size_t)G->g.nel;
+  const tomo_grid_desc& d = G->d;
+  const void* dz;
+  void *ddc, *ddv = nullptr;
+  bool h1, h2, h3 = false;
+  TRY(stage_in(G, z, be, 0, &dz, &h1));
+  TRY(stage_out(G, dcdz, be, 1, &ddc, &h2));
+  if (dvdz) TRY(stage_out(G, dvdz, be, 4, &ddv, &h3));
+  T* rho = (T*)G->rho;
+  // S1: rho = P z, s = h (Emin + rho^p (E0 - Emin))
+  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps, (const T*)dz,
+                      (const T*)G->Hs, rho, 0, 1, (T)d.E0, (T)d.Emin, (T)d.penal, (T)d.h,
+                      (T*)G->L[0].s));
+  G->launches += 1;
+  // S2: coarse moduli, coarsest factorisation
+  TRY(setup_levels<T>(G));
+  // S3-S5: PCG from a zero start
+  tomo_status st = pcg<T>(G, false, info);
+  if (st != TOMO_OK) return st;
+  // S6: compliance and dc/drho
+  TRY(compliance_and_sens<T>(G, rho, (const T*)G->xhi, (const T*)x_lo<T>(G), compliance,
+                             (T*)G->dcp));
+  // S7: dc/dz = P^T dc/drho, dV/dz = P^T v
+  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                      (const T*)G->dcp, (const T*)G->Hs, (T*)ddc, 1, 0, T(0), T(0), T(0), T(0),
+                      nullptr));
+  G->launches += 1;
+  if (ddv) TRY(volume_gradient<T>(G, (T*)ddv));
+  TRY(copy_back(G, dcdz, ddc, be, h2));
+  if (dvdz) TRY(copy_back(G, dvdz, ddv, be, h3));
+  TRY(write_scalar(G, compliance, G->dscal));
+  if (h1 || h2 || h3) TRY(sync(G));
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_get_u(tomo_grid* G, T* u) {
+  if (!u) return fail(G, TOMO_EINVAL, "null array");
+  if (!G->have_solution) return fail(G, TOMO_EINVAL, "no solution computed yet");
+  const size_t bn = sizeof(T) * 3 * (size_t)G->g.nn;
+  void* dout;
+  bool hout;
+  TRY(stage_out(G, u, bn, 3, &dout, &hout));
+  CK(launch_convert<T, T>(G->stream, 3 * G->g.nn, (const T*)G->xhi, (const T*)x_lo<T>(G),
+                          (T*)dout));
+  G->launches += 1;
+  TRY(copy_back(G, u, dout, bn, hout));
+  if (hout) TRY(sync(G));
+  return TOMO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Creation
+// ---------------------------------------------------------------------------------------
+double lam_max_element(const double K0[576]) {
+  // power iteration on diag(K0)^-1 K0 (similar to a symmetric matrix, eigenvalues >= 0)
+  std::vector<double> x(24), y(24);
+  for (int i = 0; i < 24; ++i) x[i] = 1.0 + 0.01 * i * ((i & 1) ? -1 : 1);
+  double lam = 0.0;
+  for (int it = 0; it < 2000; ++it) {
+    double nrm = 0.0;
+    for (int i = 0; i < 24; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < 24; ++j) s += K0[i * 24 + j] * x[j];
+      y[i] = s / K0[i * 25];
+      nrm += y[i] * y[i];
+    }
+    nrm = std::sqrt(nrm);
+    double xn = 0.0;
+    for (int i = 0; i < 24; ++i) xn += x[i] * x[i];
+    lam = nrm / std::sqrt(xn);
+    for (int i = 0; i < 24; ++i) x[i] = y[i] / nrm;
+  }
+  return lam;
+}
+
+std::vector<uint8_t> coarse_mask(const Geom& gf, const std::vector<uint8_t>& mf, const Geom& gc) {
+  std::vector<uint8_t> mc(gc.nn, 0);
+  for (int K = 0; K < gc.nzn; ++K)
+    for (int J = 0; J < gc.nyn; ++J)
+      for (int I = 0; I < gc.nxn; ++I) {
+        uint8_t m = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+          const int k = 2 * K + dz;
+          if (k < 0 || k >= gf.nzn) continue;
+          for (int dy = -1; dy <= 1; ++dy) {
+            const int j = 2 * J + dy;
+            if (j < 0 || j >= gf.nyn) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int i = 2 * I + dx;
+              if (i < 0 || i >= gf.nxn) continue;
+              m |= mf[i + gf.nxn * (j + gf.nyn * k)];
+            }
+          }
+        }
+        mc[I + gc.nxn * (J + gc.nyn * K)] = m;
+      }
+  return mc;
+}
+
+void free_grid(tomo_grid* G) {
+  if (!G) return;
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  for (auto& Lv : G->L) {
+    F(Lv.s);
+    F(Lv.mask);
+    F(Lv.b);
+    F(Lv.x);
+    F(Lv.xp);
+    F(Lv.t);
+  }
+  F(G->d_taps);
+  F(G->d_tapw);
+  F(G->Hs);
+  F(G->dvdz);
+  F(G->coarseA);
+  F(G->coarseD);
+  F(G->f_T);
+  F(G->f64);
+  F(G->r);
+  F(G->p);
+  F(G->q);
+  F(G->xhi);
+  F(G->xlo);
+  F(G->rho);
+  F(G->dcp);
+  F(G->s64);
+  F(G->x64);
+  F(G->r64);
+  F(G->partials);
+  F(G->counter);
+  F(G->sc);
+  F(G->dscal);
+  if (G->h_sc) cudaFreeHost(G->h_sc);
+  if (G->h_scal) cudaFreeHost(G->h_scal);
+  for (void* s : G->stage) F(s);
+  if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
+  if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
+  for (auto e : G->ev) cudaEventDestroy(e);
+  delete G;
+}
+
+template <typename T>
+tomo_status create_impl(tomo_grid* G) {
+  const Geom g = G->g;
+  const size_t nv = sizeof(T) * 3 * (size_t)g.nn, ne = sizeof(T) * (size_t)g.nel;
+  // levels
+  {
+    tomo_level L0;
+    L0.g = g;
+    L0.h = G->d.h;
+    L0.hmask.assign(g.nn, 0);
+    for (int c = 0; c < 3; ++c)
+      for (int n = 0; n < g.nn; ++n)
+        if (G->fixed[(size_t)c * g.nn + n]) L0.hmask[n] |= (uint8_t)(1u << c);
+    G->L.push_back(std::move(L0));
+  }
+  if (G->d.precond == TOMO_PRECOND_MG) {
+    const int want = G->d.mg_levels;
+    while (true) {
+      const Geom& gf = G->L.back().g;
+      const int nl = (int)G->L.size();
+      const bool small = 3 * gf.nn <= 192;
+      const bool can = std::max(gf.nx, std::max(gf.ny, gf.nz)) > 1;
+      if (!can) break;
+      if (want > 0 && nl >= want && 3 * gf.nn <= kMaxDenseDofs) break;
+      if (want <= 0 && small) break;
+      tomo_level Lc;
+      Lc.g = make_geom((gf.nx + 1) / 2, (gf.ny + 1) / 2, (gf.nz + 1) / 2);
+      Lc.h = G->L.back().h * 2.0;
+      Lc.hmask = coarse_mask(gf, G->L.back().hmask, Lc.g);
+      G->L.push_back(std::move(Lc));
+    }
+    if (G->L.size() < 2) {
+      // a single-level grid: the dense solve of the grid itself would be the whole solve;
+      // keep one coarse level so that the V-cycle structure holds
+      const Geom& gf = G->L.back().g;
+      tomo_level Lc;
+      Lc.g = make_geom((gf.nx + 1) / 2, (gf.ny + 1) / 2, (gf.nz + 1) / 2);
+      Lc.h = G->L.back().h * 2.0;
+      Lc.hmask = coarse_mask(gf, G->L.back().hmask, Lc.g);
+      G->L.push_back(std::move(Lc));
+    }
+    G->coarse_n = 3 * G->L.back().g.nn;
+    if (G->coarse_n > kMaxDenseDofs)
+      return fail(G, TOMO_EINVAL, "coarsest level has %d DOFs (> %d); use more levels",
+                  G->coarse_n, kMaxDenseDofs);
+  }
+  for (size_t l = 0; l < G->L.size(); ++l) {
+    auto& Lv = G->L[l];
+    const size_t lnv = sizeof(T) * 3 * (size_t)Lv.g.nn;
+    TRY(dalloc(G, &Lv.s, sizeof(T) * (size_t)Lv.g.nel));
+    TRY(dalloc(G, (void**)&Lv.mask, Lv.g.nn));
+    CK(cudaMemcpy(Lv.mask, Lv.hmask.data(), Lv.g.nn, cudaMemcpyHostToDevice));
+    if (l > 0) TRY(dalloc(G, &Lv.b, lnv));
+    TRY(dalloc(G, &Lv.x, lnv));
+    TRY(dalloc(G, &Lv.xp, lnv));
+    TRY(dalloc(G, &Lv.t, lnv));
+  }
+  if (G->coarse_n > 0) {
+    TRY(dalloc(G, &G->coarseA, sizeof(T) * (size_t)G->coarse_n * G->coarse_n));
+    TRY(dalloc(G, &G->coarseD, sizeof(T) * (size_t)G->coarse_n));
+  }
+  // fine vectors
+  TRY(dalloc(G, &G->f_T, nv));
+  TRY(dalloc(G, (void**)&G->f64, sizeof(double) * 3 * (size_t)g.nn));
+  TRY(dalloc(G, &G->r, nv));
+  TRY(dalloc(G, &G->p, nv));
+  TRY(dalloc(G, &G->q, nv));
+  TRY(dalloc(G, &G->xhi, nv));
+  if (G->prec == TOMO_FP32) TRY(dalloc(G, &G->xlo, nv));
+  if (G->prec == TOMO_FP32 && G->d.rr_every > 0) {
+    TRY(dalloc(G, (void**)&G->s64, sizeof(double) * (size_t)g.nel));
+    TRY(dalloc(G, (void**)&G->x64, sizeof(double) * 3 * (size_t)g.nn));
+    TRY(dalloc(G, (void**)&G->r64, sizeof(double) * 3 * (size_t)g.nn));
+  }
+  TRY(dalloc(G, &G->rho, ne));
+  TRY(dalloc(G, &G->dcp, ne));
+  TRY(dalloc(G, &G->Hs, ne));
+  TRY(dalloc(G, &G->dvdz, ne));
+  {
+    std::vector<double> fm(G->f);
+    for (size_t k = 0; k < fm.size(); ++k)
+      if (G->fixed[k]) fm[k] = 0.0;
+    G->ff = 0.0;
+    for (double v : fm) G->ff += v * v;
+    std::vector<T> ft(fm.begin(), fm.end());
+    CK(cudaMemcpy(G->f_T, ft.data(), nv, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->f64, fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice));
+  }
+  // reductions
+  G->partials_n = std::max(1 << 16, oc_partials_needed(g.nel));
+  TRY(dalloc(G, (void**)&G->partials, sizeof(double) * (size_t)G->partials_n));
+  TRY(dalloc(G, (void**)&G->counter, sizeof(unsigned) * 4));
+  CK(cudaMemset(G->counter, 0, sizeof(unsigned) * 4));
+  TRY(dalloc(G, (void**)&G->sc, sizeof(CgScalars)));
+  CK(cudaMemset(G->sc, 0, sizeof(CgScalars)));
+  TRY(dalloc(G, (void**)&G->dscal, sizeof(double) * 8));
+  CK(cudaMallocHost((void**)&G->h_sc, sizeof(CgScalars)));
+  CK(cudaMallocHost((void**)&G->h_scal, sizeof(double) * 8));
+  // filter taps and weight sums
+  G->taps = filter_taps(G->d.rmin);
+  G->ntaps = (int)G->taps.size();
+  {
+    std::vector<int4> t4(G->ntaps);
+    std::vector<T> tw(G->ntaps);
+    for (int q = 0; q < G->ntaps; ++q) {
+      t4[q] = make_int4(G->taps[q].di, G->taps[q].dj, G->taps[q].dk, 0);
+      tw[q] = (T)G->taps[q].w;
+    }
+    TRY(dalloc(G, (void**)&G->d_taps, sizeof(int4) * std::max(1, G->ntaps)));
+    TRY(dalloc(G, &G->d_tapw, sizeof(T) * std::max(1, G->ntaps)));
+    CK(cudaMemcpy(G->d_taps, t4.data(), sizeof(int4) * G->ntaps, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(G->d_tapw, tw.data(), sizeof(T) * G->ntaps, cudaMemcpyHostToDevice));
+    std::vector<T> ones(g.nel, T(1));
+    CK(cudaMemcpy(G->dcp, ones.data(), ne, cudaMemcpyHostToDevice));
+    CK(launch_filter<T>(G->stream, g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                        (const T*)G->dcp, nullptr, (T*)G->Hs, 2, 0, T(0), T(0), T(0), T(0),
+                        nullptr));
+    G->launches += 1;
+    TRY(sync(G));
+  }
+  return TOMO_OK;
+}
+
+}  // namespace
+
+// =======================================================================================
+// extern "C"
+// =======================================================================================
+extern "C" {
+
+void tomo_default_desc(tomo_grid_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->nx = d->ny = d->nz = 1;
+  d->h = 1.0;
+  d->E0 = 1.0;
+  d->Emin = 1e-9;
+  d->nu = 0.3;
+  d->penal = 3.0;
+  d->rmin = 1.5;
+  d->precision = TOMO_FP32;
+  d->precond = TOMO_PRECOND_MG;
+  d->rtol = 1e-6;
+  d->maxit = 2000;
+  d->mg_levels = 0;
+  d->smoother_degree = 2;
+  d->cheb_ratio = 10.0;
+  d->rr_every = 50;
+  d->stream = nullptr;
+}
+
+tomo_status tomo_create_grid(const tomo_grid_desc* desc, tomo_grid** out) {
+  tomo_grid* G = nullptr;
+  if (!desc || !out) return fail(nullptr, TOMO_EINVAL, "null descriptor or output");
+  *out = nullptr;
+  const tomo_grid_desc& d = *desc;
+  if (d.nx < 1 || d.ny < 1 || d.nz < 1)
+    return fail(nullptr, TOMO_EINVAL, "grid dimensions must be >= 1 (got %d %d %d)", d.nx, d.ny,
+                d.nz);
+  const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  if (3 * nn >= (1LL << 31) - 1)
+    return fail(nullptr, TOMO_EINVAL, "grid too large for 32-bit nodal indexing");
+  if (!(d.h > 0.0) || !(d.E0 > d.Emin) || !(d.Emin >= 0.0) || !(d.nu > -1.0 && d.nu < 0.5) ||
+      !(d.penal >= 1.0) || !(d.rmin > 0.0) || d.rmin > 16.0)
+    return fail(nullptr, TOMO_EINVAL,
+                "invalid material/filter parameters (need h>0, E0>Emin>=0, -1<nu<0.5, p>=1, "
+                "0<rmin<=16)");
+  if (!d.fixed_dof || !d.f) return fail(nullptr, TOMO_EINVAL, "fixed_dof and f are required");
+  if (d.precision != TOMO_FP64 && d.precision != TOMO_FP32)
+    return fail(nullptr, TOMO_EINVAL, "unknown precision %d", d.precision);
+  if (d.precond != TOMO_PRECOND_MG && d.precond != TOMO_PRECOND_JACOBI)
+    return fail(nullptr, TOMO_EINVAL, "unknown preconditioner %d", d.precond);
+  G = new (std::nothrow) tomo_grid();
+  if (!G) return fail(nullptr, TOMO_ENOMEM, "host allocation failed");
+  G->d = d;
+  G->d.fixed_dof = nullptr;
+  G->d.f = nullptr;
+  if (G->d.rtol <= 0.0) G->d.rtol = 1e-6;
+  if (G->d.maxit <= 0) G->d.maxit = 2000;
+  if (G->d.smoother_degree <= 0) G->d.smoother_degree = 2;
+  if (G->d.rr_every == 0) G->d.rr_every = 50;
+  G->cheb_ratio = G->d.cheb_ratio > 1.0 ? G->d.cheb_ratio : 10.0;
+  G->prec = d.precision;
+  G->tsize = d.precision == TOMO_FP64 ? 8 : 4;
+  G->stream = (cudaStream_t)d.stream;
+  G->g = make_geom(d.nx, d.ny, d.nz);
+  G->fixed.assign(d.fixed_dof, d.fixed_dof + 3 * nn);
+  for (auto& v : G->fixed) v = v ? 1 : 0;
+  G->f.assign(d.f, d.f + 3 * nn);
+  g_cur_err = &G->err;
+  if (cudaGetDevice(&G->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&G->num_sms, cudaDevAttrMultiProcessorCount, G->device) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    delete G;
+    return fail(nullptr, TOMO_ECUDA, "no usable CUDA device");
+  }
+  build_unit_stiffness(d.nu, G->K0);
+  if (!build_hadamard_blocks(G->K0, G->blk, &G->k0diag)) {
+    delete G;
+    return fail(nullptr, TOMO_EINVAL, "element stiffness is not cube-symmetric");
+  }
+  G->lam_hi = lam_max_element(G->K0);
+  tomo_status st = G->prec == TOMO_FP64 ? create_impl<double>(G) : create_impl<float>(G);
+  if (st != TOMO_OK) {
+    g_create_err = G->err;
+    free_grid(G);
+    return st;
+  }
+  *out = G;
+  return TOMO_OK;
+}
+
+tomo_status tomo_destroy_grid(tomo_grid* G) {
+  if (!G) return TOMO_OK;
+  cudaStreamSynchronize(G->stream);
+  free_grid(G);
+  return TOMO_OK;
+}
+
+tomo_status tomo_set_stream(tomo_grid* G, void* stream) {
+  if (!G) return TOMO_EINVAL;
+  G->stream = (cudaStream_t)stream;
+  G->d.stream = stream;
+  return TOMO_OK;
+}
+
+#define ENTER(G, want64)                  \
+  do {                                    \
+    if (!(G)) return TOMO_EINVAL;         \
+    TRY(check_prec(G, want64));           \
+    (G)->err.clear();                     \
+    g_cur_err = &(G)->err;                \
+  } while (0)
+
+tomo_status tomo_filter(tomo_grid* G, const float* in, float* out, int transpose) {
+  ENTER(G, false);
+  return do_filter<float>(G, in, out, transpose);
+}
+tomo_status tomo_filter_d(tomo_grid* G, const double* in, double* out, int transpose) {
+  ENTER(G, true);
+  return do_filter<double>(G, in, out, transpose);
+}
+tomo_status tomo_apply_stiffness(tomo_grid* G, const float* rho, const float* x, float* y) {
+  ENTER(G, false);
+  return do_apply<float>(G, rho, x, y);
+}
+tomo_status tomo_apply_stiffness_d(tomo_grid* G, const double* rho, const double* x, double* y) {
+  ENTER(G, true);
+  return do_apply<double>(G, rho, x, y);
+}
+tomo_status tomo_residual(tomo_grid* G, const float* rho, const float* u, const float* u_lo,
+                          float* r) {
+  ENTER(G, false);
+  return do_residual<float>(G, rho, u, u_lo, r);
+}
+tomo_status tomo_residual_d(tomo_grid* G, const double* rho, const double* u, double* r) {
+  ENTER(G, true);
+  return do_residual<double>(G, rho, u, nullptr, r);
+}
+tomo_status tomo_solve(tomo_grid* G, const float* rho, float* u, tomo_solve_info* info) {
+  ENTER(G, false);
+  return do_solve<float>(G, rho, u, info);
+}
+tomo_status tomo_solve_d(tomo_grid* G, const double* rho, double* u, tomo_solve_info* info) {
+  ENTER(G, true);
+  return do_solve<double>(G, rho, u, info);
+}
+tomo_status tomo_sensitivity(tomo_grid* G, const float* rho, const float* u, double* c,
+                             float* dc) {
+  ENTER(G, false);
+  return do_sensitivity<float>(G, rho, u, c, dc);
+}
+tomo_status tomo_sensitivity_d(tomo_grid* G, const double* rho, const double* u, double* c,
+                               double* dc) {
+  ENTER(G, true);
+  return do_sensitivity<double>(G, rho, u, c, dc);
+}
+tomo_status tomo_oc_step(tomo_grid* G, const float* z, const float* dcdz, const float* dvdz,
+                         double volfrac, double move, float* z_new, double* change) {
+  ENTER(G, false);
+  return do_oc<float>(G, z, dcdz, dvdz, volfrac, move, z_new, change);
+}
+tomo_status tomo_oc_step_d(tomo_grid* G, const double* z, const double* dcdz, const double* dvdz,
+                           double volfrac, double move, double* z_new, double* change) {
+  ENTER(G, true);
+  return do_oc<double>(G, z, dcdz, dvdz, volfrac, move, z_new, change);
+}
+tomo_status tomo_gradient(tomo_grid* G, const float* z, double* c, float* dcdz, float* dvdz,
+                          tomo_solve_info* info) {
+  ENTER(G, false);
+  return do_gradient<float>(G, z, c, dcdz, dvdz, info);
+}
+tomo_status tomo_gradient_d(tomo_grid* G, const double* z, double* c, double* dcdz,
+                            double* dvdz, tomo_solve_info* info) {
+  ENTER(G, true);
+  return do_gradient<double>(G, z, c, dcdz, dvdz, info);
+}
+tomo_status tomo_get_displacement(tomo_grid* G, float* u) {
+  ENTER(G, false);
+  return do_get_u<float>(G, u);
+}
+tomo_status tomo_get_displacement_d(tomo_grid* G, double* u) {
+  ENTER(G, true);
+  return do_get_u<double>(G, u);
+}
+
+tomo_status tomo_get_counts(const tomo_grid* G, int64_t* n_el, int64_t* n_nodes,
+                            int32_t* mg_levels) {
+  if (!G) return TOMO_EINVAL;
+  if (n_el) *n_el = G->g.nel;
+  if (n_nodes) *n_nodes = G->g.nn;
+  if (mg_levels) *mg_levels = (int32_t)G->L.size();
+  return TOMO_OK;
+}
+
+tomo_status tomo_get_launch_count(const tomo_grid* G, int64_t* launches) {
+  if (!G || !launches) return TOMO_EINVAL;
+  *launches = G->launches;
+  return TOMO_OK;
+}
+
+tomo_status tomo_profile_enable(tomo_grid* G, int enable) {
+  if (!G) return TOMO_EINVAL;
+  G->prof = enable != 0;
+  return TOMO_OK;
+}
+
+tomo_status tomo_profile_read(tomo_grid* G, int64_t* launches, double* total_ms,
+                              double* algorithmic_bytes) {
+  if (!G) return TOMO_EINVAL;
+  G->err.clear();
+  g_cur_err = &G->err;
+  TRY(sync(G));
+  double ms = 0.0;
+  for (size_t q = 0; q + 1 < G->ev_used; q += 2) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, G->ev[q], G->ev[q + 1]));
+    ms += t;
+  }
+  if (launches) *launches = G->prof_launches;
+  if (total_ms) *total_ms = ms;
+  if (algorithmic_bytes) *algorithmic_bytes = G->prof_bytes;
+  G->ev_used = 0;
+  G->prof_launches = 0;
+  G->prof_bytes = 0.0;
+  return TOMO_OK;
+}
+
+const char* tomo_last_error(const tomo_grid* G) {
+  if (!G) return g_create_err.c_str();
+  return G->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Shared device/host definitions of the tomo library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+namespace tomo {
+
+// ------------------------------------------------------------------------------------
+// Geometry of one grid level: nx*ny*nz hex8 elements, (nx+1)(ny+1)(nz+1) nodes.
+// Elements e = i + nx*(j + ny*k); nodes n = i + nxn*(j + nyn*k); nodal vectors SoA.
+// ------------------------------------------------------------------------------------
+struct Geom {
+  int nx, ny, nz;     // elements
+  int nxn, nyn, nzn;  // nodes per axis
+  int nn;             // nodes
+  int nel;            // elements
+};
+
+inline Geom make_geom(int nx, int ny, int nz) {
+  Geom g;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.nxn = nx + 1; g.nyn = ny + 1; g.nzn = nz + 1;
+  g.nn = g.nxn * g.nyn * g.nzn;
+  g.nel = nx * ny * nz;
+  return g;
+}
+
+// ------------------------------------------------------------------------------------
+// Element operator constants.  K0 is the 24x24 stiffness of the unit cube with E = 1
+// (element DOF order 3a + c, local node a = ax + 2 ay + 4 az).  In the per-component
+// Walsh-Hadamard basis X_c[m] = sum_s (-1)^{popc(m & s)} x_c[s] it is block diagonal with
+// eight symmetric 3x3 blocks, block k coupling the modes (c, m = k ^ (1 << c)), c = 0..2.
+// blk[k][c][c'] holds that block scaled by 1/64 so that K0 x = H (blk H x) per component.
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct ElemConst {
+  T blk[8][3][3];
+  T k0diag;      // K0 diagonal entry (identical for all 24 DOFs of the cube)
+};
+
+template <typename T>
+struct DenseK0 {
+  T k[576];
+};
+
+// Status word bits written by device code (never a trap).
+enum : unsigned {
+  DEV_OK = 0u,
+  DEV_NAN = 1u,
+  DEV_BREAKDOWN = 2u,
+  DEV_TIMEOUT = 4u,
+};
+
+// Scalars of one CG solve, kept in device memory so that no host round trip is needed
+// between kernels.
+struct CgScalars {
+  double rz;       // r^T z of the current iterate
+  double rz_new;
+  double pq;       // p^T A p
+  double rr;       // r^T r
+  double ff;       // f^T f
+  double alpha, beta;
+  double tol2;     // (rtol ||f||)^2
+  int it;          // iterations done
+  int done;        // 1 once converged or stopped
+  int maxit;
+  unsigned status; // DEV_* bits
+  int loops;       // iterations launched by the device-side loop (termination guard)
+  int rr_every;    // residual replacement interval (0: off)
+};
+
+#define TOMO_CUDA_TRY(expr)                                                        \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess) return ::tomo::cuda_fail(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+// ------------------------------------------------------------------------------------
+// Device helpers
+// ------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum NV doubles over the block, then over the grid: every block writes its partial to
+// partials[NV*blockIdx + v]; the last block to finish adds the partials in block order
+// (deterministic) and calls fin(totals) with thread 0.  counter must start at 0 and is
+// reset by the last block.  All threads of the block must call this.
+template <int NV, class Fin>
+__device__ void grid_reduce(double (&v)[NV], double* partials, unsigned* counter, Fin fin) {
+  __shared__ double s_red[32][NV];
+  __shared__ bool s_last;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int lane = tid & 31, wid = tid >> 5, nw = (nthreads + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = warp_sum(v[q]);
+    if (lane == 0) s_red[wid][q] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = lane < nw ? s_red[lane][q] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) partials[(size_t)NV * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) + q] = s;
+    }
+    if (lane == 0) {
+      __threadfence();
+      unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+      unsigned t = atomicAdd(counter, 1u);
+      s_last = (t == nb - 1);
+    }
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  for (unsigned b = tid; b < nb; b += nthreads) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] += __ldcg(partials + (size_t)NV * b + q);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = warp_sum(acc[q]);
+    if (lane == 0) s_red[wid][q] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tot[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += s_red[w][q];
+      tot[q] = s;
+    }
+    *counter = 0u;
+    fin(tot);
+  }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace tomo

@@ -1,0 +1,196 @@
+// Internal host-side declarations of the tomo library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tomo.h"
+#include "common.cuh"
+
+namespace tomo {
+
+struct FilterTap {
+  int di, dj, dk;
+  double w;
+};
+
+void build_unit_stiffness(double nu, double K0[576]);
+bool build_hadamard_blocks(const double K0[576], double blk[8][3][3], double* k0diag);
+std::vector<FilterTap> filter_taps(double rmin);
+
+// Largest coarsest-level DOF count solved by a dense inverse in one CTA.
+constexpr int kMaxDenseDofs = 648;
+// Upper bound of lambda_max(D^-1 K) over any grid: max over one element of
+// lambda_max(diag(K0)^-1 K0) (x^T K x <= lam_e x^T D x element by element).
+constexpr int kTY = 16;  // rows of node columns per CTA in the marching product
+
+enum MarchMode { M_APPLY = 0, M_RESID = 1, M_CHEB = 2 };
+
+template <typename T>
+struct MarchArgs {
+  Geom g;
+  int kz;               // node planes per z-chunk
+  const T* s;           // h*E per element
+  const uint8_t* mask;  // fixed bits per node
+  const T* x;           // input vector (hi part when pair input)
+  const T* xlo;         // lo part (pair input) or nullptr
+  const T* b;           // right-hand side (RESID, CHEB)
+  T* xprev;             // CHEB: x_{k-1} at entry, x_{k+1} at exit (own node only)
+  T* y;                 // APPLY / RESID output
+  T c1, c2;             // CHEB coefficients
+  double* partials;     // dot reduction scratch (APPLY: x.y, CHEB: b.x_new)
+  unsigned* counter;
+  CgScalars* sc;        // dot result consumer (may be null when no dot)
+  int dot_kind;         // 0 none, 1: pq -> alpha, 2: rz_new -> beta
+  const int* skip;      // if non-null and *skip != 0 the kernel returns at once
+  const CgScalars* gate;  // residual replacement: run only when gate->it % gate->rr_every == 0
+};
+
+// All kernels are launched on `st`.  Wrappers return 0 or a cudaError_t.
+template <typename T>
+cudaError_t launch_march(cudaStream_t st, int mode, const MarchArgs<T>& a, const ElemConst<T>& c,
+                         int num_sms, int* grid_ctas);
+
+template <typename T>
+cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* mask, const T* b,
+                          T c2, T k0diag, T* x1, T* x0zero, double* partials,
+                          unsigned* counter, CgScalars* sc, int dot_kind, const int* skip);
+template <typename T>
+cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* rc,
+                            const uint8_t* mask_c, const int* skip);
+template <typename T>
+cudaError_t launch_prolong_add(cudaStream_t st, Geom gf, Geom gc, const T* xc, T* xf,
+                               const uint8_t* mask_f, const int* skip);
+template <typename T>
+cudaError_t launch_coarsen_s(cudaStream_t st, Geom gf, Geom gc, const T* sf, T* sc);
+template <typename T>
+cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint8_t* mask,
+                                 const DenseK0<T>& K0, T* A, T* dscale, unsigned* status);
+template <typename T>
+cudaError_t launch_coarse_apply(cudaStream_t st, int n, const T* Ainv, const T* dscale,
+                                const T* r, T* z, const int* skip);
+
+// CG recurrences.  xlo != nullptr selects the float-pair iterate (x = xhi + xlo).
+template <typename T>
+cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* p, const T* q,
+                         double* partials, unsigned* counter, CgScalars* sc);
+template <typename T>
+cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc);
+cudaError_t launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, CgScalars* sc);
+int march_blocks_per_sm(int tsize, int mode, bool pair, bool dot);
+
+// Dots and vector helpers.
+template <typename TA, typename TB>
+cudaError_t launch_dot(cudaStream_t st, int n, const TA* a, const TB* b, const TB* blo,
+                       double* partials, unsigned* counter, double* out);
+template <typename T>
+cudaError_t launch_mask_copy(cudaStream_t st, Geom g, const T* in, const uint8_t* mask, T* out);
+// out = in (+ inlo), converted; with a gate, only on residual-replacement iterations.
+template <typename TO, typename TI>
+cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo, TO* out,
+                           const CgScalars* gate = nullptr);
+
+// Filter, material, sensitivity, OC.
+template <typename T>
+cudaError_t launch_filter(cudaStream_t st, Geom g, const int4* taps, const T* tapw, int ntaps,
+                          const T* in, const T* Hs, T* out, int mode, int material, T E0,
+                          T Emin, T penal, T h, T* s_out);
+template <typename T>
+cudaError_t launch_material(cudaStream_t st, int n, const T* rho, T E0, T Emin, T penal, T h,
+                            T* s);
+template <typename T>
+cudaError_t launch_sensitivity(cudaStream_t st, Geom g, const T* rho, const T* u, const T* ulo,
+                               const ElemConst<T>& c, T penal, T E0, T Emin, T h, T* dc);
+template <typename T>
+cudaError_t launch_oc(cudaStream_t st, int n, const T* z, const T* dc, const T* w, double vmax,
+                      double move, T* znew, double* partials, unsigned* counter,
+                      double* bracket, double* change_out, int max_blocks);
+int oc_partials_needed(int n);
+int oc_max_blocks(int n);
+
+}  // namespace tomo
+
+// ------------------------------------------------------------------------------------
+// The handle
+// ------------------------------------------------------------------------------------
+struct tomo_level {
+  tomo::Geom g;
+  double h;
+  void* s = nullptr;        // T[nel]: h * E
+  uint8_t* mask = nullptr;  // [nn]
+  void* b = nullptr;        // T[3nn] right-hand side (levels >= 1)
+  void* x = nullptr;        // T[3nn] iterate
+  void* xp = nullptr;       // T[3nn] previous iterate / ping-pong
+  void* t = nullptr;        // T[3nn] residual
+  std::vector<uint8_t> hmask;
+};
+
+struct tomo_grid {
+  tomo_grid_desc d{};
+  int prec = TOMO_FP32;
+  size_t tsize = 4;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  tomo::Geom g{};
+  std::vector<uint8_t> fixed;  // host copy, 3*nn
+  std::vector<double> f;       // host copy, 3*nn
+  double K0[576];
+  double blk[8][3][3];
+  double k0diag = 0.0;
+  double lam_hi = 0.0;         // Chebyshev upper end
+  double cheb_ratio = 10.0;    // Chebyshev interval [lam_hi / ratio, lam_hi]
+  std::vector<tomo::FilterTap> taps;
+  int4* d_taps = nullptr;      // (di, dj, dk, 0)
+  void* d_tapw = nullptr;      // T[ntaps] weights
+  int ntaps = 0;
+  void* Hs = nullptr;          // T[nel]
+  void* dvdz = nullptr;        // T[nel] P^T v (cached)
+  bool dvdz_ready = false;
+  std::vector<tomo_level> L;
+  int coarse_n = 0;            // coarsest DOFs (dense)
+  void* coarseA = nullptr;     // T[n*n]
+  void* coarseD = nullptr;     // T[n]
+  // fine-level vectors
+  void* f_T = nullptr;         // T[3nn] load
+  double* f64 = nullptr;       // double[3nn] load (compliance)
+  void* r = nullptr;
+  void* p = nullptr;
+  void* q = nullptr;
+  void* xhi = nullptr;         // iterate (FP64: x; FP32: hi part)
+  void* xlo = nullptr;         // FP32 only
+  void* rho = nullptr;         // T[nel] physical density scratch
+  void* dcp = nullptr;         // T[nel] dc/drho scratch
+  // reductions
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  tomo::CgScalars* sc = nullptr;
+  double* dscal = nullptr;     // device doubles for misc results (compliance, change, bracket)
+  tomo::CgScalars* h_sc = nullptr;  // pinned
+  double* h_scal = nullptr;         // pinned
+  // staging for host pointers
+  std::vector<void*> stage;
+  std::vector<size_t> stage_size;
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  int64_t prof_launches = 0;
+  double prof_bytes = 0.0;
+  bool have_solution = false;
+  int partials_n = 0;
+  double ff = 0.0;                  // ||f||^2 over free DOFs
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  cudaGraphExec_t loop_exec = nullptr;  // device-side PCG loop (conditional while)
+  bool use_graph = true;
+  int64_t launches = 0;             // kernels launched (executed graph bodies included)
+  int64_t iter_launches = 0;        // kernels in one captured loop body
+  // FP64 residual replacement of FP32 grids: r = f - K(x_hi + x_lo) evaluated in FP64
+  double* s64 = nullptr;            // h*E at the fine level, double
+  double* x64 = nullptr;            // iterate, double
+  double* r64 = nullptr;            // residual, double
+};

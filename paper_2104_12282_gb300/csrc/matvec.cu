@@ -1,0 +1,361 @@
+// Matrix-free hex8 stiffness product y = K(rho) x and the multigrid smoother step built on
+// it (state equation of Eq. 4, Section III-D).  K = sum_e s_e K0 with s_e = h E_e.
+//
+// Design (GB300): one thread per node column (i, j), marching along z through the node
+// planes of a z-chunk.  A CTA is 32 lanes (x) by kTY rows (y).  Element (i, j, k) is
+// evaluated by thread (i, j) from the raw 2x2x2 block of node values:
+//   own column (planes k, k+1, registers), row j+1 (shared memory), lane i+1 (shuffle).
+// Per element, per component, the 8 node values minus the value at local node 0 are
+// transformed by an 8-point Walsh-Hadamard transform (differences first, so FP32 rounding
+// is relative to the displacement differences, not to the displacements), multiplied by
+// K0's eight 3x3 Hadamard-basis blocks scaled by s_e, and transformed back to the eight
+// corner forces.  Corner forces reach their nodes without atomics: +x corners by shuffle,
+// +y corners through shared memory, +z corners carried in registers to the next plane.
+// Lanes 0 and 31 and rows 0 and kTY-1 are halo (their outputs are not written); each
+// z-chunk recomputes one element layer below it.
+#include "common.cuh"
+#include "host.h"
+
+namespace tomo {
+
+template <typename T>
+__device__ __forceinline__ void fwht8(T (&v)[8]) {
+#pragma unroll
+  for (int st = 1; st < 8; st <<= 1) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      if ((s & st) == 0) {
+        const T a = v[s], b = v[s + st];
+        v[s] = a + b;
+        v[s + st] = a - b;
+      }
+    }
+  }
+}
+
+// W_c[m] = s * sum_c' blk[k][c][c'] X_c'[k ^ (1 << c')] for k = m ^ (1 << c); translation
+// modes (m = 0) and structural zeros skipped.
+template <typename T>
+__device__ __forceinline__ void block_apply(const ElemConst<T>& C, T se, const T (&X)[3][8],
+                                            T (&W)[3][8]) {
+  T Xs[3][8];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Xs[c][0] = T(0);
+#pragma unroll
+    for (int m = 1; m < 8; ++m) Xs[c][m] = se * X[c][m];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) W[c][0] = T(0);
+  // classes 0 and 7: full 3x3
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int k = kk ? 7 : 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T acc = C.blk[k][c][0] * Xs[0][k ^ 1];
+      acc += C.blk[k][c][1] * Xs[1][k ^ 2];
+      acc += C.blk[k][c][2] * Xs[2][k ^ 4];
+      W[c][k ^ (1 << c)] = acc;
+    }
+  }
+  // classes 1, 2, 4: the translation member (c == log2 k) is decoupled and zero
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int k = 1 << t;
+    const int ca = (t + 1) % 3, cb = (t + 2) % 3;
+    const T xa = Xs[ca][k ^ (1 << ca)], xb = Xs[cb][k ^ (1 << cb)];
+    W[ca][k ^ (1 << ca)] = C.blk[k][ca][ca] * xa + C.blk[k][ca][cb] * xb;
+    W[cb][k ^ (1 << cb)] = C.blk[k][cb][ca] * xa + C.blk[k][cb][cb] * xb;
+  }
+  // classes 3, 5, 6: the member with m = 7 (component t below) is decoupled
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int k = 7 ^ (1 << t);  // t=2 -> 3, t=1 -> 5, t=0 -> 6
+    const int ca = (t + 1) % 3, cb = (t + 2) % 3;
+    const T xa = Xs[ca][k ^ (1 << ca)], xb = Xs[cb][k ^ (1 << cb)];
+    W[ca][k ^ (1 << ca)] = C.blk[k][ca][ca] * xa + C.blk[k][ca][cb] * xb;
+    W[cb][k ^ (1 << cb)] = C.blk[k][cb][ca] * xa + C.blk[k][cb][cb] * xb;
+    W[t][7] = C.blk[k][t][t] * Xs[t][7];
+  }
+}
+
+template <typename T, int MODE, bool PAIR, bool DOT>
+__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
+    k_march(const __grid_constant__ MarchArgs<T> A, const __grid_constant__ ElemConst<T> C) {
+  if (A.skip != nullptr && *A.skip) return;
+  if (A.gate != nullptr && (A.gate->rr_every <= 0 || (A.gate->it % A.gate->rr_every) != 0))
+    return;
+  const Geom g = A.g;
+  const int l = threadIdx.x, r = threadIdx.y;
+  const int i = (int)blockIdx.x * 30 - 1 + l;
+  const int j = (int)blockIdx.y * (kTY - 2) - 1 + r;
+  const int kb = (int)blockIdx.z * A.kz;
+  const int ke = min(kb + A.kz, g.nzn);
+  const int nn = g.nn;
+  const bool col_in = (i >= 0 && i < g.nxn && j >= 0 && j < g.nyn);
+  const bool el_col = (i >= 0 && i < g.nx && j >= 0 && j < g.ny && l < 31);
+  const bool out_col = col_in && l >= 1 && l <= 30 && r >= 1 && r <= kTY - 2;
+  const int colbase = col_in ? i + g.nxn * j : 0;
+  const int plane = g.nxn * g.nyn;
+  const int ecol = el_col ? i + g.nx * j : 0;
+  const int eplane = g.nx * g.ny;
+
+  constexpr int NA = PAIR ? 6 : 3;
+  __shared__ T sA[NA][kTY][32];
+  __shared__ T sG[6][kTY][32];
+  __shared__ T sS[kTY][32];
+
+  auto load_plane = [&](int k, T (&v)[NA]) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) v[q] = T(0);
+    if (col_in && k >= 0 && k < g.nzn) {
+      const int n = colbase + plane * k;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[c] = ldg(A.x + (size_t)c * nn + n);
+        if (PAIR) v[3 + c] = ldg(A.xlo + (size_t)c * nn + n);
+      }
+    }
+  };
+  auto load_s = [&](int k) -> T {
+    return (el_col && k >= 0 && k < g.nz) ? ldg(A.s + (ecol + eplane * k)) : T(0);
+  };
+
+  // raw node values: A* own column, B* row j+1; *0 plane k, *1 plane k+1
+  T A0[NA], B0[NA];
+  load_plane(kb - 1, A0);
+#pragma unroll
+  for (int q = 0; q < NA; ++q) sA[q][r][l] = A0[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NA; ++q) B0[q] = (r + 1 < kTY) ? sA[q][r + 1][l] : T(0);
+  __syncthreads();
+  // one-step-ahead prefetch of the next plane and element layer
+  T A1n[NA];
+  load_plane(kb, A1n);
+  T sen = load_s(kb - 1);
+
+  T carry[3] = {T(0), T(0), T(0)};
+  T carryS = T(0);
+  double dot = 0.0;
+
+  for (int k = kb - 1; k < ke; ++k) {
+    T A1[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) A1[q] = A1n[q];
+    const T se = sen;
+    load_plane(k + 2, A1n);
+    sen = load_s(k + 1);
+    // epilogue operands of node (i, j, k), consumed at the end of this step
+    const bool emit = out_col && k >= kb;
+    const int n_out = colbase + plane * (k < 0 ? 0 : k);
+    unsigned mk = 0u;
+    T bv[3] = {T(0), T(0), T(0)}, xp[3] = {T(0), T(0), T(0)};
+    if (emit) {
+      mk = A.mask[n_out];
+      if (MODE != M_APPLY) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bv[c] = ldg(A.b + (size_t)c * nn + n_out);
+      }
+      if (MODE == M_CHEB && A.c1 != T(0)) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xp[c] = A.xprev[(size_t)c * nn + n_out];
+      }
+    }
+
+#pragma unroll
+    for (int q = 0; q < NA; ++q) sA[q][r][l] = A1[q];
+    __syncthreads();
+    T B1[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) B1[q] = (r + 1 < kTY) ? sA[q][r + 1][l] : T(0);
+
+    // ---- forward: differences against local node 0, Walsh-Hadamard per component ----
+    T X[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      // local node s = sx + 2 sy + 4 sz
+      T v[8];
+      const T a0 = A0[c];
+      const T c0 = __shfl_down_sync(0xffffffffu, A0[c], 1);
+      const T c1v = __shfl_down_sync(0xffffffffu, A1[c], 1);
+      const T d0 = __shfl_down_sync(0xffffffffu, B0[c], 1);
+      const T d1 = __shfl_down_sync(0xffffffffu, B1[c], 1);
+      v[0] = T(0);
+      v[1] = c0 - a0;
+      v[2] = B0[c] - a0;
+      v[3] = d0 - a0;
+      v[4] = A1[c] - a0;
+      v[5] = c1v - a0;
+      v[6] = B1[c] - a0;
+      v[7] = d1 - a0;
+      if (PAIR) {
+        const T al = A0[3 + c];
+        const T cl0 = __shfl_down_sync(0xffffffffu, A0[3 + c], 1);
+        const T cl1 = __shfl_down_sync(0xffffffffu, A1[3 + c], 1);
+        const T dl0 = __shfl_down_sync(0xffffffffu, B0[3 + c], 1);
+        const T dl1 = __shfl_down_sync(0xffffffffu, B1[3 + c], 1);
+        v[1] += cl0 - al;
+        v[2] += B0[3 + c] - al;
+        v[3] += dl0 - al;
+        v[4] += A1[3 + c] - al;
+        v[5] += cl1 - al;
+        v[6] += B1[3 + c] - al;
+        v[7] += dl1 - al;
+      }
+      fwht8(v);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) X[c][m] = v[m];
+    }
+    T W[3][8];
+    block_apply(C, se, X, W);
+    // ---- inverse: corner forces y_c[s] = sum_m chi_m(s) W_c[m] ----
+    T G[3][4];  // contributions to node column i for corners (sy, sz) -> index sy + 2 sz
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = W[c][m];
+      fwht8(v);
+      // +x corners (sx = 1) belong to node column i+1: send to lane + 1
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T fromleft = __shfl_up_sync(0xffffffffu, v[2 * q + 1], 1);
+        G[c][q] = v[2 * q] + (l > 0 ? fromleft : T(0));
+      }
+    }
+    T Sx = T(0);
+    if (MODE == M_CHEB) {
+      const T fromleft = __shfl_up_sync(0xffffffffu, se, 1);
+      Sx = se + (l > 0 ? fromleft : T(0));
+    }
+    // +y corners (sy = 1) belong to node row j+1: through shared memory
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      sG[2 * c + 0][r][l] = G[c][1];  // sy=1, sz=0
+      sG[2 * c + 1][r][l] = G[c][3];  // sy=1, sz=1
+    }
+    if (MODE == M_CHEB) sS[r][l] = Sx;
+    __syncthreads();
+    T Tz[3][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T b0 = r > 0 ? sG[2 * c + 0][r - 1][l] : T(0);
+      const T b1 = r > 0 ? sG[2 * c + 1][r - 1][l] : T(0);
+      Tz[c][0] = G[c][0] + b0;  // sz = 0: node plane k
+      Tz[c][1] = G[c][2] + b1;  // sz = 1: node plane k+1
+    }
+    T Sy = T(0);
+    if (MODE == M_CHEB) Sy = Sx + (r > 0 ? sS[r - 1][l] : T(0));
+
+    // ---- node (i, j, k) is complete ----
+    T out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      out[c] = carry[c] + Tz[c][0];
+      carry[c] = Tz[c][1];
+    }
+    const T Stot = carryS + Sy;
+    carryS = Sy;
+    if (emit) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const bool fx = (mk >> c) & 1u;
+        const size_t idx = (size_t)c * nn + n_out;
+        if (MODE == M_APPLY) {
+          const T yv = fx ? T(0) : out[c];
+          A.y[idx] = yv;
+          if (DOT) dot += (double)(A0[c] * yv);
+        } else if (MODE == M_RESID) {
+          A.y[idx] = fx ? T(0) : (bv[c] - out[c]);
+        } else {
+          const T dg = C.k0diag * Stot;
+          const T w = dg > T(0) ? (bv[c] - out[c]) / dg : T(0);
+          T xn = A0[c] + A.c2 * w;
+          if (A.c1 != T(0)) xn += A.c1 * (A0[c] - xp[c]);
+          xn = fx ? T(0) : xn;
+          A.xprev[idx] = xn;
+          if (DOT) dot += (double)(bv[c] * xn);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      A0[q] = A1[q];
+      B0[q] = B1[q];
+    }
+  }
+  if (DOT) {
+    double v[1] = {dot};
+    CgScalars* sc = A.sc;
+    const int kind = A.dot_kind;
+    grid_reduce<1>(v, A.partials, A.counter, [sc, kind](const double* tot) {
+      if (kind == 1) {
+        sc->pq = tot[0];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+          sc->status |= isfinite(tot[0]) ? DEV_BREAKDOWN : DEV_NAN;
+          sc->done = 1;
+          sc->alpha = 0.0;
+        } else {
+          sc->alpha = sc->rz / tot[0];
+        }
+      } else if (kind == 2) {
+        sc->rz_new = tot[0];
+        if (!isfinite(tot[0])) {
+          sc->status |= DEV_NAN;
+          sc->done = 1;
+        }
+        sc->beta = sc->rz != 0.0 ? tot[0] / sc->rz : 0.0;
+        sc->rz = tot[0];
+      }
+    });
+  }
+}
+
+template <typename T>
+cudaError_t launch_march(cudaStream_t st, int mode, const MarchArgs<T>& a, const ElemConst<T>& c,
+                         int num_sms, int* grid_ctas) {
+  const Geom& g = a.g;
+  MarchArgs<T> args = a;
+  const int gx = (g.nxn + 29) / 30;
+  const int gy = (g.nyn + kTY - 3) / (kTY - 2);
+  // z-chunks: about one full wave of resident CTAs (2 per SM), chunks of >= 4 planes
+  const int tiles = gx * gy;
+  const int target = (sizeof(T) == 4 ? 2 : 1) * (num_sms > 0 ? num_sms : 152);
+  int nzc = target / tiles;
+  if (nzc < 1) nzc = 1;
+  int kz = (g.nzn + nzc - 1) / nzc;
+  if (kz < 4) kz = 4;
+  if (kz > g.nzn) kz = g.nzn;
+  nzc = (g.nzn + kz - 1) / kz;
+  args.kz = kz;
+  dim3 grid(gx, gy, nzc), block(32, kTY);
+  if (grid_ctas) *grid_ctas = gx * gy * nzc;
+  const bool pair = a.xlo != nullptr;
+  const bool dot = a.dot_kind != 0;
+  if (mode == M_APPLY) {
+    if (dot) k_march<T, M_APPLY, false, true><<<grid, block, 0, st>>>(args, c);
+    else k_march<T, M_APPLY, false, false><<<grid, block, 0, st>>>(args, c);
+  } else if (mode == M_RESID) {
+    if constexpr (sizeof(T) == 4) {
+      if (pair) {
+        k_march<T, M_RESID, true, false><<<grid, block, 0, st>>>(args, c);
+        return cudaGetLastError();
+      }
+    }
+    if (pair) return cudaErrorInvalidValue;
+    k_march<T, M_RESID, false, false><<<grid, block, 0, st>>>(args, c);
+  } else {
+    if (dot) k_march<T, M_CHEB, false, true><<<grid, block, 0, st>>>(args, c);
+    else k_march<T, M_CHEB, false, false><<<grid, block, 0, st>>>(args, c);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_march<float>(cudaStream_t, int, const MarchArgs<float>&,
+                                         const ElemConst<float>&, int, int*);
+template cudaError_t launch_march<double>(cudaStream_t, int, const MarchArgs<double>&,
+                                          const ElemConst<double>&, int, int*);
+
+}  // namespace tomo

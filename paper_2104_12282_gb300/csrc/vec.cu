@@ -1,0 +1,502 @@
+// Multigrid transfers, coarse operators, the coarsest dense solve, CG recurrences and
+// reductions.  The solve of the state equation of Eq. 4 (Section III-D) is preconditioned
+// CG, the standard solver the paper names (PCG; multigrid is the stated alternative).
+#include "common.cuh"
+#include "host.h"
+
+namespace tomo {
+
+constexpr int kRedBlocks = 304;  // reduction grid (2 x 152 SMs)
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ bool skipped(const int* skip) { return skip != nullptr && *skip; }
+
+// ---------------------------------------------------------------------------------------
+// First Chebyshev step from a zero guess: x1 = c2 D^-1 b, x0 = 0.  D = k0diag * (sum of s_e
+// over the elements around the node) is the diagonal of K (all three components equal).
+// Optional dot b.x1 for the Jacobi-preconditioned CG (dot_kind 2).
+// ---------------------------------------------------------------------------------------
+template <typename T, bool DOT>
+__global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restrict__ mask,
+                         const T* __restrict__ b, T c2, T k0diag, T* __restrict__ x1,
+                         T* __restrict__ x0, double* partials, unsigned* counter, CgScalars* sc,
+                         const int* skip) {
+  if (skipped(skip)) return;
+  double dot = 0.0;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nn; n += gridDim.x * blockDim.x) {
+    const int i = n % g.nxn, j = (n / g.nxn) % g.nyn, k = n / (g.nxn * g.nyn);
+    T S = T(0);
+#pragma unroll
+    for (int dz = -1; dz <= 0; ++dz)
+#pragma unroll
+      for (int dy = -1; dy <= 0; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 0; ++dx) {
+          const int ei = i + dx, ej = j + dy, ek = k + dz;
+          if (ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny && ek >= 0 && ek < g.nz)
+            S += s[ei + g.nx * (ej + g.ny * ek)];
+        }
+    const T dg = k0diag * S;
+    const unsigned mk = mask[n];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t idx = (size_t)c * g.nn + n;
+      const T bv = b[idx];
+      const T v = (((mk >> c) & 1u) || !(dg > T(0))) ? T(0) : c2 * bv / dg;
+      x1[idx] = v;
+      if (x0) x0[idx] = T(0);
+      if (DOT) dot += (double)(bv * v);
+    }
+  }
+  if (DOT) {
+    double v[1] = {dot};
+    grid_reduce<1>(v, partials, counter, [sc](const double* tot) {
+      sc->rz_new = tot[0];
+      if (!isfinite(tot[0])) { sc->status |= DEV_NAN; sc->done = 1; }
+      sc->beta = sc->rz != 0.0 ? tot[0] / sc->rz : 0.0;
+      sc->rz = tot[0];
+    });
+  }
+}
+
+template <typename T>
+cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* mask, const T* b,
+                          T c2, T k0diag, T* x1, T* x0zero, double* partials,
+                          unsigned* counter, CgScalars* sc, int dot_kind, const int* skip) {
+  int blocks = (g.nn + 255) / 256;
+  if (dot_kind) {
+    if (blocks > kRedBlocks) blocks = kRedBlocks;
+    k_jacobi<T, true><<<blocks, 256, 0, st>>>(g, s, mask, b, c2, k0diag, x1, x0zero, partials,
+                                              counter, sc, skip);
+  } else {
+    if (blocks > 4096) blocks = 4096;
+    k_jacobi<T, false><<<blocks, 256, 0, st>>>(g, s, mask, b, c2, k0diag, x1, x0zero, nullptr,
+                                               nullptr, nullptr, skip);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Restriction r_c = P^T r_f (trilinear, weights 1, 1/2 per axis), masked on the coarse grid.
+// Fine node i maps to coarse node i/2 (even) or to (i-1)/2 and (i+1)/2 (odd).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ rc,
+                           const uint8_t* __restrict__ mask_c, const int* skip) {
+  if (skipped(skip)) return;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gc.nn; n += gridDim.x * blockDim.x) {
+    const int I = n % gc.nxn, J = (n / gc.nxn) % gc.nyn, K = n / (gc.nxn * gc.nyn);
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int k = 2 * K + dz;
+      if (k < 0 || k >= gf.nzn) continue;
+      const T wz = dz == 0 ? T(1) : T(0.5);
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int j = 2 * J + dy;
+        if (j < 0 || j >= gf.nyn) continue;
+        const T wy = dy == 0 ? wz : T(0.5) * wz;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int i = 2 * I + dx;
+          if (i < 0 || i >= gf.nxn) continue;
+          const T w = dx == 0 ? wy : T(0.5) * wy;
+          const int m = i + gf.nxn * (j + gf.nyn * k);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[c] += w * rf[(size_t)c * gf.nn + m];
+        }
+      }
+    }
+    const unsigned mk = mask_c[n];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rc[(size_t)c * gc.nn + n] = ((mk >> c) & 1u) ? T(0) : acc[c];
+  }
+}
+
+template <typename T>
+cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* rc,
+                            const uint8_t* mask_c, const int* skip) {
+  int blocks = (gc.nn + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_restrict<T><<<blocks, 256, 0, st>>>(gf, gc, rf, rc, mask_c, skip);
+  return cudaGetLastError();
+}
+
+// x_f += P x_c (trilinear interpolation), masked on the fine grid.
+template <typename T>
+__global__ void k_prolong_add(Geom gf, Geom gc, const T* __restrict__ xc, T* __restrict__ xf,
+                              const uint8_t* __restrict__ mask_f, const int* skip) {
+  if (skipped(skip)) return;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gf.nn; n += gridDim.x * blockDim.x) {
+    const int i = n % gf.nxn, j = (n / gf.nxn) % gf.nyn, k = n / (gf.nxn * gf.nyn);
+    const int i0 = i >> 1, i1 = (i + 1) >> 1;
+    const int j0 = j >> 1, j1 = (j + 1) >> 1;
+    const int k0 = k >> 1, k1 = (k + 1) >> 1;
+    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
+    const unsigned mk = mask_f[n];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* v = xc + (size_t)c * gc.nn;
+      T acc;
+      auto at = [&](int a, int b2, int d) { return v[a + gc.nxn * (b2 + gc.nyn * d)]; };
+      if ((i & 1) == 0 && (j & 1) == 0 && (k & 1) == 0) {
+        acc = at(i0, j0, k0);
+      } else {
+        acc = T(0);
+        const int ii[2] = {i0, i1}, jj[2] = {j0, j1}, kk[2] = {k0, k1};
+        const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+        for (int c3 = 0; c3 < nk; ++c3)
+          for (int b3 = 0; b3 < nj; ++b3)
+            for (int a3 = 0; a3 < ni; ++a3) acc += at(ii[a3], jj[b3], kk[c3]);
+        acc *= wi * wj * wk;
+      }
+      const size_t idx = (size_t)c * gf.nn + n;
+      if (!((mk >> c) & 1u)) xf[idx] += acc;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(cudaStream_t st, Geom gf, Geom gc, const T* xc, T* xf,
+                               const uint8_t* mask_f, const int* skip) {
+  int blocks = (gf.nn + 255) / 256;
+  if (blocks > 16384) blocks = 16384;
+  k_prolong_add<T><<<blocks, 256, 0, st>>>(gf, gc, xc, xf, mask_f, skip);
+  return cudaGetLastError();
+}
+
+// Coarse element (edge 2h) modulus = mean of its (up to 8) children; with s = h E this is
+// s_c = (sum of children s_f) / 4.  Children outside the fine grid count as void.
+template <typename T>
+__global__ void k_coarsen_s(Geom gf, Geom gc, const T* __restrict__ sf, T* __restrict__ sc) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gc.nel; e += gridDim.x * blockDim.x) {
+    const int I = e % gc.nx, J = (e / gc.nx) % gc.ny, K = e / (gc.nx * gc.ny);
+    T acc = T(0);
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+          if (i < gf.nx && j < gf.ny && k < gf.nz) acc += sf[i + gf.nx * (j + gf.ny * k)];
+        }
+    sc[e] = acc * T(0.25);
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarsen_s(cudaStream_t st, Geom gf, Geom gc, const T* sf, T* sc) {
+  int blocks = (gc.nel + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_coarsen_s<T><<<blocks, 256, 0, st>>>(gf, gc, sf, sc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Coarsest level: assemble the dense K (fixed DOFs -> identity), scale symmetrically by
+// D^-1/2, invert in place by Gauss-Jordan (SPD: no pivoting), one CTA.
+// A holds D^-1/2 K^-1 D^-1/2 ... stored as inv(D^-1/2 K D^-1/2); dscale = D^-1/2.
+// ---------------------------------------------------------------------------------------
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(1024) k_coarse_factor(Geom g, const T* __restrict__ s,
+                                                        const uint8_t* __restrict__ mask,
+                                                        const __grid_constant__ DenseK0<T> K0,
+                                                        T* __restrict__ A, T* __restrict__ dscale,
+                                                        unsigned* status) {
+  const int n = 3 * g.nn;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  extern __shared__ unsigned char smem_raw[];
+  T* col = reinterpret_cast<T*>(smem_raw);
+  T* M = SMEM ? col + n : A;  // the working matrix: shared memory when it fits
+  __shared__ T s_piv;
+  for (int q = tid; q < n * n; q += nt) M[q] = T(0);
+  __syncthreads();
+  for (int e = 0; e < g.nel; ++e) {
+    const int ei = e % g.nx, ej = (e / g.nx) % g.ny, ek = e / (g.nx * g.ny);
+    const T se = s[e];
+    for (int pq = tid; pq < 576; pq += nt) {
+      const int p = pq / 24, q = pq % 24;
+      const int a = p / 3, c = p % 3, b = q / 3, d = q % 3;
+      const int na = (ei + (a & 1)) + g.nxn * ((ej + ((a >> 1) & 1)) + g.nyn * (ek + (a >> 2)));
+      const int nb = (ei + (b & 1)) + g.nxn * ((ej + ((b >> 1) & 1)) + g.nyn * (ek + (b >> 2)));
+      if (((mask[na] >> c) & 1u) || ((mask[nb] >> d) & 1u)) continue;
+      M[(size_t)(c * g.nn + na) * n + d * g.nn + nb] += se * K0.k[pq];
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < n; q += nt) {
+    const int node = q % g.nn, c = q / g.nn;
+    if ((mask[node] >> c) & 1u) M[(size_t)q * n + q] = T(1);
+    T dv = M[(size_t)q * n + q];
+    if (!(dv > T(0))) {
+      atomicOr(status, DEV_BREAKDOWN);
+      dv = T(1);
+      M[(size_t)q * n + q] = T(1);
+    }
+    dscale[q] = T(1) / sqrt(dv);
+  }
+  __syncthreads();
+  for (int q = tid; q < n * n; q += nt) {
+    const int a = q / n, b = q % n;
+    M[q] *= dscale[a] * dscale[b];
+  }
+  __syncthreads();
+  // in-place Gauss-Jordan inversion of the scaled SPD matrix (no pivoting)
+  for (int k = 0; k < n; ++k) {
+    for (int i = tid; i < n; i += nt) col[i] = M[(size_t)i * n + k];
+    __syncthreads();
+    if (tid == 0) {
+      T p = col[k];
+      if (!(p > T(0))) {
+        atomicOr(status, DEV_BREAKDOWN);
+        p = T(1);
+      }
+      s_piv = T(1) / p;
+    }
+    __syncthreads();
+    const T ip = s_piv;
+    for (int jcol = tid; jcol < n; jcol += nt) {
+      const T v = (jcol == k) ? T(1) : M[(size_t)k * n + jcol];
+      M[(size_t)k * n + jcol] = v * ip;
+    }
+    __syncthreads();
+    for (int q = tid; q < n * n; q += nt) {
+      const int i = q / n, jcol = q % n;
+      if (i == k) continue;
+      const T v = (jcol == k) ? T(0) : M[q];
+      M[q] = v - col[i] * M[(size_t)k * n + jcol];
+    }
+    __syncthreads();
+  }
+  if (SMEM)
+    for (int q = tid; q < n * n; q += nt) A[q] = M[q];
+}
+
+template <typename T>
+cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint8_t* mask,
+                                 const DenseK0<T>& K0, T* A, T* dscale, unsigned* status) {
+  const int n = 3 * g.nn;
+  const size_t full = sizeof(T) * ((size_t)n * n + n);
+  if (full <= 200 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_factor<T, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024 + 1024);
+    if (e != cudaSuccess) return e;
+    k_coarse_factor<T, true><<<1, 1024, full, st>>>(g, s, mask, K0, A, dscale, status);
+  } else {
+    k_coarse_factor<T, false><<<1, 1024, sizeof(T) * (size_t)n, st>>>(g, s, mask, K0, A, dscale,
+                                                                      status);
+  }
+  return cudaGetLastError();
+}
+
+// z = D^-1/2 Ainv D^-1/2 r (one CTA, a warp per row).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_apply(int n, const T* __restrict__ Ainv,
+                                                       const T* __restrict__ dsc,
+                                                       const T* __restrict__ r, T* __restrict__ z,
+                                                       const int* skip) {
+  if (skipped(skip)) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* rs = reinterpret_cast<T*>(smem_raw);
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = dsc[q] * r[q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int row = w; row < n; row += nw) {
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) acc += (double)(Ainv[(size_t)row * n + c] * rs[c]);
+    acc = warp_sum(acc);
+    if (lane == 0) z[row] = dsc[row] * (T)acc;
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarse_apply(cudaStream_t st, int n, const T* Ainv, const T* dscale,
+                                const T* r, T* z, const int* skip) {
+  k_coarse_apply<T><<<1, 1024, sizeof(T) * (size_t)n, st>>>(n, Ainv, dscale, r, z, skip);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// CG: x += alpha p, r -= alpha q, rr = r.r; convergence test in the finaliser.
+// With xlo the iterate is the unevaluated pair xhi + xlo (float): the product alpha*p is
+// formed exactly as prod + err (FMA) and added with TwoSum, so the pair keeps ~48 bits.
+// ---------------------------------------------------------------------------------------
+template <typename T, bool PAIRX>
+__global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __restrict__ r,
+                        const T* __restrict__ p, const T* __restrict__ q, double* partials,
+                        unsigned* counter, CgScalars* sc) {
+  if (sc->done) return;
+  const double alpha_d = sc->alpha;
+  const T alpha = (T)alpha_d;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const T pv = p[i];
+    if constexpr (PAIRX) {
+      // exact product prod + perr, then TwoSum(hi, prod); the rn intrinsics keep the
+      // compiler from contracting these steps into FMAs (that would break the error terms)
+      const float prod = __fmul_rn(alpha, pv);
+      const float perr = __fmaf_rn(alpha, pv, -prod);
+      const float a = xhi[i];
+      const float s = __fadd_rn(a, prod);
+      const float bb = __fsub_rn(s, a);
+      const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
+      const float lo = __fadd_rn(__fadd_rn(xlo[i], err), perr);
+      const float hi2 = __fadd_rn(s, lo);
+      xlo[i] = __fsub_rn(lo, __fsub_rn(hi2, s));
+      xhi[i] = hi2;
+    } else {
+      xhi[i] += alpha * pv;
+    }
+    const T rv = r[i] - alpha * q[i];
+    r[i] = rv;
+    acc += (double)(rv * rv);
+  }
+  double v[1] = {acc};
+  grid_reduce<1>(v, partials, counter, [sc](const double* tot) {
+    sc->rr = tot[0];
+    sc->it += 1;
+    if (!isfinite(tot[0])) { sc->status |= DEV_NAN; sc->done = 1; }
+    else if (tot[0] <= sc->tol2 || sc->it >= sc->maxit) sc->done = 1;
+  });
+}
+
+template <typename T>
+cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* p, const T* q,
+                         double* partials, unsigned* counter, CgScalars* sc) {
+  if (xlo) {
+    if constexpr (sizeof(T) == 4) {
+      k_cg_xr<T, true><<<kRedBlocks * 2, kRedThreads, 0, st>>>(n, xhi, xlo, r, p, q, partials,
+                                                               counter, sc);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
+  k_cg_xr<T, false><<<kRedBlocks * 2, kRedThreads, 0, st>>>(n, xhi, nullptr, r, p, q, partials,
+                                                            counter, sc);
+  return cudaGetLastError();
+}
+
+// Device-side loop control of the conditional-while graph: continue while CG has not
+// stopped; the launch counter bounds the loop even if a reduction never reported.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc) {
+  sc->loops += 1;
+  const bool go = !sc->done && sc->loops < sc->maxit + 8;
+  if (!go) sc->done = 1;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, CgScalars* sc) {
+  k_loop_cond<<<1, 1, 0, st>>>(h, sc);
+  return cudaGetLastError();
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void k_cg_p(int n, T* __restrict__ p, const T* __restrict__ z, CgScalars* sc) {
+  if (sc->done) return;
+  const T beta = (T)sc->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+template <typename T>
+cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 8 * 152) blocks = 8 * 152;
+  k_cg_p<T><<<blocks, 256, 0, st>>>(n, p, z, sc);
+  return cudaGetLastError();
+}
+
+// out = a . (b + blo), accumulated in double.
+template <typename TA, typename TB>
+__global__ void k_dot(int n, const TA* __restrict__ a, const TB* __restrict__ b,
+                      const TB* __restrict__ blo, double* partials, unsigned* counter,
+                      double* out) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double bv = (double)b[i];
+    if (blo) bv += (double)blo[i];
+    acc += (double)a[i] * bv;
+  }
+  double v[1] = {acc};
+  grid_reduce<1>(v, partials, counter, [out](const double* tot) { *out = tot[0]; });
+}
+
+template <typename TA, typename TB>
+cudaError_t launch_dot(cudaStream_t st, int n, const TA* a, const TB* b, const TB* blo,
+                       double* partials, unsigned* counter, double* out) {
+  k_dot<TA, TB><<<kRedBlocks, kRedThreads, 0, st>>>(n, a, b, blo, partials, counter, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_mask_copy(Geom g, const T* __restrict__ in, const uint8_t* __restrict__ mask,
+                            T* __restrict__ out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * g.nn; q += gridDim.x * blockDim.x) {
+    const int c = q / g.nn, node = q % g.nn;
+    out[q] = ((mask[node] >> c) & 1u) ? T(0) : in[q];
+  }
+}
+
+template <typename T>
+cudaError_t launch_mask_copy(cudaStream_t st, Geom g, const T* in, const uint8_t* mask, T* out) {
+  int blocks = (3 * g.nn + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_mask_copy<T><<<blocks, 256, 0, st>>>(g, in, mask, out);
+  return cudaGetLastError();
+}
+
+template <typename TO, typename TI>
+__global__ void k_convert(int n, const TI* __restrict__ in, const TI* __restrict__ inlo,
+                          TO* __restrict__ out, const CgScalars* gate) {
+  if (gate != nullptr &&
+      (gate->done || gate->rr_every <= 0 || (gate->it % gate->rr_every) != 0))
+    return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (inlo) out[i] = (TO)((double)in[i] + (double)inlo[i]);
+    else out[i] = (TO)in[i];
+  }
+}
+
+template <typename TO, typename TI>
+cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo, TO* out,
+                           const CgScalars* gate) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_convert<TO, TI><<<blocks, 256, 0, st>>>(n, in, inlo, out, gate);
+  return cudaGetLastError();
+}
+
+#define INST(T)                                                                               \
+  template cudaError_t launch_jacobi<T>(cudaStream_t, Geom, const T*, const uint8_t*, const T*, \
+                                        T, T, T*, T*, double*, unsigned*, CgScalars*, int,     \
+                                        const int*);                                         \
+  template cudaError_t launch_restrict<T>(cudaStream_t, Geom, Geom, const T*, T*,             \
+                                          const uint8_t*, const int*);                       \
+  template cudaError_t launch_prolong_add<T>(cudaStream_t, Geom, Geom, const T*, T*,          \
+                                             const uint8_t*, const int*);                    \
+  template cudaError_t launch_coarsen_s<T>(cudaStream_t, Geom, Geom, const T*, T*);           \
+  template cudaError_t launch_coarse_factor<T>(cudaStream_t, Geom, const T*, const uint8_t*,  \
+                                               const DenseK0<T>&, T*, T*, unsigned*);        \
+  template cudaError_t launch_coarse_apply<T>(cudaStream_t, int, const T*, const T*, const T*, \
+                                              T*, const int*);                               \
+  template cudaError_t launch_cg_xr<T>(cudaStream_t, int, T*, T*, T*, const T*, const T*,     \
+                                       double*, unsigned*, CgScalars*);                      \
+  template cudaError_t launch_cg_p<T>(cudaStream_t, int, T*, const T*, CgScalars*);           \
+  template cudaError_t launch_mask_copy<T>(cudaStream_t, Geom, const T*, const uint8_t*, T*);
+INST(float)
+INST(double)
+#undef INST
+template cudaError_t launch_dot<double, float>(cudaStream_t, int, const double*, const float*,
+                                               const float*, double*, unsigned*, double*);
+template cudaError_t launch_dot<double, double>(cudaStream_t, int, const double*, const double*,
+                                                const double*, double*, unsigned*, double*);
+template cudaError_t launch_dot<float, float>(cudaStream_t, int, const float*, const float*,
+                                              const float*, double*, unsigned*, double*);
+template cudaError_t launch_convert<float, float>(cudaStream_t, int, const float*, const float*,
+                                                  float*, const CgScalars*);
+template cudaError_t launch_convert<double, float>(cudaStream_t, int, const float*, const float*,
+                                                   double*, const CgScalars*);
+template cudaError_t launch_convert<float, double>(cudaStream_t, int, const double*,
+                                                   const double*, float*, const CgScalars*);
+template cudaError_t launch_convert<double, double>(cudaStream_t, int, const double*,
+                                                    const double*, double*, const CgScalars*);
+
+}  // namespace tomo

@@ -1,0 +1,307 @@
+"""Python binding of the tomo C ABI (``include/tomo.h``): argument marshalling only.
+
+Every computation runs in ``libtomo.so`` (CUDA, sm_103a).  Arrays may be torch tensors (on
+the grid's CUDA device or on the CPU) or numpy arrays; their data pointers are handed to the
+library, which stages host arrays itself.  If the library is not built this module raises
+on load: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libtomo.so")
+
+FP64, FP32 = 0, 1
+PRECOND_MG, PRECOND_JACOBI = 0, 1
+STATUS = {0: "TOMO_OK", 1: "TOMO_EINVAL", 2: "TOMO_ENOMEM", 3: "TOMO_ENOCONV", 4: "TOMO_ENAN",
+          5: "TOMO_ETIMEOUT", 6: "TOMO_ECUDA", 7: "TOMO_EBUSY"}
+
+
+class TomoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("h", ctypes.c_double), ("E0", ctypes.c_double), ("Emin", ctypes.c_double),
+                ("nu", ctypes.c_double), ("penal", ctypes.c_double), ("rmin", ctypes.c_double),
+                ("fixed_dof", ctypes.POINTER(ctypes.c_uint8)),
+                ("f", ctypes.POINTER(ctypes.c_double)),
+                ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int32),
+                ("mg_levels", ctypes.c_int32), ("smoother_degree", ctypes.c_int32),
+                ("cheb_ratio", ctypes.c_double), ("rr_every", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("status", ctypes.c_int32), ("mg_levels", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtomo.so is not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    G = ctypes.c_void_p
+    st = ctypes.c_int
+    sig = {
+        "tomo_default_desc": (None, [ctypes.POINTER(GridDesc)]),
+        "tomo_create_grid": (st, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_void_p)]),
+        "tomo_destroy_grid": (st, [G]),
+        "tomo_set_stream": (st, [G, P]),
+        "tomo_filter": (st, [G, P, P, ctypes.c_int]),
+        "tomo_filter_d": (st, [G, P, P, ctypes.c_int]),
+        "tomo_apply_stiffness": (st, [G, P, P, P]),
+        "tomo_apply_stiffness_d": (st, [G, P, P, P]),
+        "tomo_residual": (st, [G, P, P, P, P]),
+        "tomo_residual_d": (st, [G, P, P, P]),
+        "tomo_solve": (st, [G, P, P, ctypes.POINTER(SolveInfo)]),
+        "tomo_solve_d": (st, [G, P, P, ctypes.POINTER(SolveInfo)]),
+        "tomo_sensitivity": (st, [G, P, P, P, P]),
+        "tomo_sensitivity_d": (st, [G, P, P, P, P]),
+        "tomo_oc_step": (st, [G, P, P, P, ctypes.c_double, ctypes.c_double, P, P]),
+        "tomo_oc_step_d": (st, [G, P, P, P, ctypes.c_double, ctypes.c_double, P, P]),
+        "tomo_gradient": (st, [G, P, P, P, P, ctypes.POINTER(SolveInfo)]),
+        "tomo_gradient_d": (st, [G, P, P, P, P, ctypes.POINTER(SolveInfo)]),
+        "tomo_get_displacement": (st, [G, P]),
+        "tomo_get_displacement_d": (st, [G, P]),
+        "tomo_get_counts": (st, [G, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+        "tomo_get_launch_count": (st, [G, ctypes.POINTER(ctypes.c_int64)]),
+        "tomo_profile_enable": (st, [G, ctypes.c_int]),
+        "tomo_profile_read": (st, [G, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
+        "tomo_last_error": (ctypes.c_char_p, [G]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return ["tomo_default_desc", "tomo_create_grid", "tomo_destroy_grid", "tomo_set_stream",
+            "tomo_filter", "tomo_filter_d", "tomo_apply_stiffness", "tomo_apply_stiffness_d",
+            "tomo_residual", "tomo_residual_d", "tomo_solve", "tomo_solve_d", "tomo_sensitivity", "tomo_sensitivity_d",
+            "tomo_oc_step", "tomo_oc_step_d", "tomo_gradient", "tomo_gradient_d",
+            "tomo_get_displacement", "tomo_get_displacement_d", "tomo_get_counts",
+            "tomo_get_launch_count", "tomo_profile_enable", "tomo_profile_read",
+            "tomo_last_error"]
+
+
+def _ptr(a, dtype, count, name):
+    """Data pointer of a torch tensor or numpy array after type/size checks."""
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = torch.float32 if dtype == np.float32 else torch.float64
+            if a.dtype != want:
+                raise TypeError(f"{name}: expected {want}, got {a.dtype}")
+            if not a.is_contiguous():
+                raise ValueError(f"{name}: tensor must be contiguous")
+            if a.numel() != count:
+                raise ValueError(f"{name}: expected {count} values, got {a.numel()}")
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype:
+            raise TypeError(f"{name}: expected {np.dtype(dtype)}, got {a.dtype}")
+        if not a.flags.c_contiguous:
+            raise ValueError(f"{name}: array must be C-contiguous")
+        if a.size != count:
+            raise ValueError(f"{name}: expected {count} values, got {a.size}")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"{name}: expected a torch tensor or numpy array")
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+@dataclass
+class Info:
+    iters: int
+    rel_res: float
+    status: int
+    mg_levels: int
+
+
+class Grid:
+    """A tomo grid handle (``tomo_create_grid``).  Float entry points for FP32 grids,
+    double for FP64 grids; the same Python method serves both."""
+
+    def __init__(self, nx, ny, nz, fixed, f, *, h=1.0, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0,
+                 rmin=1.5, precision=FP32, precond=PRECOND_MG, rtol=1e-6, maxit=2000,
+                 mg_levels=0, smoother_degree=2, cheb_ratio=10.0, rr_every=50, stream=None):
+        L = lib()
+        d = GridDesc()
+        L.tomo_default_desc(ctypes.byref(d))
+        nn = (nx + 1) * (ny + 1) * (nz + 1)
+        self._fixed = np.ascontiguousarray(np.asarray(fixed).astype(np.uint8).ravel())
+        self._f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).ravel())
+        if self._fixed.size != 3 * nn or self._f.size != 3 * nn:
+            raise ValueError(f"fixed and f must have 3*N_n = {3 * nn} entries")
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.h, d.E0, d.Emin, d.nu, d.penal, d.rmin = h, E0, Emin, nu, penal, rmin
+        d.fixed_dof = self._fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        d.f = self._f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.precision, d.precond = precision, precond
+        d.rtol, d.maxit, d.mg_levels = rtol, maxit, mg_levels
+        d.smoother_degree, d.cheb_ratio, d.rr_every = smoother_degree, cheb_ratio, rr_every
+        d.stream = stream if stream is not None else _current_stream()
+        h_out = ctypes.c_void_p()
+        st = L.tomo_create_grid(ctypes.byref(d), ctypes.byref(h_out))
+        if st != 0:
+            raise TomoError(st, L.tomo_last_error(None).decode())
+        self._h = h_out
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n_el = nx * ny * nz
+        self.n_nodes = nn
+        self.precision = precision
+        self.dtype = np.float64 if precision == FP64 else np.float32
+        self._sfx = "_d" if precision == FP64 else ""
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        d = p.dims
+        return cls(d.nx, d.ny, d.nz, p.fixed, p.f, h=p.h, E0=p.E0, Emin=p.Emin, nu=p.nu,
+                   penal=p.penal, rmin=p.rmin, **kw)
+
+    # -- helpers --------------------------------------------------------------------------
+    def _call(self, name, *args):
+        st = getattr(lib(), name + self._sfx)(self._h, *args)
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def _e(self, a, name):
+        return _ptr(a, self.dtype, self.n_el, name)
+
+    def _n(self, a, name):
+        return _ptr(a, self.dtype, 3 * self.n_nodes, name)
+
+    # -- entry points ---------------------------------------------------------------------
+    def set_stream(self, stream):
+        st = lib().tomo_set_stream(self._h, ctypes.c_void_p(stream))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def filter(self, x, out, transpose=False):
+        self._call("tomo_filter", self._e(x, "in"), self._e(out, "out"), int(bool(transpose)))
+
+    def apply_stiffness(self, rho, x, y):
+        self._call("tomo_apply_stiffness", self._e(rho, "rho"), self._n(x, "x"), self._n(y, "y"))
+
+    def residual(self, rho, u, r, u_lo=None):
+        if self.precision == FP64:
+            if u_lo is not None:
+                raise ValueError("u_lo is for FP32 grids")
+            self._call("tomo_residual", self._e(rho, "rho"), self._n(u, "u"), self._n(r, "r"))
+        else:
+            self._call("tomo_residual", self._e(rho, "rho"), self._n(u, "u"),
+                       self._n(u_lo, "u_lo") if u_lo is not None else None, self._n(r, "r"))
+
+    def solve(self, rho, u) -> Info:
+        info = SolveInfo()
+        name = "tomo_solve"
+        st = getattr(lib(), name + self._sfx)(self._h, self._e(rho, "rho"), self._n(u, "u"),
+                                              ctypes.byref(info))
+        if st not in (0,):
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+        return Info(info.iters, info.rel_res, info.status, info.mg_levels)
+
+    def sensitivity(self, rho, u, dc=None) -> float:
+        c = ctypes.c_double()
+        self._call("tomo_sensitivity", self._e(rho, "rho"), self._n(u, "u"), ctypes.byref(c),
+                   self._e(dc, "dc") if dc is not None else None)
+        return c.value
+
+    def oc_step(self, z, dcdz, dvdz, volfrac, move, z_new) -> float:
+        ch = ctypes.c_double()
+        self._call("tomo_oc_step", self._e(z, "z"), self._e(dcdz, "dcdz"), self._e(dvdz, "dvdz"),
+                   ctypes.c_double(volfrac), ctypes.c_double(move), self._e(z_new, "z_new"),
+                   ctypes.byref(ch))
+        return ch.value
+
+    def gradient(self, z, dcdz, dvdz=None):
+        """Returns (compliance, Info)."""
+        c = ctypes.c_double()
+        info = SolveInfo()
+        self._call("tomo_gradient", self._e(z, "z"), ctypes.byref(c), self._e(dcdz, "dcdz"),
+                   self._e(dvdz, "dvdz") if dvdz is not None else None, ctypes.byref(info))
+        return c.value, Info(info.iters, info.rel_res, info.status, info.mg_levels)
+
+    def get_displacement(self, u):
+        self._call("tomo_get_displacement", self._n(u, "u"))
+
+    def counts(self):
+        ne, nn, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        st = lib().tomo_get_counts(self._h, ctypes.byref(ne), ctypes.byref(nn), ctypes.byref(nl))
+        if st != 0:
+            raise TomoError(st, "tomo_get_counts")
+        return ne.value, nn.value, nl.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        st = lib().tomo_get_launch_count(self._h, ctypes.byref(n))
+        if st != 0:
+            raise TomoError(st, "tomo_get_launch_count")
+        return n.value
+
+    def profile_enable(self, on=True):
+        lib().tomo_profile_enable(self._h, int(bool(on)))
+
+    def profile_read(self):
+        n, ms, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        st = lib().tomo_profile_read(self._h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+        return n.value, ms.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tomo_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
