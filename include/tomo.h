@@ -159,6 +159,27 @@ tomo_status tomo_oc_step_d(tomo_grid* grid, const double* z, const double* dcdz,
                            const double* dvdz, double volfrac, double move, double* z_new,
                            double* change);
 
+/* tomo_oc_step without any allocation, for callers that may not allocate device memory
+ * (code running while a stream is captured into a CUDA graph, runtimes that own all device
+ * memory through their own pool, loops that cannot afford an allocation's implicit
+ * synchronisation).  The paper has no counterpart: this is a deployment variant of
+ * tomo_oc_step for FP32 data, computing the same update with the same multiplier search.
+ *   n_el:   number of design variables, 1 <= n_el <= 4,194,304 (larger: TOMO_EINVAL);
+ *   h:      element edge (V_max = volfrac * n_el * h^3);
+ *   z, dcdz, dvdz, z_new: DEVICE float arrays of n_el entries (host pointers: TOMO_EINVAL);
+ *   change: DEVICE double receiving max |z_new - z|, or NULL;
+ *   stream: cudaStream_t the work is queued on (NULL = legacy default); nothing waits.
+ * Scratch: a static device array of about 0.5 MiB inside this library, held by every GPU
+ * that loads it until the process exits.  The first call on a device resolves that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU
+ * (different streams, or several devices' worth of work on one) race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or other allocating call is made.
+ * Errors: TOMO_EINVAL / TOMO_ECUDA, described by tomo_last_error(NULL). */
+tomo_status tomo_oc_step_noalloc(int64_t n_el, double h, const float* z, const float* dcdz,
+                                 const float* dvdz, double volfrac, double move, float* z_new,
+                                 double* change, void* stream);
+
 /* One exact-gradient evaluation (Algorithm 1, exact branch; Eq. 4-5): rho = P z,
  * E = Emin + rho^p (E0 - Emin), solve K u = f from a zero start, *compliance = f^T u,
  * dcdz = P^T dc/drho, dvdz = P^T v.  z, dcdz, dvdz: N_el.  dvdz may be NULL (then it is not

@@ -71,6 +71,8 @@ def _load():
         "tomo_sensitivity_d": (st, [G, P, P, P, P]),
         "tomo_oc_step": (st, [G, P, P, P, ctypes.c_double, ctypes.c_double, P, P]),
         "tomo_oc_step_d": (st, [G, P, P, P, ctypes.c_double, ctypes.c_double, P, P]),
+        "tomo_oc_step_noalloc": (st, [ctypes.c_int64, ctypes.c_double, P, P, P, ctypes.c_double,
+                                      ctypes.c_double, P, P, P]),
         "tomo_gradient": (st, [G, P, P, P, P, ctypes.POINTER(SolveInfo)]),
         "tomo_gradient_d": (st, [G, P, P, P, P, ctypes.POINTER(SolveInfo)]),
         "tomo_get_displacement": (st, [G, P]),
@@ -106,7 +108,8 @@ def exported_symbols():
     return ["tomo_default_desc", "tomo_create_grid", "tomo_destroy_grid", "tomo_set_stream",
             "tomo_filter", "tomo_filter_d", "tomo_apply_stiffness", "tomo_apply_stiffness_d",
             "tomo_residual", "tomo_residual_d", "tomo_solve", "tomo_solve_d", "tomo_sensitivity", "tomo_sensitivity_d",
-            "tomo_oc_step", "tomo_oc_step_d", "tomo_gradient", "tomo_gradient_d",
+            "tomo_oc_step", "tomo_oc_step_d", "tomo_oc_step_noalloc", "tomo_gradient",
+            "tomo_gradient_d",
             "tomo_get_displacement", "tomo_get_displacement_d", "tomo_get_counts",
             "tomo_get_launch_count", "tomo_profile_enable", "tomo_profile_read",
             "tomo_last_error"]
@@ -148,6 +151,21 @@ def _current_stream():
     except ImportError:
         pass
     return ctypes.c_void_p(0)
+
+
+def oc_step_noalloc(n_el, h, z, dcdz, dvdz, volfrac, move, z_new, change=None, stream=None):
+    """tomo_oc_step_noalloc: FP32 device arrays, no grid handle, no allocation."""
+    args = [_ptr(a, np.float32, n_el, nm) for a, nm in
+            ((z, "z"), (dcdz, "dcdz"), (dvdz, "dvdz"))]
+    zn = _ptr(z_new, np.float32, n_el, "z_new")
+    ch = None
+    if change is not None:
+        ch = _ptr(change, np.float64, 1, "change")
+    st = lib().tomo_oc_step_noalloc(ctypes.c_int64(n_el), ctypes.c_double(h), *args,
+                                    ctypes.c_double(volfrac), ctypes.c_double(move), zn, ch,
+                                    stream if stream is not None else _current_stream())
+    if st != 0:
+        raise TomoError(st, lib().tomo_last_error(None).decode())
 
 
 @dataclass
