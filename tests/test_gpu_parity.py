@@ -189,8 +189,10 @@ def test_residual_of_float_pair_matches_oracle(kind):
     u, _, _ = m.solve(E, "direct")
     uhi = u.astype(np.float32)
     ulo = (u - uhi.astype(np.float64)).astype(np.float32)
-    fn = np.linalg.norm(p.f)
     ref_hi = np.where(m.fixed, 0.0, p.f - m.apply(E, uhi.astype(np.float64)))
+    # size of the terms the product sums: || |K| |u| ||
+    scale = np.linalg.norm(np.where(m.fixed, 0.0, fem.apply_elementwise(
+        d.nx, d.ny, d.nz, E, p.h, np.abs(m.K0), np.abs(uhi.astype(np.float64)))))
     with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
         r = torch.empty(d.n_dof, dtype=torch.float32, device=DEV)
         g.residual(T(rho, tomo.FP32), T(uhi, tomo.FP32), r, u_lo=T(ulo, tomo.FP32))
@@ -200,11 +202,11 @@ def test_residual_of_float_pair_matches_oracle(kind):
         torch.cuda.synchronize()
         r_hi = H(r)
     # residual of u_hi alone: the oracle's FP64 residual of u_hi up to the FP32 rounding of
-    # the product (a few 1e-6 of ||f||)
-    assert np.linalg.norm(r_hi - ref_hi) <= 2e-5 * fn
-    # pair: the exact solution's residual is 0, so only that rounding remains; it is well
-    # below the residual caused by rounding u itself to float
-    assert np.linalg.norm(r_pair) <= 2e-5 * fn
+    # the product, which the differences-first transform keeps far below eps * |K||u|
+    assert np.linalg.norm(r_hi - ref_hi) <= 1e-9 * scale
+    # pair: the exact solution's residual is 0, so only that rounding remains, well below
+    # the residual caused by rounding u itself to float
+    assert np.linalg.norm(r_pair) <= 1e-9 * scale
     assert np.linalg.norm(r_pair) <= 0.2 * np.linalg.norm(ref_hi)
 
 
