@@ -85,8 +85,11 @@ typedef struct {
   double rtol;          /* CG stop: ||r|| <= rtol ||f||; <= 0 selects 1e-6 */
   int32_t maxit;        /* CG iteration cap; <= 0 selects 2000 */
   int32_t mg_levels;    /* multigrid levels; <= 0 coarsens until the coarsest grid is small */
-  int32_t smoother_degree; /* Chebyshev degree per pre/post smoothing; <= 0 selects 2 */
-  double cheb_ratio;    /* smoothing interval [lmax/ratio, lmax] of D^-1 K; <= 1 selects 10 */
+  int32_t smoother_degree; /* Chebyshev degree per pre/post smoothing, fine level; <= 0: 2 */
+  int32_t coarse_degree;   /* the same on the coarser levels; <= 0: smoother_degree */
+  double cheb_ratio;    /* smoothing interval [lmax/ratio, lmax] of D^-1 K; <= 1 selects 20 */
+  double cheb_lmax;     /* lmax; <= 0 selects the element bound max eig(diag(K0)^-1 K0), which
+                           bounds eig(D^-1 K) on any grid (5.32 for nu = 0.3) */
   int32_t rr_every;     /* residual replacement r = f - K x (evaluated in FP64) every rr_every
                            iterations; 0 selects 50, < 0 off */
   void* stream;         /* cudaStream_t for all work on this grid; NULL = legacy default */
@@ -202,12 +205,23 @@ tomo_status tomo_get_counts(const tomo_grid* grid, int64_t* n_el, int64_t* n_nod
  * loop counted once per executed iteration). */
 tomo_status tomo_get_launch_count(const tomo_grid* grid, int64_t* launches);
 
-/* Kernel timing for roofline reports.  When enabled, the library brackets every launch
- * of the fine-level matrix-free kernels (products and smoother steps) with CUDA events
- * on the grid's stream and accumulates their count, total milliseconds and algorithmic
- * DRAM bytes (inputs read once plus outputs written once).  tomo_profile_read waits for
- * the stream, returns the totals since the last reset and resets them. */
+/* Timing for roofline and phase reports.  enable bit 0: the library brackets every launch
+ * of the fine-level matrix-free kernels (products and smoother steps) with CUDA events on
+ * the grid's stream and accumulates their count, total milliseconds and algorithmic DRAM
+ * bytes (inputs read once plus outputs written once); the CG loop is then issued from the
+ * host (same kernels, same order) because event records cannot sit inside the device-side
+ * loop.  tomo_profile_read waits for the stream, returns the totals since the last reset
+ * and resets them.  enable bit 1: events at phase boundaries only (device-side loop kept);
+ * tomo_profile_phases returns the accumulated milliseconds of ms[0] filter + material,
+ * ms[1] multigrid level setup, ms[2] CG solve, ms[3] compliance + sensitivity, ms[4] filter
+ * adjoints, ms[6] OC step (ms[5] unused) and the number of gradient calls, then resets. */
 tomo_status tomo_profile_enable(tomo_grid* grid, int enable);
+tomo_status tomo_profile_phases(tomo_grid* grid, double* ms, int64_t* calls);
+/* With enable bit 0 set, every kernel of the multigrid preconditioner is also timed and
+ * binned by level: after tomo_profile_read, ms[l] / launches[l] (l < max_levels) hold the
+ * device time and launch count of level l (level 0: the fine-level products only), then
+ * reset. */
+tomo_status tomo_profile_levels(tomo_grid* grid, double* ms, int64_t* launches, int max_levels);
 tomo_status tomo_profile_read(tomo_grid* grid, int64_t* launches, double* total_ms,
                               double* algorithmic_bytes);
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -164,12 +165,51 @@ tomo_status prof_begin(tomo_grid* G, cudaEvent_t* e0) {
   return TOMO_OK;
 }
 
-tomo_status prof_end(tomo_grid* G, double bytes) {
+tomo_status prof_end(tomo_grid* G, double bytes, int tag = -1) {
   if (!G->prof) return TOMO_OK;
   CK(cudaEventRecord(G->ev[G->ev_used + 1], G->stream));
   G->ev_used += 2;
-  G->prof_launches += 1;
-  G->prof_bytes += bytes;
+  if ((int)G->ev_tag.size() < (int)G->ev_used / 2) G->ev_tag.resize(G->ev_used / 2);
+  G->ev_tag[G->ev_used / 2 - 1] = tag;
+  if (tag < 0) {
+    G->prof_launches += 1;
+    G->prof_bytes += bytes;
+  }
+  return TOMO_OK;
+}
+
+// Level timing of one launch (kernel-timing mode): tag = level + 1.
+struct LevelTimer {
+  tomo_grid* G;
+  int level;
+  bool on;
+  cudaEvent_t e0;
+  LevelTimer(tomo_grid* g, int l) : G(g), level(l), on(g->prof) {
+    if (on && prof_begin(G, &e0) != TOMO_OK) on = false;
+  }
+  ~LevelTimer() {
+    if (on) prof_end(G, 0.0, level + 1);
+  }
+};
+
+// Phase marks: 0 start, 1 filter+material, 2 level setup, 3 PCG, 4 sensitivity, 5 filter
+// adjoints (gradient); 6 start, 7 end (OC step).
+tomo_status pmark(tomo_grid* G, int i) {
+  if (!G->phase_prof) return TOMO_OK;
+  if (!G->phase_ev[i]) CK(cudaEventCreate(&G->phase_ev[i]));
+  CK(cudaEventRecord(G->phase_ev[i], G->stream));
+  return TOMO_OK;
+}
+
+tomo_status pcollect(tomo_grid* G, int first, int last) {
+  if (!G->phase_prof) return TOMO_OK;
+  CK(cudaEventSynchronize(G->phase_ev[last]));
+  for (int i = first; i < last; ++i) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, G->phase_ev[i], G->phase_ev[i + 1]));
+    G->phase_ms[i] += ms;
+  }
+  G->phase_calls += 1;
   return TOMO_OK;
 }
 
@@ -178,21 +218,57 @@ tomo_status march(tomo_grid* G, int level, int mode, MarchArgs<T> a, const T* s_
   const bool prof = G->prof && level == 0;
   cudaEvent_t e0;
   if (prof) TRY(prof_begin(G, &e0));
+  std::unique_ptr<LevelTimer> lt;  // coarse levels: timed and binned by level
+  if (G->prof && level > 0) lt.reset(new LevelTimer(G, level));
   a.g = G->L[level].g;
   a.s = s_override ? s_override : (const T*)G->L[level].s;
   a.mask = G->L[level].mask;
   a.partials = G->partials;
   a.counter = G->counter;
   int ctas = 0;
-  CK(launch_march<T>(G->stream, mode, a, elem_const<T>(G), G->num_sms, &ctas));
+  bool fused_kernel = false;  // k_march2: the FP32 product/smoother the roofline reports
+  if constexpr (sizeof(T) == 4) {
+    if (a.xlo == nullptr) {
+      fused_kernel = true;
+      March2Args m{};
+      m.g = a.g;
+      m.s = a.s;
+      m.mask = a.mask;
+      m.x = a.x;
+      m.b = a.b;
+      m.xprev = a.xprev;
+      m.y = a.y;
+      m.c1 = a.c1;
+      m.c2 = a.c2;
+      m.partials = a.partials;
+      m.counter = a.counter;
+      m.sc = a.sc;
+      m.dot_kind = a.dot_kind;
+      m.skip = a.skip;
+      m.xprev_zero = a.xprev_zero;
+      if (a.gate != nullptr) return fail(G, TOMO_EINVAL, "gated product needs the FP64 path");
+      March2Const k{(float)G->kinds.a0, (float)G->kinds.b0, (float)G->kinds.a7,
+                    (float)G->kinds.b7, (float)G->kinds.ta, (float)G->kinds.tb,
+                    (float)G->kinds.ua, (float)G->kinds.ud, (float)G->k0diag};
+      CK(launch_march2(G->stream, mode, m, k, G->num_sms));
+    } else {
+      CK(launch_march<T>(G->stream, mode, a, elem_const<T>(G), G->num_sms, &ctas));
+    }
+  } else {
+    CK(launch_march<T>(G->stream, mode, a, elem_const<T>(G), G->num_sms, &ctas));
+  }
   G->launches += 1;
-  if (prof) {
+  if (prof && !fused_kernel && G->d.precision == TOMO_FP32) {
+    // Level-0 launches of the generic kernel on the mixed path (FP64 residual replacement,
+    // float-pair products) count toward level 0 but not toward the reported kernel.
+    TRY(prof_end(G, 0.0, 1));
+  } else if (prof) {
     const double nv = 3.0 * a.g.nn * sizeof(T);
     double bytes = nv + a.g.nel * (double)sizeof(T) + a.g.nn;  // x, s, mask
     if (a.xlo) bytes += nv;
     if (mode == M_APPLY) bytes += nv;                  // y
     else if (mode == M_RESID) bytes += 2 * nv;         // b, y
-    else bytes += (a.c1 != T(0) ? 3 : 2) * nv;         // b, (xprev), x_new
+    else bytes += ((a.c1 != T(0) && !a.xprev_zero) ? 3 : 2) * nv;  // b, (xprev), x_new
     TRY(prof_end(G, bytes));
   }
   return TOMO_OK;
@@ -236,11 +312,15 @@ Cheb cheb(const tomo_grid* G) {
 
 // Chebyshev smoothing of K_l x = b on [lam_hi/ratio, lam_hi] of D^-1 K, degree K steps.
 // zero_start: x_0 = 0 (first step needs no product).  On return *X holds the result.
+int level_degree(const tomo_grid* G, int l) {
+  return l == 0 ? G->d.smoother_degree : G->d.coarse_degree;
+}
+
 template <typename T>
 tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_start, bool dot,
-                   const int* skip) {
+                   const int* skip, bool first_done = false) {
   const Cheb cb = cheb(G);
-  const int K = G->d.smoother_degree;
+  const int K = level_degree(G, l);
   const T k0d = (T)G->k0diag;
   auto& Lv = G->L[l];
   double rho_prev = 1.0 / cb.sigma;
@@ -258,10 +338,13 @@ tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_star
     }
     const int dk = (dot && last) ? 2 : 0;
     if (s == 0 && zero_start) {
-      CK(launch_jacobi<T>(G->stream, Lv.g, (const T*)Lv.s, Lv.mask, b, (T)c2, k0d, *X, *Y,
-                          G->partials, G->counter, G->sc, dk, skip));
-      G->launches += 1;
-      // X = x1, Y = x0 = 0: the recurrence continues with (x = X, xprev = Y)
+      if (!first_done) {  // (else the restriction that produced b already wrote X)
+        LevelTimer lt(G, l);
+        CK(launch_jacobi<T>(G->stream, Lv.g, (const T*)Lv.s, Lv.mask, b, (T)c2, k0d, *X,
+                            nullptr, G->partials, G->counter, G->sc, dk, skip));
+        G->launches += 1;
+      }
+      // X = x1; x0 = 0 is implicit: the next step is told not to read Y
       continue;
     }
     MarchArgs<T> a{};
@@ -273,6 +356,7 @@ tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_star
     a.sc = G->sc;
     a.dot_kind = dk;
     a.skip = skip;
+    a.xprev_zero = (s == 1 && zero_start) ? 1 : 0;
     TRY(march<T>(G, l, M_CHEB, a));
     std::swap(*X, *Y);
   }
@@ -281,10 +365,12 @@ tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_star
 
 // z = V-cycle(b) on level l; *out receives the buffer holding z.
 template <typename T>
-tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int* skip) {
+tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int* skip,
+                   bool first_done = false) {
   auto& Lv = G->L[l];
   const int nl = (int)G->L.size();
   if (l == nl - 1) {
+    LevelTimer lt(G, l);
     CK(launch_coarse_apply<T>(G->stream, G->coarse_n, (const T*)G->coarseA,
                               (const T*)G->coarseD, b, (T*)Lv.x, skip));
     G->launches += 1;
@@ -293,7 +379,7 @@ tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int
   }
   T* X = (T*)Lv.x;
   T* Y = (T*)Lv.xp;
-  TRY(smooth<T>(G, l, b, &X, &Y, true, false, skip));
+  TRY(smooth<T>(G, l, b, &X, &Y, true, false, skip, first_done));
   {
     MarchArgs<T> a{};
     a.x = X;
@@ -303,11 +389,22 @@ tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int
     TRY(march<T>(G, l, M_RESID, a));
   }
   auto& Lc = G->L[l + 1];
-  CK(launch_restrict<T>(G->stream, Lv.g, Lc.g, (const T*)Lv.t, (T*)Lc.b, Lc.mask, skip));
+  // the first Chebyshev step of the next level (from zero) is pointwise: fuse it here
+  const bool fuse = (l + 1 < nl - 1);
+  const Cheb cb = cheb(G);
+  {
+  LevelTimer lt(G, l);
+  CK(launch_restrict<T>(G->stream, Lv.g, Lc.g, (const T*)Lv.t, (T*)Lc.b, Lc.mask, skip,
+                        fuse ? (T*)Lc.x : nullptr, (const T*)Lc.s, (T)(1.0 / cb.theta),
+                        (T)G->k0diag));
   G->launches += 1;
+  }
   T* zc = nullptr;
-  TRY(vcycle<T>(G, l + 1, (const T*)Lc.b, &zc, false, skip));
-  CK(launch_prolong_add<T>(G->stream, Lv.g, Lc.g, zc, X, Lv.mask, skip));
+  TRY(vcycle<T>(G, l + 1, (const T*)Lc.b, &zc, false, skip, fuse));
+  {
+    LevelTimer lt(G, l);
+    CK(launch_prolong_add<T>(G->stream, Lv.g, Lc.g, zc, X, Lv.mask, skip));
+  }
   G->launches += 1;
   TRY(smooth<T>(G, l, b, &X, &Y, false, dot, skip));
   *out = X;
@@ -489,8 +586,15 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
   TRY(precond<T>(G, r, &z));
   CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
   G->launches += 1;
+  if (G->use_graph && !G->prof && !G->loop_exec) {
+    if (build_loop_graph<T>(G) != TOMO_OK) {
+      // the device-side loop could not be captured: issue the iterations from the host
+      cudaGetLastError();
+      G->use_graph = false;
+      G->err.clear();
+    }
+  }
   if (G->use_graph && !G->prof) {
-    if (!G->loop_exec) TRY(build_loop_graph<T>(G));
     CK(cudaGraphLaunch(G->loop_exec, G->stream));
     CK(cudaMemcpyAsync(G->h_sc, G->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, G->stream));
     TRY(sync(G));
@@ -736,10 +840,18 @@ tomo_status do_oc(tomo_grid* G, const T* z, const T* dcdz, const T* dvdz, double
   TRY(stage_out(G, znew, be, 5, &dzn, &h4));
   if (dzn == dz || dzn == ddc || dzn == dw) return fail(G, TOMO_EINVAL, "z_new overlaps an input");
   const double vmax = volfrac * (double)G->g.nel * G->d.h * G->d.h * G->d.h;
+  TRY(pmark(G, 6));
   CK(launch_oc<T>(G->stream, G->g.nel, (const T*)dz, (const T*)ddc, (const T*)dw, vmax, move,
                   (T*)dzn, G->partials, G->counter, G->dscal + 2, G->dscal + 1,
                   oc_max_blocks(G->g.nel)));
   G->launches += (sizeof(T) == 8) ? 11 : 10;
+  TRY(pmark(G, 7));
+  if (G->phase_prof) {
+    CK(cudaEventSynchronize(G->phase_ev[7]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, G->phase_ev[6], G->phase_ev[7]));
+    G->phase_ms[6] += ms;
+  }
   TRY(copy_back(G, znew, dzn, be, h4));
   TRY(write_scalar(G, change, G->dscal + 1));
   if (h1 || h2 || h3 || h4) TRY(sync(G));
@@ -759,25 +871,32 @@ tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T
   TRY(stage_out(G, dcdz, be, 1, &ddc, &h2));
   if (dvdz) TRY(stage_out(G, dvdz, be, 4, &ddv, &h3));
   T* rho = (T*)G->rho;
+  TRY(pmark(G, 0));
   // S1: rho = P z, s = h (Emin + rho^p (E0 - Emin))
   CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps, (const T*)dz,
                       (const T*)G->Hs, rho, 0, 1, (T)d.E0, (T)d.Emin, (T)d.penal, (T)d.h,
                       (T*)G->L[0].s));
   G->launches += 1;
+  TRY(pmark(G, 1));
   // S2: coarse moduli, coarsest factorisation
   TRY(setup_levels<T>(G));
+  TRY(pmark(G, 2));
   // S3-S5: PCG from a zero start
   tomo_status st = pcg<T>(G, false, info);
   if (st != TOMO_OK) return st;
+  TRY(pmark(G, 3));
   // S6: compliance and dc/drho
   TRY(compliance_and_sens<T>(G, rho, (const T*)G->xhi, (const T*)x_lo<T>(G), compliance,
                              (T*)G->dcp));
+  TRY(pmark(G, 4));
   // S7: dc/dz = P^T dc/drho, dV/dz = P^T v
   CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
                       (const T*)G->dcp, (const T*)G->Hs, (T*)ddc, 1, 0, T(0), T(0), T(0), T(0),
                       nullptr));
   G->launches += 1;
   if (ddv) TRY(volume_gradient<T>(G, (T*)ddv));
+  TRY(pmark(G, 5));
+  TRY(pcollect(G, 0, 5));
   TRY(copy_back(G, dcdz, ddc, be, h2));
   if (dvdz) TRY(copy_back(G, dvdz, ddv, be, h3));
   TRY(write_scalar(G, compliance, G->dscal));
@@ -891,6 +1010,8 @@ void free_grid(tomo_grid* G) {
   if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
   if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
   for (auto e : G->ev) cudaEventDestroy(e);
+  for (auto e : G->phase_ev)
+    if (e) cudaEventDestroy(e);
   delete G;
 }
 
@@ -1040,7 +1161,9 @@ void tomo_default_desc(tomo_grid_desc* d) {
   d->maxit = 2000;
   d->mg_levels = 0;
   d->smoother_degree = 2;
-  d->cheb_ratio = 10.0;
+  d->coarse_degree = 0;
+  d->cheb_ratio = 20.0;
+  d->cheb_lmax = 0.0;
   d->rr_every = 50;
   d->stream = nullptr;
 }
@@ -1074,8 +1197,9 @@ tomo_status tomo_create_grid(const tomo_grid_desc* desc, tomo_grid** out) {
   if (G->d.rtol <= 0.0) G->d.rtol = 1e-6;
   if (G->d.maxit <= 0) G->d.maxit = 2000;
   if (G->d.smoother_degree <= 0) G->d.smoother_degree = 2;
+  if (G->d.coarse_degree <= 0) G->d.coarse_degree = G->d.smoother_degree;
   if (G->d.rr_every == 0) G->d.rr_every = 50;
-  G->cheb_ratio = G->d.cheb_ratio > 1.0 ? G->d.cheb_ratio : 10.0;
+  G->cheb_ratio = G->d.cheb_ratio > 1.0 ? G->d.cheb_ratio : 20.0;
   G->prec = d.precision;
   G->tsize = d.precision == TOMO_FP64 ? 8 : 4;
   G->stream = (cudaStream_t)d.stream;
@@ -1096,7 +1220,11 @@ tomo_status tomo_create_grid(const tomo_grid_desc* desc, tomo_grid** out) {
     delete G;
     return fail(nullptr, TOMO_EINVAL, "element stiffness is not cube-symmetric");
   }
-  G->lam_hi = lam_max_element(G->K0);
+  if (!block_kinds(G->blk, &G->kinds)) {
+    delete G;
+    return fail(nullptr, TOMO_EINVAL, "element stiffness blocks are not of the isotropic kinds");
+  }
+  G->lam_hi = G->d.cheb_lmax > 0.0 ? G->d.cheb_lmax : lam_max_element(G->K0);
   tomo_status st = G->prec == TOMO_FP64 ? create_impl<double>(G) : create_impl<float>(G);
   if (st != TOMO_OK) {
     g_create_err = G->err;
@@ -1218,7 +1346,30 @@ tomo_status tomo_get_launch_count(const tomo_grid* G, int64_t* launches) {
 
 tomo_status tomo_profile_enable(tomo_grid* G, int enable) {
   if (!G) return TOMO_EINVAL;
-  G->prof = enable != 0;
+  G->prof = (enable & 1) != 0;
+  G->phase_prof = (enable & 2) != 0;
+  return TOMO_OK;
+}
+
+tomo_status tomo_profile_levels(tomo_grid* G, double* ms, int64_t* launches, int max_levels) {
+  if (!G || !ms || max_levels < 1) return TOMO_EINVAL;
+  for (int l = 0; l < max_levels && l < 16; ++l) {
+    ms[l] = G->level_ms[l];
+    if (launches) launches[l] = G->level_n[l];
+    G->level_ms[l] = 0.0;
+    G->level_n[l] = 0;
+  }
+  return TOMO_OK;
+}
+
+tomo_status tomo_profile_phases(tomo_grid* G, double* ms, int64_t* calls) {
+  if (!G || !ms) return TOMO_EINVAL;
+  for (int i = 0; i < 7; ++i) {
+    ms[i] = G->phase_ms[i];
+    G->phase_ms[i] = 0.0;
+  }
+  if (calls) *calls = G->phase_calls;
+  G->phase_calls = 0;
   return TOMO_OK;
 }
 
@@ -1232,7 +1383,15 @@ tomo_status tomo_profile_read(tomo_grid* G, int64_t* launches, double* total_ms,
   for (size_t q = 0; q + 1 < G->ev_used; q += 2) {
     float t = 0.0f;
     CK(cudaEventElapsedTime(&t, G->ev[q], G->ev[q + 1]));
-    ms += t;
+    const int tag = (q / 2 < G->ev_tag.size()) ? G->ev_tag[q / 2] : -1;
+    if (tag < 0) {
+      ms += t;
+      G->level_ms[0] += t;
+      G->level_n[0] += 1;
+    } else if (tag - 1 < 16) {
+      G->level_ms[tag - 1] += t;
+      G->level_n[tag - 1] += 1;
+    }
   }
   if (launches) *launches = G->prof_launches;
   if (total_ms) *total_ms = ms;

@@ -79,10 +79,38 @@ struct CgScalars {
 
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
+// Programmatic dependent launch: every kernel of the library is launched with programmatic
+// stream serialisation, and starts with PDL_ENTER(): it waits for the grids it depends on
+// to complete (griddepcontrol.wait, before touching any memory) and at once lets its own
+// dependents be scheduled (griddepcontrol.launch_dependents), so that the launch latency of
+// the next kernel overlaps this one.  A dependent still cannot read anything until this
+// grid has completed and its writes are visible.
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ------------------------------------------------------------------------------------
 // Device helpers
 // ------------------------------------------------------------------------------------
 #ifdef __CUDACC__
+
+#define PDL_ENTER()                                            \
+  do {                                                         \
+    asm volatile("griddepcontrol.wait;" ::: "memory");         \
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+  } while (0)
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }

@@ -107,6 +107,43 @@ bool build_hadamard_blocks(const double K0[576], double blk[8][3][3], double* k0
   return true;
 }
 
+// The eight Hadamard-basis blocks of the isotropic cube come in four kinds (related by axis
+// permutations): class 0 (normal strains) and class 7 are p I + q (11^T - I); classes 1, 2, 4
+// couple two members with [[a, b], [b, a]] (the translation member is zero); classes 3, 5, 6
+// couple two members with a (11^T) and leave the m = 7 member alone with d.  Returns false if
+// blk does not have this form.
+bool block_kinds(const double blk[8][3][3], BlockKinds* out) {
+  const double p0 = blk[0][0][0], q0 = blk[0][0][1], p7 = blk[7][0][0], q7 = blk[7][0][1];
+  const double ta = blk[1][1][1], tb = blk[1][1][2];
+  const double ua = blk[3][0][0], ud = blk[3][2][2];
+  const double tol = 1e-12 * std::fabs(p0);
+  auto eq = [&](double a, double b) { return std::fabs(a - b) <= tol; };
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) {
+      if (!eq(blk[0][c][d], c == d ? p0 : q0)) return false;
+      if (!eq(blk[7][c][d], c == d ? p7 : q7)) return false;
+    }
+  for (int t = 0; t < 3; ++t) {
+    const int k = 1 << t, ca = (t + 1) % 3, cb = (t + 2) % 3;
+    if (!eq(blk[k][ca][ca], ta) || !eq(blk[k][cb][cb], ta) || !eq(blk[k][ca][cb], tb) ||
+        !eq(blk[k][cb][ca], tb))
+      return false;
+    const int k2 = 7 ^ (1 << t);
+    if (!eq(blk[k2][ca][ca], ua) || !eq(blk[k2][cb][cb], ua) || !eq(blk[k2][ca][cb], ua) ||
+        !eq(blk[k2][cb][ca], ua) || !eq(blk[k2][t][t], ud))
+      return false;
+  }
+  out->a0 = p0 - q0;
+  out->b0 = q0;
+  out->a7 = p7 - q7;
+  out->b7 = q7;
+  out->ta = ta;
+  out->tb = tb;
+  out->ua = ua;
+  out->ud = ud;
+  return true;
+}
+
 std::vector<FilterTap> filter_taps(double rmin) {
   std::vector<FilterTap> taps;
   const int R = (int)std::ceil(rmin) - 1;

@@ -15,6 +15,7 @@ template <typename T, int MODE, bool MAT>
 __global__ void k_filter(Geom g, const int4* __restrict__ taps, const T* __restrict__ tapw,
                          int ntaps, const T* __restrict__ in, const T* __restrict__ Hs,
                          T* __restrict__ out, T E0, T Emin, T penal, T h, T* __restrict__ s_out) {
+  PDL_ENTER();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.nel; e += gridDim.x * blockDim.x) {
     const int i = e % g.nx, j = (e / g.nx) % g.ny, k = e / (g.nx * g.ny);
     T acc = T(0);
@@ -40,16 +41,16 @@ cudaError_t launch_filter(cudaStream_t st, Geom g, const int4* taps, const T* ta
   int blocks = (g.nel + 255) / 256;
   if (blocks > 16384) blocks = 16384;
   if (mode == 0 && material)
-    k_filter<T, 0, true><<<blocks, 256, 0, st>>>(g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
+    pdl_launch(k_filter<T, 0, true>, blocks, 256, 0, st, g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
                                                  penal, h, s_out);
   else if (mode == 0)
-    k_filter<T, 0, false><<<blocks, 256, 0, st>>>(g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
+    pdl_launch(k_filter<T, 0, false>, blocks, 256, 0, st, g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
                                                   penal, h, s_out);
   else if (mode == 1)
-    k_filter<T, 1, false><<<blocks, 256, 0, st>>>(g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
+    pdl_launch(k_filter<T, 1, false>, blocks, 256, 0, st, g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
                                                   penal, h, s_out);
   else
-    k_filter<T, 2, false><<<blocks, 256, 0, st>>>(g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
+    pdl_launch(k_filter<T, 2, false>, blocks, 256, 0, st, g, taps, tapw, ntaps, in, Hs, out, E0, Emin,
                                                   penal, h, s_out);
   return cudaGetLastError();
 }
@@ -58,6 +59,7 @@ cudaError_t launch_filter(cudaStream_t st, Geom g, const int4* taps, const T* ta
 template <typename T>
 __global__ void k_material(int n, const T* __restrict__ rho, T E0, T Emin, T penal, T h,
                            T* __restrict__ s) {
+  PDL_ENTER();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
     s[e] = h * (Emin + pow(rho[e], penal) * (E0 - Emin));
 }
@@ -67,7 +69,7 @@ cudaError_t launch_material(cudaStream_t st, int n, const T* rho, T E0, T Emin, 
                             T* s) {
   int blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_material<T><<<blocks, 256, 0, st>>>(n, rho, E0, Emin, penal, h, s);
+  pdl_launch(k_material<T>, blocks, 256, 0, st, n, rho, E0, Emin, penal, h, s);
   return cudaGetLastError();
 }
 
@@ -80,6 +82,7 @@ template <typename T, bool PAIR>
 __global__ void k_sensitivity(Geom g, const T* __restrict__ rho, const T* __restrict__ u,
                               const T* __restrict__ ulo, const __grid_constant__ ElemConst<T> C,
                               T penal, T E0, T Emin, T h, T* __restrict__ dc) {
+  PDL_ENTER();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.nel; e += gridDim.x * blockDim.x) {
     const int i = e % g.nx, j = (e / g.nx) % g.ny, k = e / (g.nx * g.ny);
     T X[3][8];
@@ -134,12 +137,12 @@ cudaError_t launch_sensitivity(cudaStream_t st, Geom g, const T* rho, const T* u
   if (blocks > 16384) blocks = 16384;
   if (ulo) {
     if constexpr (sizeof(T) == 4) {
-      k_sensitivity<T, true><<<blocks, 128, 0, st>>>(g, rho, u, ulo, c, penal, E0, Emin, h, dc);
+      pdl_launch(k_sensitivity<T, true>, blocks, 128, 0, st, g, rho, u, ulo, c, penal, E0, Emin, h, dc);
       return cudaGetLastError();
     }
     return cudaErrorInvalidValue;
   }
-  k_sensitivity<T, false><<<blocks, 128, 0, st>>>(g, rho, u, nullptr, c, penal, E0, Emin, h, dc);
+  pdl_launch(k_sensitivity<T, false>, blocks, 128, 0, st, g, rho, u, nullptr, c, penal, E0, Emin, h, dc);
   return cudaGetLastError();
 }
 
@@ -159,6 +162,7 @@ template <typename T>
 __global__ void __launch_bounds__(kOcThreads)
     k_oc_pass(int n, const T* __restrict__ z, const T* __restrict__ dc, const T* __restrict__ w,
               double vmax, T move, double* bracket, double* partials, unsigned* counter) {
+  PDL_ENTER();
   __shared__ T s_scale[kOcCand];
   __shared__ double s_w[kOcThreads / 32][kOcCand];
   __shared__ bool s_last;
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(kOcThreads)
     k_oc_final(int n, const T* __restrict__ z, const T* __restrict__ dc, const T* __restrict__ w,
                T move, const double* bracket, T* __restrict__ znew, double* partials,
                unsigned* counter, double* change_out) {
+  PDL_ENTER();
   __shared__ float s_m[kOcThreads / 32];
   __shared__ bool s_last;
   const double ec = 0.5 * (bracket[0] + bracket[1]);
@@ -303,6 +308,7 @@ __global__ void __launch_bounds__(kOcThreads)
 template <typename T>
 __global__ void k_oc_change64(int n, const T* __restrict__ z, const T* __restrict__ znew,
                               double* partials, unsigned* counter, double* change_out) {
+  PDL_ENTER();
   __shared__ double s_m[kOcThreads / 32];
   __shared__ bool s_last;
   double mx = 0.0;
@@ -349,14 +355,14 @@ cudaError_t launch_oc(cudaStream_t st, int n, const T* z, const T* dc, const T* 
   if (e != cudaSuccess) return e;
   // 31^9 > 200 / (1e-10 / ln 2): nine passes always reach the tolerance
   for (int pass = 0; pass < 9; ++pass)
-    k_oc_pass<T><<<blocks, kOcThreads, 0, st>>>(n, z, dc, w, vmax, (T)move, bracket, partials,
+    pdl_launch(k_oc_pass<T>, blocks, kOcThreads, 0, st, n, z, dc, w, vmax, (T)move, bracket, partials,
                                                 counter);
   int fb = (n + kOcThreads - 1) / kOcThreads;
   if (fb > 2 * 152 * 4) fb = 2 * 152 * 4;
-  k_oc_final<T><<<fb, kOcThreads, 0, st>>>(n, z, dc, w, (T)move, bracket, znew, partials,
+  pdl_launch(k_oc_final<T>, fb, kOcThreads, 0, st, n, z, dc, w, (T)move, bracket, znew, partials,
                                            counter, change_out);
   if (sizeof(T) == 8)
-    k_oc_change64<T><<<fb, kOcThreads, 0, st>>>(n, z, znew, partials, counter, change_out);
+    pdl_launch(k_oc_change64<T>, fb, kOcThreads, 0, st, n, z, znew, partials, counter, change_out);
   return cudaGetLastError();
 }
 

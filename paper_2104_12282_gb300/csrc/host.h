@@ -21,6 +21,15 @@ void build_unit_stiffness(double nu, double K0[576]);
 bool build_hadamard_blocks(const double K0[576], double blk[8][3][3], double* k0diag);
 std::vector<FilterTap> filter_taps(double rmin);
 
+// Scalar constants of the four block kinds of K0 in the Hadamard basis (see element.cu).
+struct BlockKinds {
+  double a0, b0;  // class 0: W = a0 X + b0 (sum X) 1
+  double a7, b7;  // class 7: same form
+  double ta, tb;  // classes 1, 2, 4: [[ta, tb], [tb, ta]]
+  double ua, ud;  // classes 3, 5, 6: ua on the coupled pair (all four entries), ud alone
+};
+bool block_kinds(const double blk[8][3][3], BlockKinds* out);
+
 // Largest coarsest-level DOF count solved by a dense inverse in one CTA.
 constexpr int kMaxDenseDofs = 648;
 // Upper bound of lambda_max(D^-1 K) over any grid: max over one element of
@@ -47,7 +56,32 @@ struct MarchArgs {
   int dot_kind;         // 0 none, 1: pq -> alpha, 2: rz_new -> beta
   const int* skip;      // if non-null and *skip != 0 the kernel returns at once
   const CgScalars* gate;  // residual replacement: run only when gate->it % gate->rr_every == 0
+  int xprev_zero;       // CHEB: the previous iterate is zero (first step after a zero start)
 };
+
+// FP32 two-rows-per-thread product (matvec2.cu); same modes as k_march, no pair input.
+struct March2Args {
+  Geom g;
+  int kz;
+  const float* s;
+  const uint8_t* mask;
+  const float* x;
+  const float* b;
+  float* xprev;
+  float* y;
+  float c1, c2;
+  double* partials;
+  unsigned* counter;
+  CgScalars* sc;
+  int dot_kind;
+  const int* skip;
+  int xprev_zero;  // CHEB: the previous iterate is zero (first step after a zero start)
+};
+struct March2Const {
+  float a0, b0, a7, b7, ta, tb, ua, ud, k0diag;
+};
+cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const March2Const& c,
+                          int num_sms);
 
 // All kernels are launched on `st`.  Wrappers return 0 or a cudaError_t.
 template <typename T>
@@ -60,7 +94,8 @@ cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* ma
                           unsigned* counter, CgScalars* sc, int dot_kind, const int* skip);
 template <typename T>
 cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* rc,
-                            const uint8_t* mask_c, const int* skip);
+                            const uint8_t* mask_c, const int* skip, T* x1 = nullptr,
+                            const T* sc = nullptr, T c2 = T(0), T k0diag = T(0));
 template <typename T>
 cudaError_t launch_prolong_add(cudaStream_t st, Geom gf, Geom gc, const T* xc, T* xf,
                                const uint8_t* mask_f, const int* skip);
@@ -142,6 +177,7 @@ struct tomo_grid {
   double K0[576];
   double blk[8][3][3];
   double k0diag = 0.0;
+  tomo::BlockKinds kinds{};    // the four block kinds of K0 in the mode basis
   double lam_hi = 0.0;         // Chebyshev upper end
   double cheb_ratio = 10.0;    // Chebyshev interval [lam_hi / ratio, lam_hi]
   std::vector<tomo::FilterTap> taps;
@@ -181,12 +217,20 @@ struct tomo_grid {
   size_t ev_used = 0;
   int64_t prof_launches = 0;
   double prof_bytes = 0.0;
+  std::vector<int> ev_tag;          // per event pair: -1 fine-level product, else level + 1
+  double level_ms[16] = {};         // eager V-cycle time per level (all kernels), level 0..15
+  int64_t level_n[16] = {};
   bool have_solution = false;
   int partials_n = 0;
   double ff = 0.0;                  // ||f||^2 over free DOFs
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   cudaGraphExec_t loop_exec = nullptr;  // device-side PCG loop (conditional while)
   bool use_graph = true;
+  // phase timing (events at phase boundaries; the CG loop stays a graph)
+  bool phase_prof = false;
+  cudaEvent_t phase_ev[8] = {};
+  double phase_ms[8] = {};
+  int64_t phase_calls = 0;
   int64_t launches = 0;             // kernels launched (executed graph bodies included)
   int64_t iter_launches = 0;        // kernels in one captured loop body
   // FP64 residual replacement of FP32 grids: r = f - K(x_hi + x_lo) evaluated in FP64

@@ -83,6 +83,7 @@ __device__ __forceinline__ void block_apply(const ElemConst<T>& C, T se, const T
 template <typename T, int MODE, bool PAIR, bool DOT>
 __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
     k_march(const __grid_constant__ MarchArgs<T> A, const __grid_constant__ ElemConst<T> C) {
+  PDL_ENTER();
   if (A.skip != nullptr && *A.skip) return;
   if (A.gate != nullptr && (A.gate->rr_every <= 0 || (A.gate->it % A.gate->rr_every) != 0))
     return;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
         for (int c = 0; c < 3; ++c) bv[c] = ldg(A.b + (size_t)c * nn + n_out);
       }
-      if (MODE == M_CHEB && A.c1 != T(0)) {
+      if (MODE == M_CHEB && A.c1 != T(0) && !A.xprev_zero) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) xp[c] = A.xprev[(size_t)c * nn + n_out];
       }
@@ -335,20 +336,20 @@ cudaError_t launch_march(cudaStream_t st, int mode, const MarchArgs<T>& a, const
   const bool pair = a.xlo != nullptr;
   const bool dot = a.dot_kind != 0;
   if (mode == M_APPLY) {
-    if (dot) k_march<T, M_APPLY, false, true><<<grid, block, 0, st>>>(args, c);
-    else k_march<T, M_APPLY, false, false><<<grid, block, 0, st>>>(args, c);
+    if (dot) pdl_launch(k_march<T, M_APPLY, false, true>, grid, block, 0, st, args, c);
+    else pdl_launch(k_march<T, M_APPLY, false, false>, grid, block, 0, st, args, c);
   } else if (mode == M_RESID) {
     if constexpr (sizeof(T) == 4) {
       if (pair) {
-        k_march<T, M_RESID, true, false><<<grid, block, 0, st>>>(args, c);
+        pdl_launch(k_march<T, M_RESID, true, false>, grid, block, 0, st, args, c);
         return cudaGetLastError();
       }
     }
     if (pair) return cudaErrorInvalidValue;
-    k_march<T, M_RESID, false, false><<<grid, block, 0, st>>>(args, c);
+    pdl_launch(k_march<T, M_RESID, false, false>, grid, block, 0, st, args, c);
   } else {
-    if (dot) k_march<T, M_CHEB, false, true><<<grid, block, 0, st>>>(args, c);
-    else k_march<T, M_CHEB, false, false><<<grid, block, 0, st>>>(args, c);
+    if (dot) pdl_launch(k_march<T, M_CHEB, false, true>, grid, block, 0, st, args, c);
+    else pdl_launch(k_march<T, M_CHEB, false, false>, grid, block, 0, st, args, c);
   }
   return cudaGetLastError();
 }

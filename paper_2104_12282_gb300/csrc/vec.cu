@@ -21,6 +21,7 @@ __global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restr
                          const T* __restrict__ b, T c2, T k0diag, T* __restrict__ x1,
                          T* __restrict__ x0, double* partials, unsigned* counter, CgScalars* sc,
                          const int* skip) {
+  PDL_ENTER();
   if (skipped(skip)) return;
   double dot = 0.0;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nn; n += gridDim.x * blockDim.x) {
@@ -66,11 +67,11 @@ cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* ma
   int blocks = (g.nn + 255) / 256;
   if (dot_kind) {
     if (blocks > kRedBlocks) blocks = kRedBlocks;
-    k_jacobi<T, true><<<blocks, 256, 0, st>>>(g, s, mask, b, c2, k0diag, x1, x0zero, partials,
+    pdl_launch(k_jacobi<T, true>, blocks, 256, 0, st, g, s, mask, b, c2, k0diag, x1, x0zero, partials,
                                               counter, sc, skip);
   } else {
     if (blocks > 4096) blocks = 4096;
-    k_jacobi<T, false><<<blocks, 256, 0, st>>>(g, s, mask, b, c2, k0diag, x1, x0zero, nullptr,
+    pdl_launch(k_jacobi<T, false>, blocks, 256, 0, st, g, s, mask, b, c2, k0diag, x1, x0zero, nullptr,
                                                nullptr, nullptr, skip);
   }
   return cudaGetLastError();
@@ -80,9 +81,13 @@ cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* ma
 // Restriction r_c = P^T r_f (trilinear, weights 1, 1/2 per axis), masked on the coarse grid.
 // Fine node i maps to coarse node i/2 (even) or to (i-1)/2 and (i+1)/2 (odd).
 // ---------------------------------------------------------------------------------------
+// Optionally fused with the first (zero-start) Chebyshev step on the coarse level:
+// x1 = c2 D^-1 r_c, D from the coarse moduli sc.
 template <typename T>
 __global__ void k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ rc,
-                           const uint8_t* __restrict__ mask_c, const int* skip) {
+                           const uint8_t* __restrict__ mask_c, const int* skip,
+                           T* __restrict__ x1, const T* __restrict__ sc, T c2, T k0diag) {
+  PDL_ENTER();
   if (skipped(skip)) return;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gc.nn; n += gridDim.x * blockDim.x) {
     const int I = n % gc.nxn, J = (n / gc.nxn) % gc.nyn, K = n / (gc.nxn * gc.nyn);
@@ -108,15 +113,30 @@ __global__ void k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __rest
     const unsigned mk = mask_c[n];
 #pragma unroll
     for (int c = 0; c < 3; ++c) rc[(size_t)c * gc.nn + n] = ((mk >> c) & 1u) ? T(0) : acc[c];
+    if (x1 != nullptr) {
+      T S = T(0);
+      for (int dz = -1; dz <= 0; ++dz)
+        for (int dy = -1; dy <= 0; ++dy)
+          for (int dx = -1; dx <= 0; ++dx) {
+            const int ei = I + dx, ej = J + dy, ek = K + dz;
+            if (ei >= 0 && ei < gc.nx && ej >= 0 && ej < gc.ny && ek >= 0 && ek < gc.nz)
+              S += sc[ei + gc.nx * (ej + gc.ny * ek)];
+          }
+      const T dg = k0diag * S;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        x1[(size_t)c * gc.nn + n] = (((mk >> c) & 1u) || !(dg > T(0))) ? T(0) : c2 * acc[c] / dg;
+    }
   }
 }
 
 template <typename T>
 cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* rc,
-                            const uint8_t* mask_c, const int* skip) {
+                            const uint8_t* mask_c, const int* skip, T* x1, const T* sc, T c2,
+                            T k0diag) {
   int blocks = (gc.nn + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_restrict<T><<<blocks, 256, 0, st>>>(gf, gc, rf, rc, mask_c, skip);
+  pdl_launch(k_restrict<T>, blocks, 256, 0, st, gf, gc, rf, rc, mask_c, skip, x1, sc, c2, k0diag);
   return cudaGetLastError();
 }
 
@@ -124,6 +144,7 @@ cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* r
 template <typename T>
 __global__ void k_prolong_add(Geom gf, Geom gc, const T* __restrict__ xc, T* __restrict__ xf,
                               const uint8_t* __restrict__ mask_f, const int* skip) {
+  PDL_ENTER();
   if (skipped(skip)) return;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gf.nn; n += gridDim.x * blockDim.x) {
     const int i = n % gf.nxn, j = (n / gf.nxn) % gf.nyn, k = n / (gf.nxn * gf.nyn);
@@ -159,7 +180,7 @@ cudaError_t launch_prolong_add(cudaStream_t st, Geom gf, Geom gc, const T* xc, T
                                const uint8_t* mask_f, const int* skip) {
   int blocks = (gf.nn + 255) / 256;
   if (blocks > 16384) blocks = 16384;
-  k_prolong_add<T><<<blocks, 256, 0, st>>>(gf, gc, xc, xf, mask_f, skip);
+  pdl_launch(k_prolong_add<T>, blocks, 256, 0, st, gf, gc, xc, xf, mask_f, skip);
   return cudaGetLastError();
 }
 
@@ -167,6 +188,7 @@ cudaError_t launch_prolong_add(cudaStream_t st, Geom gf, Geom gc, const T* xc, T
 // s_c = (sum of children s_f) / 4.  Children outside the fine grid count as void.
 template <typename T>
 __global__ void k_coarsen_s(Geom gf, Geom gc, const T* __restrict__ sf, T* __restrict__ sc) {
+  PDL_ENTER();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gc.nel; e += gridDim.x * blockDim.x) {
     const int I = e % gc.nx, J = (e / gc.nx) % gc.ny, K = e / (gc.nx * gc.ny);
     T acc = T(0);
@@ -184,7 +206,7 @@ template <typename T>
 cudaError_t launch_coarsen_s(cudaStream_t st, Geom gf, Geom gc, const T* sf, T* sc) {
   int blocks = (gc.nel + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_coarsen_s<T><<<blocks, 256, 0, st>>>(gf, gc, sf, sc);
+  pdl_launch(k_coarsen_s<T>, blocks, 256, 0, st, gf, gc, sf, sc);
   return cudaGetLastError();
 }
 
@@ -199,6 +221,7 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(Geom g, const T* __restr
                                                         const __grid_constant__ DenseK0<T> K0,
                                                         T* __restrict__ A, T* __restrict__ dscale,
                                                         unsigned* status) {
+  PDL_ENTER();
   const int n = 3 * g.nn;
   const int tid = threadIdx.x, nt = blockDim.x;
   extern __shared__ unsigned char smem_raw[];
@@ -278,38 +301,45 @@ cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          200 * 1024 + 1024);
     if (e != cudaSuccess) return e;
-    k_coarse_factor<T, true><<<1, 1024, full, st>>>(g, s, mask, K0, A, dscale, status);
+    pdl_launch(k_coarse_factor<T, true>, 1, 1024, full, st, g, s, mask, K0, A, dscale, status);
   } else {
-    k_coarse_factor<T, false><<<1, 1024, sizeof(T) * (size_t)n, st>>>(g, s, mask, K0, A, dscale,
+    pdl_launch(k_coarse_factor<T, false>, 1, 1024, sizeof(T) * (size_t)n, st, g, s, mask, K0, A, dscale,
                                                                       status);
   }
   return cudaGetLastError();
 }
 
-// z = D^-1/2 Ainv D^-1/2 r (one CTA, a warp per row).
+// z = D^-1/2 Ainv D^-1/2 r.  Ainv is symmetric, so thread `row` walks column `row`
+// (Ainv[c * n + row], consecutive threads read consecutive addresses); accumulated in T.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_apply(int n, const T* __restrict__ Ainv,
                                                        const T* __restrict__ dsc,
                                                        const T* __restrict__ r, T* __restrict__ z,
                                                        const int* skip) {
+  PDL_ENTER();
   if (skipped(skip)) return;
   extern __shared__ unsigned char smem_raw[];
   T* rs = reinterpret_cast<T*>(smem_raw);
   for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = dsc[q] * r[q];
   __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int row = w; row < n; row += nw) {
-    double acc = 0.0;
-    for (int c = lane; c < n; c += 32) acc += (double)(Ainv[(size_t)row * n + c] * rs[c]);
-    acc = warp_sum(acc);
-    if (lane == 0) z[row] = dsc[row] * (T)acc;
+  for (int row = threadIdx.x; row < n; row += blockDim.x) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int c = 0;
+    for (; c + 3 < n; c += 4) {
+      a0 += __ldg(Ainv + (size_t)(c + 0) * n + row) * rs[c + 0];
+      a1 += __ldg(Ainv + (size_t)(c + 1) * n + row) * rs[c + 1];
+      a2 += __ldg(Ainv + (size_t)(c + 2) * n + row) * rs[c + 2];
+      a3 += __ldg(Ainv + (size_t)(c + 3) * n + row) * rs[c + 3];
+    }
+    for (; c < n; ++c) a0 += __ldg(Ainv + (size_t)c * n + row) * rs[c];
+    z[row] = dsc[row] * ((a0 + a1) + (a2 + a3));
   }
 }
 
 template <typename T>
 cudaError_t launch_coarse_apply(cudaStream_t st, int n, const T* Ainv, const T* dscale,
                                 const T* r, T* z, const int* skip) {
-  k_coarse_apply<T><<<1, 1024, sizeof(T) * (size_t)n, st>>>(n, Ainv, dscale, r, z, skip);
+  pdl_launch(k_coarse_apply<T>, 1, 1024, sizeof(T) * (size_t)n, st, n, Ainv, dscale, r, z, skip);
   return cudaGetLastError();
 }
 
@@ -322,6 +352,7 @@ template <typename T, bool PAIRX>
 __global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __restrict__ r,
                         const T* __restrict__ p, const T* __restrict__ q, double* partials,
                         unsigned* counter, CgScalars* sc) {
+  PDL_ENTER();
   if (sc->done) return;
   const double alpha_d = sc->alpha;
   const T alpha = (T)alpha_d;
@@ -362,13 +393,13 @@ cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* 
                          double* partials, unsigned* counter, CgScalars* sc) {
   if (xlo) {
     if constexpr (sizeof(T) == 4) {
-      k_cg_xr<T, true><<<kRedBlocks * 2, kRedThreads, 0, st>>>(n, xhi, xlo, r, p, q, partials,
+      pdl_launch(k_cg_xr<T, true>, kRedBlocks * 2, kRedThreads, 0, st, n, xhi, xlo, r, p, q, partials,
                                                                counter, sc);
       return cudaGetLastError();
     }
     return cudaErrorInvalidValue;
   }
-  k_cg_xr<T, false><<<kRedBlocks * 2, kRedThreads, 0, st>>>(n, xhi, nullptr, r, p, q, partials,
+  pdl_launch(k_cg_xr<T, false>, kRedBlocks * 2, kRedThreads, 0, st, n, xhi, nullptr, r, p, q, partials,
                                                             counter, sc);
   return cudaGetLastError();
 }
@@ -376,6 +407,7 @@ cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* 
 // Device-side loop control of the conditional-while graph: continue while CG has not
 // stopped; the launch counter bounds the loop even if a reduction never reported.
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc) {
+  PDL_ENTER();
   sc->loops += 1;
   const bool go = !sc->done && sc->loops < sc->maxit + 8;
   if (!go) sc->done = 1;
@@ -383,13 +415,14 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc) {
 }
 
 cudaError_t launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, CgScalars* sc) {
-  k_loop_cond<<<1, 1, 0, st>>>(h, sc);
+  pdl_launch(k_loop_cond, 1, 1, 0, st, h, sc);
   return cudaGetLastError();
 }
 
 // p = z + beta p
 template <typename T>
 __global__ void k_cg_p(int n, T* __restrict__ p, const T* __restrict__ z, CgScalars* sc) {
+  PDL_ENTER();
   if (sc->done) return;
   const T beta = (T)sc->beta;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -400,7 +433,7 @@ template <typename T>
 cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc) {
   int blocks = (n + 255) / 256;
   if (blocks > 8 * 152) blocks = 8 * 152;
-  k_cg_p<T><<<blocks, 256, 0, st>>>(n, p, z, sc);
+  pdl_launch(k_cg_p<T>, blocks, 256, 0, st, n, p, z, sc);
   return cudaGetLastError();
 }
 
@@ -409,6 +442,7 @@ template <typename TA, typename TB>
 __global__ void k_dot(int n, const TA* __restrict__ a, const TB* __restrict__ b,
                       const TB* __restrict__ blo, double* partials, unsigned* counter,
                       double* out) {
+  PDL_ENTER();
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double bv = (double)b[i];
@@ -422,13 +456,14 @@ __global__ void k_dot(int n, const TA* __restrict__ a, const TB* __restrict__ b,
 template <typename TA, typename TB>
 cudaError_t launch_dot(cudaStream_t st, int n, const TA* a, const TB* b, const TB* blo,
                        double* partials, unsigned* counter, double* out) {
-  k_dot<TA, TB><<<kRedBlocks, kRedThreads, 0, st>>>(n, a, b, blo, partials, counter, out);
+  pdl_launch(k_dot<TA, TB>, kRedBlocks, kRedThreads, 0, st, n, a, b, blo, partials, counter, out);
   return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void k_mask_copy(Geom g, const T* __restrict__ in, const uint8_t* __restrict__ mask,
                             T* __restrict__ out) {
+  PDL_ENTER();
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * g.nn; q += gridDim.x * blockDim.x) {
     const int c = q / g.nn, node = q % g.nn;
     out[q] = ((mask[node] >> c) & 1u) ? T(0) : in[q];
@@ -439,13 +474,14 @@ template <typename T>
 cudaError_t launch_mask_copy(cudaStream_t st, Geom g, const T* in, const uint8_t* mask, T* out) {
   int blocks = (3 * g.nn + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_mask_copy<T><<<blocks, 256, 0, st>>>(g, in, mask, out);
+  pdl_launch(k_mask_copy<T>, blocks, 256, 0, st, g, in, mask, out);
   return cudaGetLastError();
 }
 
 template <typename TO, typename TI>
 __global__ void k_convert(int n, const TI* __restrict__ in, const TI* __restrict__ inlo,
                           TO* __restrict__ out, const CgScalars* gate) {
+  PDL_ENTER();
   if (gate != nullptr &&
       (gate->done || gate->rr_every <= 0 || (gate->it % gate->rr_every) != 0))
     return;
@@ -460,7 +496,7 @@ cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo,
                            const CgScalars* gate) {
   int blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_convert<TO, TI><<<blocks, 256, 0, st>>>(n, in, inlo, out, gate);
+  pdl_launch(k_convert<TO, TI>, blocks, 256, 0, st, n, in, inlo, out, gate);
   return cudaGetLastError();
 }
 
@@ -469,7 +505,7 @@ cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo,
                                         T, T, T*, T*, double*, unsigned*, CgScalars*, int,     \
                                         const int*);                                         \
   template cudaError_t launch_restrict<T>(cudaStream_t, Geom, Geom, const T*, T*,             \
-                                          const uint8_t*, const int*);                       \
+                                          const uint8_t*, const int*, T*, const T*, T, T);   \
   template cudaError_t launch_prolong_add<T>(cudaStream_t, Geom, Geom, const T*, T*,          \
                                              const uint8_t*, const int*);                    \
   template cudaError_t launch_coarsen_s<T>(cudaStream_t, Geom, Geom, const T*, T*);           \

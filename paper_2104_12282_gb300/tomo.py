@@ -37,7 +37,9 @@ class GridDesc(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int32),
                 ("mg_levels", ctypes.c_int32), ("smoother_degree", ctypes.c_int32),
-                ("cheb_ratio", ctypes.c_double), ("rr_every", ctypes.c_int32),
+                ("coarse_degree", ctypes.c_int32),
+                ("cheb_ratio", ctypes.c_double), ("cheb_lmax", ctypes.c_double),
+                ("rr_every", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -81,6 +83,10 @@ def _load():
                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
         "tomo_get_launch_count": (st, [G, ctypes.POINTER(ctypes.c_int64)]),
         "tomo_profile_enable": (st, [G, ctypes.c_int]),
+        "tomo_profile_phases": (st, [G, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int64)]),
+        "tomo_profile_levels": (st, [G, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
         "tomo_profile_read": (st, [G, ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -111,7 +117,9 @@ def exported_symbols():
             "tomo_oc_step", "tomo_oc_step_d", "tomo_oc_step_noalloc", "tomo_gradient",
             "tomo_gradient_d",
             "tomo_get_displacement", "tomo_get_displacement_d", "tomo_get_counts",
-            "tomo_get_launch_count", "tomo_profile_enable", "tomo_profile_read",
+            "tomo_get_launch_count", "tomo_profile_enable", "tomo_profile_phases",
+            "tomo_profile_levels",
+            "tomo_profile_read",
             "tomo_last_error"]
 
 
@@ -182,7 +190,8 @@ class Grid:
 
     def __init__(self, nx, ny, nz, fixed, f, *, h=1.0, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0,
                  rmin=1.5, precision=FP32, precond=PRECOND_MG, rtol=1e-6, maxit=2000,
-                 mg_levels=0, smoother_degree=2, cheb_ratio=10.0, rr_every=50, stream=None):
+                 mg_levels=0, smoother_degree=2, coarse_degree=0, cheb_ratio=20.0, cheb_lmax=0.0,
+                 rr_every=50, stream=None):
         L = lib()
         d = GridDesc()
         L.tomo_default_desc(ctypes.byref(d))
@@ -198,6 +207,8 @@ class Grid:
         d.precision, d.precond = precision, precond
         d.rtol, d.maxit, d.mg_levels = rtol, maxit, mg_levels
         d.smoother_degree, d.cheb_ratio, d.rr_every = smoother_degree, cheb_ratio, rr_every
+        d.coarse_degree = coarse_degree
+        d.cheb_lmax = cheb_lmax
         d.stream = stream if stream is not None else _current_stream()
         h_out = ctypes.c_void_p()
         st = L.tomo_create_grid(ctypes.byref(d), ctypes.byref(h_out))
@@ -297,8 +308,29 @@ class Grid:
             raise TomoError(st, "tomo_get_launch_count")
         return n.value
 
-    def profile_enable(self, on=True):
-        lib().tomo_profile_enable(self._h, int(bool(on)))
+    def profile_enable(self, on=True, phases=False):
+        lib().tomo_profile_enable(self._h, (1 if on else 0) | (2 if phases else 0))
+
+    def profile_levels(self, n=16):
+        """(ms, launches) per multigrid level, accumulated by profile_read()."""
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        st = lib().tomo_profile_levels(self._h, ms, cnt, n)
+        if st != 0:
+            raise TomoError(st, "tomo_profile_levels")
+        return list(ms), list(cnt)
+
+    def profile_phases(self):
+        """Accumulated ms per phase since the last call: filter, levels, cg, sensitivity,
+        adjoints, oc; and the number of gradient calls."""
+        ms = (ctypes.c_double * 7)()
+        n = ctypes.c_int64()
+        st = lib().tomo_profile_phases(self._h, ms, ctypes.byref(n))
+        if st != 0:
+            raise TomoError(st, "tomo_profile_phases")
+        names = ["filter", "levels", "cg", "sensitivity", "adjoints", "unused", "oc"]
+        out = {k: ms[i] for i, k in enumerate(names) if k != "unused"}
+        return out, n.value
 
     def profile_read(self):
         n, ms, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
