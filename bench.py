@@ -53,6 +53,35 @@ def dist_env():
 
 
 # ---------------------------------------------------------------------------------------
+# Replicas: one process per GPU, no exchange on the data path; the process group only
+# brackets the timed region (barrier) and takes the slowest rank's time.
+# ---------------------------------------------------------------------------------------
+def init_ranks(backend):
+    """torch.distributed module with the default group initialised, or None at N = 1."""
+    world, _, _ = dist_env()
+    if world == 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(dist, x, device=None):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps_per_rank, slowest_ms):
+    """Units processed by all ranks divided by the slowest rank's time (units/s)."""
+    return world * steps_per_rank / (slowest_ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------------------
 def oracle_sample(seed):
@@ -209,25 +238,17 @@ def run_ours(args):
     from paper_2104_12282_gb300 import tomo
 
     world, rank, local = dist_env()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group(backend="nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    dist = init_ranks("nccl")
 
     def barrier():
         if dist is not None:
             dist.barrier(device_ids=[dev.index])
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x):
+        return max_over_ranks(dist, x, dev)
 
     p = P.mbb_192x96x76(args.seed)
     fields = [P.bumpy_field(p.dims, args.seed + k) for k in range(2)]
@@ -268,8 +289,8 @@ def run_ours(args):
         barrier()
     launches = g.launch_count() - l0
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = max_over_ranks(sum(ms))
-    value = world * args.steps / (total_ms * 1e-3)
+    total_ms = slowest(sum(ms))
+    value = whole_job_rate(world, args.steps, total_ms)
 
     # ---------------- roofline of the smoother/product kernel ----------------
     g.profile_enable(True)
@@ -298,8 +319,8 @@ def run_ours(args):
         step(g, zh[s % 2], dch, dvh, znh)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = max_over_ranks(sum(e2e_ms))
-    e2e_value = world * args.steps / (e2e_total * 1e-3)
+    e2e_total = slowest(sum(e2e_ms))
+    e2e_value = whole_job_rate(world, args.steps, e2e_total)
     nb = 4 * p.n_el
     h2d = 4 * nb   # z (gradient), z, dcdz, dvdz (OC step)
     d2h = 3 * nb   # dcdz, dvdz (gradient), z_new (OC step)
@@ -324,7 +345,7 @@ def run_ours(args):
         ms64.append(e0.elapsed_time(e1))
         c64s.append(c)
     g64.close()
-    value64 = world * args.fp64_steps / (max_over_ranks(sum(ms64)) * 1e-3)
+    value64 = whole_job_rate(world, args.fp64_steps, slowest(sum(ms64)))
     # FP64 reference compliance at 1e-10 (untimed) for the accuracy column
     gref = make(tomo.FP64, 1e-10)
     cref = []

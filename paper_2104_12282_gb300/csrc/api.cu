@@ -458,17 +458,16 @@ tomo_status enqueue_iteration(tomo_grid* G) {
       rr.gate = G->sc;
       TRY(march<T>(G, 0, M_RESID, rr));
     } else {
-      CK(launch_convert<double, float>(G->stream, n, xhi, xlo, G->x64, G->sc));
-      G->launches += 1;
+      // one launch: the float-pair iterate is joined into double on load, the FP64
+      // residual is rounded to float on store
       MarchArgs<double> rr{};
-      rr.x = G->x64;
+      rr.xf_hi = xhi;
+      rr.xf_lo = xlo;
       rr.b = G->f64;
-      rr.y = G->r64;
+      rr.yf = r;
       rr.skip = &G->sc->done;
       rr.gate = G->sc;
       TRY(march<double>(G, 0, M_RESID, rr, G->s64));
-      CK(launch_convert<float, double>(G->stream, n, G->r64, nullptr, r, G->sc));
-      G->launches += 1;
     }
   }
   T* z = nullptr;
@@ -641,6 +640,7 @@ tomo_status volume_gradient(tomo_grid* G, T* out) {
     G->dvdz_ready = true;  // G->dvdz holds the constant element volumes
   }
   CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                      G->filter_radius,
                       (const T*)G->dvdz, (const T*)G->Hs, out, 1, 0, T(0), T(0), T(0), T(0),
                       nullptr));
   G->launches += 1;
@@ -673,7 +673,8 @@ tomo_status do_filter(tomo_grid* G, const T* in, T* out, int transpose) {
   TRY(stage_in(G, in, bytes, 0, &din, &hin));
   TRY(stage_out(G, out, bytes, 1, &dout, &hout));
   if (din == dout) return fail(G, TOMO_EINVAL, "in and out overlap");
-  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps, (const T*)din,
+  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                      G->filter_radius, (const T*)din,
                       (const T*)G->Hs, (T*)dout, transpose ? 1 : 0, 0, T(0), T(0), T(0), T(0),
                       nullptr));
   G->launches += 1;
@@ -873,7 +874,8 @@ tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T
   T* rho = (T*)G->rho;
   TRY(pmark(G, 0));
   // S1: rho = P z, s = h (Emin + rho^p (E0 - Emin))
-  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps, (const T*)dz,
+  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                      G->filter_radius, (const T*)dz,
                       (const T*)G->Hs, rho, 0, 1, (T)d.E0, (T)d.Emin, (T)d.penal, (T)d.h,
                       (T*)G->L[0].s));
   G->launches += 1;
@@ -891,6 +893,7 @@ tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T
   TRY(pmark(G, 4));
   // S7: dc/dz = P^T dc/drho, dV/dz = P^T v
   CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                      G->filter_radius,
                       (const T*)G->dcp, (const T*)G->Hs, (T*)ddc, 1, 0, T(0), T(0), T(0), T(0),
                       nullptr));
   G->launches += 1;
@@ -998,8 +1001,6 @@ void free_grid(tomo_grid* G) {
   F(G->rho);
   F(G->dcp);
   F(G->s64);
-  F(G->x64);
-  F(G->r64);
   F(G->partials);
   F(G->counter);
   F(G->sc);
@@ -1086,8 +1087,6 @@ tomo_status create_impl(tomo_grid* G) {
   if (G->prec == TOMO_FP32) TRY(dalloc(G, &G->xlo, nv));
   if (G->prec == TOMO_FP32 && G->d.rr_every > 0) {
     TRY(dalloc(G, (void**)&G->s64, sizeof(double) * (size_t)g.nel));
-    TRY(dalloc(G, (void**)&G->x64, sizeof(double) * 3 * (size_t)g.nn));
-    TRY(dalloc(G, (void**)&G->r64, sizeof(double) * 3 * (size_t)g.nn));
   }
   TRY(dalloc(G, &G->rho, ne));
   TRY(dalloc(G, &G->dcp, ne));
@@ -1116,6 +1115,10 @@ tomo_status create_impl(tomo_grid* G) {
   // filter taps and weight sums
   G->taps = filter_taps(G->d.rmin);
   G->ntaps = (int)G->taps.size();
+  G->filter_radius = 0;
+  for (const auto& t : G->taps)
+    G->filter_radius = std::max(G->filter_radius,
+                                std::max(std::abs(t.di), std::max(std::abs(t.dj), std::abs(t.dk))));
   {
     std::vector<int4> t4(G->ntaps);
     std::vector<T> tw(G->ntaps);
@@ -1130,6 +1133,7 @@ tomo_status create_impl(tomo_grid* G) {
     std::vector<T> ones(g.nel, T(1));
     CK(cudaMemcpy(G->dcp, ones.data(), ne, cudaMemcpyHostToDevice));
     CK(launch_filter<T>(G->stream, g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                        G->filter_radius,
                         (const T*)G->dcp, nullptr, (T*)G->Hs, 2, 0, T(0), T(0), T(0), T(0),
                         nullptr));
     G->launches += 1;

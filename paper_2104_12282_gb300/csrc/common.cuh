@@ -115,6 +115,23 @@ inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// A thread's sum of FP32 terms kept as the unevaluated pair hi + lo (Knuth's TwoSum per
+// term): ~44 significant bits from FP32 arithmetic alone.  FP64 runs at 1/64 of the FP32
+// rate on this part, so accumulating every element in FP64 would bound the streaming
+// kernels; the pair becomes a double once per thread, before the grid reduction.  The rn
+// intrinsics keep nvcc from contracting the error terms.
+struct FloatPairSum {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -34,10 +34,116 @@ __global__ void k_filter(Geom g, const int4* __restrict__ taps, const T* __restr
   }
 }
 
+// Tiled form of the same filter for tap radius R <= 3: a CTA stages a 32 x 8 x 8 element
+// tile with an R-element halo in shared memory (mode 1 divides by Hs once per staged
+// element, not once per tap), builds the (2R+1)^3 weight table from the tap list, and each
+// thread accumulates a column of 8 outputs along z, reusing each staged column for all
+// (2R+1) z-offsets.  Elements outside the domain stage as 0 (the filter is truncated).
+constexpr int kFtX = 32, kFtY = 8, kFtZ = 8;
+
+template <typename T, int R, int MODE, bool MAT>
+__global__ void __launch_bounds__(kFtX * kFtY)
+    k_filter_tiled(Geom g, const int4* __restrict__ taps, const T* __restrict__ tapw, int ntaps,
+                   const T* __restrict__ in, const T* __restrict__ Hs, T* __restrict__ out,
+                   T E0, T Emin, T penal, T h, T* __restrict__ s_out) {
+  constexpr int W = 2 * R + 1;
+  constexpr int SX = kFtX + 2 * R, SY = kFtY + 2 * R, SZ = kFtZ + 2 * R;
+  __shared__ T tile[SZ][SY][SX];
+  __shared__ T wt[W * W * W];
+  PDL_ENTER();
+  const int tid = threadIdx.x + kFtX * threadIdx.y;
+  const int i0 = blockIdx.x * kFtX, j0 = blockIdx.y * kFtY, k0 = blockIdx.z * kFtZ;
+  for (int q = tid; q < W * W * W; q += kFtX * kFtY) wt[q] = T(0);
+  __syncthreads();
+  for (int t = tid; t < ntaps; t += kFtX * kFtY) {
+    const int4 d = taps[t];
+    wt[(d.z + R) * W * W + (d.y + R) * W + (d.x + R)] = tapw[t];
+  }
+  for (int q = tid; q < SX * SY * SZ; q += kFtX * kFtY) {
+    const int x = q % SX, y = (q / SX) % SY, z = q / (SX * SY);
+    const int i = i0 + x - R, j = j0 + y - R, k = k0 + z - R;
+    T v = T(0);
+    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) {
+      const int e = i + g.nx * (j + g.ny * k);
+      v = ldg(in + e);
+      if (MODE == 1) v = v / ldg(Hs + e);
+    }
+    tile[z][y][x] = v;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  T acc[kFtZ];
+#pragma unroll
+  for (int z = 0; z < kFtZ; ++z) acc[z] = T(0);
+#pragma unroll 1
+  for (int dj = 0; dj < W; ++dj) {
+#pragma unroll
+    for (int di = 0; di < W; ++di) {
+      T col[SZ];
+#pragma unroll
+      for (int z = 0; z < SZ; ++z) col[z] = tile[z][ty + dj][tx + di];
+#pragma unroll
+      for (int dk = 0; dk < W; ++dk) {
+        const T w = wt[dk * W * W + dj * W + di];
+#pragma unroll
+        for (int z = 0; z < kFtZ; ++z) acc[z] += w * col[z + dk];
+      }
+    }
+  }
+  const int i = i0 + tx, j = j0 + ty;
+  if (i >= g.nx || j >= g.ny) return;
+#pragma unroll
+  for (int z = 0; z < kFtZ; ++z) {
+    const int k = k0 + z;
+    if (k >= g.nz) break;
+    const int e = i + g.nx * (j + g.ny * k);
+    T v = acc[z];
+    if (MODE == 0) v = v / Hs[e];
+    out[e] = v;
+    if (MAT) s_out[e] = h * (Emin + pow(v, penal) * (E0 - Emin));
+  }
+}
+
+template <typename T, int R>
+bool launch_filter_tiled(cudaStream_t st, Geom g, const int4* taps, const T* tapw, int ntaps,
+                         const T* in, const T* Hs, T* out, int mode, int material, T E0,
+                         T Emin, T penal, T h, T* s_out) {
+  const dim3 grid((g.nx + kFtX - 1) / kFtX, (g.ny + kFtY - 1) / kFtY, (g.nz + kFtZ - 1) / kFtZ);
+  const dim3 block(kFtX, kFtY);
+  if (grid.y > 65535 || grid.z > 65535) return false;
+  if (mode == 0 && material)
+    pdl_launch(k_filter_tiled<T, R, 0, true>, grid, block, 0, st, g, taps, tapw, ntaps, in, Hs,
+               out, E0, Emin, penal, h, s_out);
+  else if (mode == 0)
+    pdl_launch(k_filter_tiled<T, R, 0, false>, grid, block, 0, st, g, taps, tapw, ntaps, in, Hs,
+               out, E0, Emin, penal, h, s_out);
+  else if (mode == 1)
+    pdl_launch(k_filter_tiled<T, R, 1, false>, grid, block, 0, st, g, taps, tapw, ntaps, in, Hs,
+               out, E0, Emin, penal, h, s_out);
+  else
+    pdl_launch(k_filter_tiled<T, R, 2, false>, grid, block, 0, st, g, taps, tapw, ntaps, in, Hs,
+               out, E0, Emin, penal, h, s_out);
+  return true;
+}
+
 template <typename T>
 cudaError_t launch_filter(cudaStream_t st, Geom g, const int4* taps, const T* tapw, int ntaps,
-                          const T* in, const T* Hs, T* out, int mode, int material, T E0,
-                          T Emin, T penal, T h, T* s_out) {
+                          int radius, const T* in, const T* Hs, T* out, int mode, int material,
+                          T E0, T Emin, T penal, T h, T* s_out) {
+  bool done = false;
+  if (radius == 0)
+    done = launch_filter_tiled<T, 0>(st, g, taps, tapw, ntaps, in, Hs, out, mode, material, E0,
+                                     Emin, penal, h, s_out);
+  else if (radius == 1)
+    done = launch_filter_tiled<T, 1>(st, g, taps, tapw, ntaps, in, Hs, out, mode, material, E0,
+                                     Emin, penal, h, s_out);
+  else if (radius == 2)
+    done = launch_filter_tiled<T, 2>(st, g, taps, tapw, ntaps, in, Hs, out, mode, material, E0,
+                                     Emin, penal, h, s_out);
+  else if (radius == 3 && sizeof(T) == 4)
+    done = launch_filter_tiled<T, 3>(st, g, taps, tapw, ntaps, in, Hs, out, mode, material, E0,
+                                     Emin, penal, h, s_out);
+  if (done) return cudaGetLastError();
   int blocks = (g.nel + 255) / 256;
   if (blocks > 16384) blocks = 16384;
   if (mode == 0 && material)
@@ -380,7 +486,7 @@ int oc_max_blocks(int n) {
 }
 
 #define INST(T)                                                                                \
-  template cudaError_t launch_filter<T>(cudaStream_t, Geom, const int4*, const T*, int,        \
+  template cudaError_t launch_filter<T>(cudaStream_t, Geom, const int4*, const T*, int, int,   \
                                         const T*, const T*, T*, int, int, T, T, T, T, T*);     \
   template cudaError_t launch_material<T>(cudaStream_t, int, const T*, T, T, T, T, T*);       \
   template cudaError_t launch_sensitivity<T>(cudaStream_t, Geom, const T*, const T*, const T*, \

@@ -57,6 +57,11 @@ struct MarchArgs {
   const int* skip;      // if non-null and *skip != 0 the kernel returns at once
   const CgScalars* gate;  // residual replacement: run only when gate->it % gate->rr_every == 0
   int xprev_zero;       // CHEB: the previous iterate is zero (first step after a zero start)
+  // T = double, RESID only: the input is the float pair (xf_hi, xf_lo), joined exactly into
+  // double on load, and the residual is written rounded to float into yf
+  const float* xf_hi;
+  const float* xf_lo;
+  float* yf;
 };
 
 // FP32 two-rows-per-thread product (matvec2.cu); same modes as k_march, no pair input.
@@ -131,8 +136,8 @@ cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo,
 // Filter, material, sensitivity, OC.
 template <typename T>
 cudaError_t launch_filter(cudaStream_t st, Geom g, const int4* taps, const T* tapw, int ntaps,
-                          const T* in, const T* Hs, T* out, int mode, int material, T E0,
-                          T Emin, T penal, T h, T* s_out);
+                          int radius, const T* in, const T* Hs, T* out, int mode, int material,
+                          T E0, T Emin, T penal, T h, T* s_out);
 template <typename T>
 cudaError_t launch_material(cudaStream_t st, int n, const T* rho, T E0, T Emin, T penal, T h,
                             T* s);
@@ -189,6 +194,7 @@ struct tomo_grid {
   bool dvdz_ready = false;
   std::vector<tomo_level> L;
   int coarse_n = 0;            // coarsest DOFs (dense)
+  int filter_radius = 0;       // largest |offset| component of the filter taps
   void* coarseA = nullptr;     // T[n*n]
   void* coarseD = nullptr;     // T[n]
   // fine-level vectors
@@ -235,6 +241,4 @@ struct tomo_grid {
   int64_t iter_launches = 0;        // kernels in one captured loop body
   // FP64 residual replacement of FP32 grids: r = f - K(x_hi + x_lo) evaluated in FP64
   double* s64 = nullptr;            // h*E at the fine level, double
-  double* x64 = nullptr;            // iterate, double
-  double* r64 = nullptr;            // residual, double
 };

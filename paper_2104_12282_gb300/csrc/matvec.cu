@@ -102,7 +102,11 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
   const int ecol = el_col ? i + g.nx * j : 0;
   const int eplane = g.nx * g.ny;
 
-  constexpr int NA = PAIR ? 6 : 3;
+  // PAIR with T = float: the input pair is carried as two arrays and differenced separately;
+  // PAIR with T = double: the float pair is joined into one double on load (exact: 48 bits)
+  constexpr bool SPLIT = PAIR && sizeof(T) == 4;
+  constexpr bool JOIN = PAIR && sizeof(T) == 8;
+  constexpr int NA = SPLIT ? 6 : 3;
   __shared__ T sA[NA][kTY][32];
   __shared__ T sG[6][kTY][32];
   __shared__ T sS[kTY][32];
@@ -114,8 +118,12 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
       const int n = colbase + plane * k;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        v[c] = ldg(A.x + (size_t)c * nn + n);
-        if (PAIR) v[3 + c] = ldg(A.xlo + (size_t)c * nn + n);
+        if constexpr (JOIN) {
+          v[c] = (T)__ldg(A.xf_hi + (size_t)c * nn + n) + (T)__ldg(A.xf_lo + (size_t)c * nn + n);
+        } else {
+          v[c] = ldg(A.x + (size_t)c * nn + n);
+          if constexpr (SPLIT) v[3 + c] = ldg(A.xlo + (size_t)c * nn + n);
+        }
       }
     }
   };
@@ -191,7 +199,7 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
       v[5] = c1v - a0;
       v[6] = B1[c] - a0;
       v[7] = d1 - a0;
-      if (PAIR) {
+      if constexpr (SPLIT) {
         const T al = A0[3 + c];
         const T cl0 = __shfl_down_sync(0xffffffffu, A0[3 + c], 1);
         const T cl1 = __shfl_down_sync(0xffffffffu, A1[3 + c], 1);
@@ -269,7 +277,9 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
           A.y[idx] = yv;
           if (DOT) dot += (double)(A0[c] * yv);
         } else if (MODE == M_RESID) {
-          A.y[idx] = fx ? T(0) : (bv[c] - out[c]);
+          const T rv = fx ? T(0) : (bv[c] - out[c]);
+          if constexpr (JOIN) A.yf[idx] = (float)rv;
+          else A.y[idx] = rv;
         } else {
           const T dg = C.k0diag * Stot;
           const T w = dg > T(0) ? (bv[c] - out[c]) / dg : T(0);
@@ -333,20 +343,14 @@ cudaError_t launch_march(cudaStream_t st, int mode, const MarchArgs<T>& a, const
   args.kz = kz;
   dim3 grid(gx, gy, nzc), block(32, kTY);
   if (grid_ctas) *grid_ctas = gx * gy * nzc;
-  const bool pair = a.xlo != nullptr;
+  const bool pair = sizeof(T) == 4 ? a.xlo != nullptr : a.xf_hi != nullptr;
   const bool dot = a.dot_kind != 0;
   if (mode == M_APPLY) {
     if (dot) pdl_launch(k_march<T, M_APPLY, false, true>, grid, block, 0, st, args, c);
     else pdl_launch(k_march<T, M_APPLY, false, false>, grid, block, 0, st, args, c);
   } else if (mode == M_RESID) {
-    if constexpr (sizeof(T) == 4) {
-      if (pair) {
-        pdl_launch(k_march<T, M_RESID, true, false>, grid, block, 0, st, args, c);
-        return cudaGetLastError();
-      }
-    }
-    if (pair) return cudaErrorInvalidValue;
-    pdl_launch(k_march<T, M_RESID, false, false>, grid, block, 0, st, args, c);
+    if (pair) pdl_launch(k_march<T, M_RESID, true, false>, grid, block, 0, st, args, c);
+    else pdl_launch(k_march<T, M_RESID, false, false>, grid, block, 0, st, args, c);
   } else {
     if (dot) pdl_launch(k_march<T, M_CHEB, false, true>, grid, block, 0, st, args, c);
     else pdl_launch(k_march<T, M_CHEB, false, false>, grid, block, 0, st, args, c);

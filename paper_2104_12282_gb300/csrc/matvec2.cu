@@ -23,6 +23,10 @@ namespace tomo {
 namespace {
 
 constexpr int TYP = 8;            // thread rows per CTA (two node rows each)
+// resident CTAs per SM the register allocation aims at (2: 128 registers, no spills)
+#ifndef TOMO_MARCH2_MIN_BLOCKS
+#define TOMO_MARCH2_MIN_BLOCKS 2
+#endif
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -42,7 +46,7 @@ __device__ __forceinline__ float2 shup2(float2 v) {
 }
 
 template <int MODE, bool DOT>
-__global__ void __launch_bounds__(32 * TYP, 2)
+__global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
     k_march2(const __grid_constant__ March2Args A, const __grid_constant__ March2Const K) {
   PDL_ENTER();
   if (A.skip != nullptr && *A.skip) return;
@@ -105,7 +109,9 @@ __global__ void __launch_bounds__(32 * TYP, 2)
 
   float2 carry[3] = {bc2(0.0f), bc2(0.0f), bc2(0.0f)};
   float2 carryS = bc2(0.0f);
-  double dot = 0.0;
+  // fused inner product: per step the three components are summed in FP32, then added to
+  // the pair dhi + dlo with TwoSum (FP64 runs at 1/64 of the FP32 rate on this part)
+  float2 dhi = bc2(0.0f), dlo = bc2(0.0f);
 
   for (int k = kb - 1; k < ke; ++k) {
     float2 A1[3];
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(32 * TYP, 2)
         inv.x = Stot.x > 0.0f ? 1.0f / (K.k0diag * Stot.x) : 0.0f;
         inv.y = Stot.y > 0.0f ? 1.0f / (K.k0diag * Stot.y) : 0.0f;
       }
+      float2 pc = bc2(0.0f);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         float2 v;
@@ -313,9 +320,15 @@ __global__ void __launch_bounds__(32 * TYP, 2)
         if (w1) dst[(size_t)c * nn + n1] = v.y;
         if (DOT) {
           const float2 d2 = (MODE == M_APPLY) ? A0[c] : bv[c];
-          if (w0) dot += (double)(d2.x * v.x);
-          if (w1) dot += (double)(d2.y * v.y);
+          pc = fma2(make_float2(w0 ? d2.x : 0.0f, w1 ? d2.y : 0.0f), v, pc);
         }
+      }
+      if (DOT) {
+        const float2 s = add2(dhi, pc);
+        const float2 bb = sub2(s, dhi);
+        const float2 err = add2(sub2(dhi, sub2(s, bb)), sub2(pc, bb));
+        dhi = s;
+        dlo = add2(dlo, err);
       }
     }
 #pragma unroll
@@ -327,7 +340,7 @@ __global__ void __launch_bounds__(32 * TYP, 2)
     }
   }
   if (DOT) {
-    double v[1] = {dot};
+    double v[1] = {((double)dhi.x + (double)dlo.x) + ((double)dhi.y + (double)dlo.y)};
     CgScalars* sc = A.sc;
     const int kind = A.dot_kind;
     grid_reduce<1>(v, A.partials, A.counter, [sc, kind](const double* tot) {

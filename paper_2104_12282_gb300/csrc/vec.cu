@@ -23,20 +23,20 @@ __global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restr
                          const int* skip) {
   PDL_ENTER();
   if (skipped(skip)) return;
-  double dot = 0.0;
+  double dot = 0.0;       // FP64 grids
+  FloatPairSum dotf;      // FP32 grids
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nn; n += gridDim.x * blockDim.x) {
     const int i = n % g.nxn, j = (n / g.nxn) % g.nyn, k = n / (g.nxn * g.nyn);
-    T S = T(0);
-#pragma unroll
-    for (int dz = -1; dz <= 0; ++dz)
-#pragma unroll
-      for (int dy = -1; dy <= 0; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 0; ++dx) {
-          const int ei = i + dx, ej = j + dy, ek = k + dz;
-          if (ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny && ek >= 0 && ek < g.nz)
-            S += s[ei + g.nx * (ej + g.ny * ek)];
-        }
+    // the (up to) eight elements around the node: indices clamped, absent ones weighted 0
+    const int xa = max(i - 1, 0), xb = min(i, g.nx - 1);
+    const int ya = g.nx * max(j - 1, 0), yb = g.nx * min(j, g.ny - 1);
+    const int za = g.nx * g.ny * max(k - 1, 0), zb = g.nx * g.ny * min(k, g.nz - 1);
+    const T wxa = i > 0 ? T(1) : T(0), wxb = i < g.nx ? T(1) : T(0);
+    const T wya = j > 0 ? T(1) : T(0), wyb = j < g.ny ? T(1) : T(0);
+    const T wza = k > 0 ? T(1) : T(0), wzb = k < g.nz ? T(1) : T(0);
+    auto row = [&](int off) { return wxa * s[off + xa] + wxb * s[off + xb]; };
+    const T S = wza * (wya * row(za + ya) + wyb * row(za + yb)) +
+                wzb * (wya * row(zb + ya) + wyb * row(zb + yb));
     const T dg = k0diag * S;
     const unsigned mk = mask[n];
 #pragma unroll
@@ -46,10 +46,14 @@ __global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restr
       const T v = (((mk >> c) & 1u) || !(dg > T(0))) ? T(0) : c2 * bv / dg;
       x1[idx] = v;
       if (x0) x0[idx] = T(0);
-      if (DOT) dot += (double)(bv * v);
+      if (DOT) {
+        if constexpr (sizeof(T) == 4) dotf.add(__fmul_rn(bv, v));
+        else dot += bv * v;
+      }
     }
   }
   if (DOT) {
+    if constexpr (sizeof(T) == 4) dot = dotf.value();
     double v[1] = {dot};
     grid_reduce<1>(v, partials, counter, [sc](const double* tot) {
       sc->rz_new = tot[0];
@@ -91,23 +95,35 @@ __global__ void k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __rest
   if (skipped(skip)) return;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gc.nn; n += gridDim.x * blockDim.x) {
     const int I = n % gc.nxn, J = (n / gc.nxn) % gc.nyn, K = n / (gc.nxn * gc.nyn);
-    T acc[3] = {T(0), T(0), T(0)};
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int k = 2 * K + dz;
-      if (k < 0 || k >= gf.nzn) continue;
-      const T wz = dz == 0 ? T(1) : T(0.5);
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int j = 2 * J + dy;
-        if (j < 0 || j >= gf.nyn) continue;
-        const T wy = dy == 0 ? wz : T(0.5) * wz;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int i = 2 * I + dx;
-          if (i < 0 || i >= gf.nxn) continue;
-          const T w = dx == 0 ? wy : T(0.5) * wy;
-          const int m = i + gf.nxn * (j + gf.nyn * k);
+    // fine indices 2I-1, 2I, 2I+1 per axis with weights 1/2, 1, 1/2; indices outside the
+    // fine grid are clamped and weighted 0 (same code path for every node)
+    int ix[3], iy[3], iz[3];
+    T wx[3], wy[3], wz[3];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) acc[c] += w * rf[(size_t)c * gf.nn + m];
+    for (int d = 0; d < 3; ++d) {
+      const int a = 2 * I + d - 1, b = 2 * J + d - 1, e = 2 * K + d - 1;
+      const T w = d == 1 ? T(1) : T(0.5);
+      wx[d] = (a >= 0 && a < gf.nxn) ? w : T(0);
+      wy[d] = (b >= 0 && b < gf.nyn) ? w : T(0);
+      wz[d] = (e >= 0 && e < gf.nzn) ? w : T(0);
+      ix[d] = min(max(a, 0), gf.nxn - 1);
+      iy[d] = gf.nxn * min(max(b, 0), gf.nyn - 1);
+      iz[d] = gf.nxn * gf.nyn * min(max(e, 0), gf.nzn - 1);
+    }
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* v = rf + (size_t)c * gf.nn;
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz) {
+        T az = T(0);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const int row = iz[dz] + iy[dy];
+          const T ay = wx[0] * v[row + ix[0]] + wx[1] * v[row + ix[1]] + wx[2] * v[row + ix[2]];
+          az += wy[dy] * ay;
         }
+        acc[c] += wz[dz] * az;
       }
     }
     const unsigned mk = mask_c[n];
@@ -140,7 +156,9 @@ cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* r
   return cudaGetLastError();
 }
 
-// x_f += P x_c (trilinear interpolation), masked on the fine grid.
+// x_f += P x_c (trilinear interpolation), masked on the fine grid.  Every fine node takes
+// the same 2x2x2 form (an even index uses one coarse node with weights 1 and 0), so the
+// warp does not diverge on index parity.
 template <typename T>
 __global__ void k_prolong_add(Geom gf, Geom gc, const T* __restrict__ xc, T* __restrict__ xf,
                               const uint8_t* __restrict__ mask_f, const int* skip) {
@@ -151,24 +169,21 @@ __global__ void k_prolong_add(Geom gf, Geom gc, const T* __restrict__ xc, T* __r
     const int i0 = i >> 1, i1 = (i + 1) >> 1;
     const int j0 = j >> 1, j1 = (j + 1) >> 1;
     const int k0 = k >> 1, k1 = (k + 1) >> 1;
-    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
+    const T h = T(0.5);
+    const T wi0 = (i & 1) ? h : T(1), wi1 = (i & 1) ? h : T(0);
+    const T wj0 = (j & 1) ? h : T(1), wj1 = (j & 1) ? h : T(0);
+    const T wk0 = (k & 1) ? h : T(1), wk1 = (k & 1) ? h : T(0);
+    const int r00 = gc.nxn * (j0 + gc.nyn * k0), r10 = gc.nxn * (j1 + gc.nyn * k0);
+    const int r01 = gc.nxn * (j0 + gc.nyn * k1), r11 = gc.nxn * (j1 + gc.nyn * k1);
     const unsigned mk = mask_f[n];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T* v = xc + (size_t)c * gc.nn;
-      T acc;
-      auto at = [&](int a, int b2, int d) { return v[a + gc.nxn * (b2 + gc.nyn * d)]; };
-      if ((i & 1) == 0 && (j & 1) == 0 && (k & 1) == 0) {
-        acc = at(i0, j0, k0);
-      } else {
-        acc = T(0);
-        const int ii[2] = {i0, i1}, jj[2] = {j0, j1}, kk[2] = {k0, k1};
-        const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-        for (int c3 = 0; c3 < nk; ++c3)
-          for (int b3 = 0; b3 < nj; ++b3)
-            for (int a3 = 0; a3 < ni; ++a3) acc += at(ii[a3], jj[b3], kk[c3]);
-        acc *= wi * wj * wk;
-      }
+      const T a00 = wi0 * v[r00 + i0] + wi1 * v[r00 + i1];
+      const T a10 = wi0 * v[r10 + i0] + wi1 * v[r10 + i1];
+      const T a01 = wi0 * v[r01 + i0] + wi1 * v[r01 + i1];
+      const T a11 = wi0 * v[r11 + i0] + wi1 * v[r11 + i1];
+      const T acc = wk0 * (wj0 * a00 + wj1 * a10) + wk1 * (wj0 * a01 + wj1 * a11);
       const size_t idx = (size_t)c * gf.nn + n;
       if (!((mk >> c) & 1u)) xf[idx] += acc;
     }
@@ -225,9 +240,8 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(Geom g, const T* __restr
   const int n = 3 * g.nn;
   const int tid = threadIdx.x, nt = blockDim.x;
   extern __shared__ unsigned char smem_raw[];
-  T* col = reinterpret_cast<T*>(smem_raw);
-  T* M = SMEM ? col + n : A;  // the working matrix: shared memory when it fits
-  __shared__ T s_piv;
+  T* col = reinterpret_cast<T*>(smem_raw);  // 4n: pivot column and row snapshots
+  T* M = SMEM ? col + 4 * n : A;            // the working matrix: shared memory when it fits
   for (int q = tid; q < n * n; q += nt) M[q] = T(0);
   __syncthreads();
   for (int e = 0; e < g.nel; ++e) {
@@ -260,30 +274,45 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(Geom g, const T* __restr
     M[q] *= dscale[a] * dscale[b];
   }
   __syncthreads();
-  // in-place Gauss-Jordan inversion of the scaled SPD matrix (no pivoting)
+  // In-place Gauss-Jordan inversion of the scaled SPD matrix (no pivoting).  Each thread
+  // owns the entries of one column j at rows i0, i0 + R, ...; pivot step k needs column k
+  // and row k as they were before the step, which the owners of column k+1 and row k+1
+  // write into the other half of a double buffer while updating, so one barrier per step.
+  T* colb = col;          // [2][n] snapshots of the pivot column
+  T* rowb = col + 2 * n;  // [2][n] snapshots of the pivot row
+  const int R = nt / n > 0 ? nt / n : 1;
+  const bool own = tid < R * n;
+  const int j = own ? tid % n : 0, i0 = own ? tid / n : 0;
+  if (own)
+    for (int i = i0; i < n; i += R) {
+      const T v = M[(size_t)i * n + j];
+      if (j == 0) colb[i] = v;
+      if (i == 0) rowb[j] = v;
+    }
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
-    for (int i = tid; i < n; i += nt) col[i] = M[(size_t)i * n + k];
-    __syncthreads();
-    if (tid == 0) {
-      T p = col[k];
-      if (!(p > T(0))) {
-        atomicOr(status, DEV_BREAKDOWN);
-        p = T(1);
+    const T* cs = colb + (k & 1) * n;
+    const T* rs = rowb + (k & 1) * n;
+    T* cn = colb + ((k + 1) & 1) * n;
+    T* rn = rowb + ((k + 1) & 1) * n;
+    T p = rs[k];
+    if (!(p > T(0))) {
+      if (tid == 0) atomicOr(status, DEV_BREAKDOWN);
+      p = T(1);
+    }
+    const T ip = T(1) / p;
+    if (own) {
+      const T rj = (j == k) ? T(1) : rs[j] * ip;
+      for (int i = i0; i < n; i += R) {
+        const size_t q = (size_t)i * n + j;
+        T v;
+        if (i == k) v = (j == k) ? ip : rj;
+        else if (j == k) v = -cs[i] * ip;
+        else v = M[q] - cs[i] * rj;
+        M[q] = v;
+        if (j == k + 1) cn[i] = v;
+        if (i == k + 1) rn[j] = v;
       }
-      s_piv = T(1) / p;
-    }
-    __syncthreads();
-    const T ip = s_piv;
-    for (int jcol = tid; jcol < n; jcol += nt) {
-      const T v = (jcol == k) ? T(1) : M[(size_t)k * n + jcol];
-      M[(size_t)k * n + jcol] = v * ip;
-    }
-    __syncthreads();
-    for (int q = tid; q < n * n; q += nt) {
-      const int i = q / n, jcol = q % n;
-      if (i == k) continue;
-      const T v = (jcol == k) ? T(0) : M[q];
-      M[q] = v - col[i] * M[(size_t)k * n + jcol];
     }
     __syncthreads();
   }
@@ -295,7 +324,7 @@ template <typename T>
 cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint8_t* mask,
                                  const DenseK0<T>& K0, T* A, T* dscale, unsigned* status) {
   const int n = 3 * g.nn;
-  const size_t full = sizeof(T) * ((size_t)n * n + n);
+  const size_t full = sizeof(T) * ((size_t)n * n + 4 * n);
   if (full <= 200 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_coarse_factor<T, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -303,7 +332,7 @@ cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint
     if (e != cudaSuccess) return e;
     pdl_launch(k_coarse_factor<T, true>, 1, 1024, full, st, g, s, mask, K0, A, dscale, status);
   } else {
-    pdl_launch(k_coarse_factor<T, false>, 1, 1024, sizeof(T) * (size_t)n, st, g, s, mask, K0, A, dscale,
+    pdl_launch(k_coarse_factor<T, false>, 1, 1024, sizeof(T) * 4 * (size_t)n, st, g, s, mask, K0, A, dscale,
                                                                       status);
   }
   return cudaGetLastError();
@@ -348,6 +377,21 @@ cudaError_t launch_coarse_apply(cudaStream_t st, int n, const T* Ainv, const T* 
 // With xlo the iterate is the unevaluated pair xhi + xlo (float): the product alpha*p is
 // formed exactly as prod + err (FMA) and added with TwoSum, so the pair keeps ~48 bits.
 // ---------------------------------------------------------------------------------------
+// x (+)= alpha p as the float pair (hi, lo): the product alpha*p is formed exactly as
+// prod + perr (FMA) and added to hi with TwoSum; the rn intrinsics keep the compiler from
+// contracting these steps into FMAs (that would break the error terms)
+__device__ __forceinline__ void pair_axpy(float alpha, float pv, float& hi, float& lo) {
+  const float prod = __fmul_rn(alpha, pv);
+  const float perr = __fmaf_rn(alpha, pv, -prod);
+  const float s = __fadd_rn(hi, prod);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
+  const float l2 = __fadd_rn(__fadd_rn(lo, err), perr);
+  const float hi2 = __fadd_rn(s, l2);
+  lo = __fsub_rn(l2, __fsub_rn(hi2, s));
+  hi = hi2;
+}
+
 template <typename T, bool PAIRX>
 __global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __restrict__ r,
                         const T* __restrict__ p, const T* __restrict__ q, double* partials,
@@ -356,29 +400,60 @@ __global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __re
   if (sc->done) return;
   const double alpha_d = sc->alpha;
   const T alpha = (T)alpha_d;
-  double acc = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  double acc = 0.0;      // FP64 grids
+  FloatPairSum accf;     // FP32 grids
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  int i0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    // float4 body: 16-byte accesses keep enough bytes in flight to stream at HBM rate
+    const int n4 = n >> 2;
+    for (int v = tid; v < n4; v += nt) {
+      const float4 pv = reinterpret_cast<const float4*>(p)[v];
+      const float4 qv = reinterpret_cast<const float4*>(q)[v];
+      float4 rv = reinterpret_cast<const float4*>(r)[v];
+      float4 hv = reinterpret_cast<const float4*>(xhi)[v];
+      if constexpr (PAIRX) {
+        float4 lv = reinterpret_cast<const float4*>(xlo)[v];
+        pair_axpy(alpha, pv.x, hv.x, lv.x);
+        pair_axpy(alpha, pv.y, hv.y, lv.y);
+        pair_axpy(alpha, pv.z, hv.z, lv.z);
+        pair_axpy(alpha, pv.w, hv.w, lv.w);
+        reinterpret_cast<float4*>(xlo)[v] = lv;
+      } else {
+        hv.x += alpha * pv.x;
+        hv.y += alpha * pv.y;
+        hv.z += alpha * pv.z;
+        hv.w += alpha * pv.w;
+      }
+      reinterpret_cast<float4*>(xhi)[v] = hv;
+      rv.x = rv.x - alpha * qv.x;
+      rv.y = rv.y - alpha * qv.y;
+      rv.z = rv.z - alpha * qv.z;
+      rv.w = rv.w - alpha * qv.w;
+      reinterpret_cast<float4*>(r)[v] = rv;
+      accf.add(__fmul_rn(rv.x, rv.x));
+      accf.add(__fmul_rn(rv.y, rv.y));
+      accf.add(__fmul_rn(rv.z, rv.z));
+      accf.add(__fmul_rn(rv.w, rv.w));
+    }
+    i0 = n4 << 2;
+  }
+  for (int i = i0 + tid; i < n; i += nt) {
     const T pv = p[i];
     if constexpr (PAIRX) {
-      // exact product prod + perr, then TwoSum(hi, prod); the rn intrinsics keep the
-      // compiler from contracting these steps into FMAs (that would break the error terms)
-      const float prod = __fmul_rn(alpha, pv);
-      const float perr = __fmaf_rn(alpha, pv, -prod);
-      const float a = xhi[i];
-      const float s = __fadd_rn(a, prod);
-      const float bb = __fsub_rn(s, a);
-      const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
-      const float lo = __fadd_rn(__fadd_rn(xlo[i], err), perr);
-      const float hi2 = __fadd_rn(s, lo);
-      xlo[i] = __fsub_rn(lo, __fsub_rn(hi2, s));
-      xhi[i] = hi2;
+      float hi = xhi[i], lo = xlo[i];
+      pair_axpy(alpha, pv, hi, lo);
+      xhi[i] = hi;
+      xlo[i] = lo;
     } else {
       xhi[i] += alpha * pv;
     }
     const T rv = r[i] - alpha * q[i];
     r[i] = rv;
-    acc += (double)(rv * rv);
+    if constexpr (sizeof(T) == 4) accf.add(__fmul_rn(rv, rv));
+    else acc += rv * rv;
   }
+  if constexpr (sizeof(T) == 4) acc = accf.value();
   double v[1] = {acc};
   grid_reduce<1>(v, partials, counter, [sc](const double* tot) {
     sc->rr = tot[0];
@@ -425,8 +500,22 @@ __global__ void k_cg_p(int n, T* __restrict__ p, const T* __restrict__ z, CgScal
   PDL_ENTER();
   if (sc->done) return;
   const T beta = (T)sc->beta;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  int i0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    const int n4 = n >> 2;
+    for (int v = tid; v < n4; v += nt) {
+      const float4 zv = reinterpret_cast<const float4*>(z)[v];
+      float4 pv = reinterpret_cast<const float4*>(p)[v];
+      pv.x = zv.x + beta * pv.x;
+      pv.y = zv.y + beta * pv.y;
+      pv.z = zv.z + beta * pv.z;
+      pv.w = zv.w + beta * pv.w;
+      reinterpret_cast<float4*>(p)[v] = pv;
+    }
+    i0 = n4 << 2;
+  }
+  for (int i = i0 + tid; i < n; i += nt) p[i] = z[i] + beta * p[i];
 }
 
 template <typename T>
