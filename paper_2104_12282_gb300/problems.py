@@ -129,6 +129,25 @@ def mbb_block(nx: int, ny: int, nz: int, *, h: float = 1.0, volfrac: float = 0.1
     return Problem("mbb_block", d, h, E0, Emin, nu, penal, rmin, volfrac, fixed, f, move, z0)
 
 
+def coarse_problem(p: Problem, nb: int) -> Problem:
+    """The same problem (supports, load, material) on the coarse grid of the two-scale
+    scheme: ceil(n / N_B) elements per axis of edge N_B h.  Only the cantilever and the
+    MBB-type block are defined here; their loads are resolution independent (total 1)."""
+    d = p.dims
+    dims = (-(-d.nx // nb), -(-d.ny // nb), -(-d.nz // nb))
+    kw = dict(h=p.h * nb, volfrac=p.volfrac, rmin=p.rmin, E0=p.E0, Emin=p.Emin, nu=p.nu,
+              penal=p.penal, move=p.move)
+    if p.name == "cantilever":
+        q = cantilever(*dims, **kw)
+    elif p.name == "mbb_block":
+        q = mbb_block(*dims, **kw)
+    else:
+        raise ValueError(f"no coarse definition for problem {p.name!r}")
+    q.meta["block_size"] = nb
+    q.meta["fine"] = (d.nx, d.ny, d.nz)
+    return q
+
+
 def bumpy_field(d: GridDims, seed: int, *, lo: float = 0.05, hi: float = 1.0,
                 n_bumps: int = 8, amp: float = 0.3, sigma=(4.0, 16.0)) -> np.ndarray:
     """Design field: U[lo, hi] noise plus smooth Gaussian bumps, clipped to [lo, hi].
