@@ -54,6 +54,8 @@ def _shift_accumulate(nx, ny, nz, x, rmin):
     X = x.reshape(nz, ny, nx)
     out = np.zeros_like(X)
     for di, dj, dk, w in stencil_offsets(rmin):
+        if abs(di) >= nx or abs(dj) >= ny or abs(dk) >= nz:
+            continue  # no pair of in-domain elements at this offset
         # out[k, j, i] += w * X[k+dk, j+dj, i+di] where in range
         ks = slice(max(0, -dk), nz - max(0, dk))
         js = slice(max(0, -dj), ny - max(0, dj))

@@ -41,8 +41,9 @@ def test_rows_sum_to_one_and_identity_below_one():
     assert np.abs(filt.filter_forward(nx, ny, nz, 0.7, z) - z).max() <= 2e-16
 
 
-@pytest.mark.parametrize("rmin", [1.5, 2.5])
+@pytest.mark.parametrize("rmin", [1.5, 2.5, 5.5, 7.2])
 def test_forward_and_transpose_against_dense(rmin):
+    """Includes radii whose offsets exceed the grid (7 x 4 x 3 with rmin 5.5, 7.2)."""
     nx, ny, nz = 7, 4, 3
     H, Hs = filt.filter_matrix(nx, ny, nz, rmin)
     Pd = H.toarray() / Hs[:, None]
