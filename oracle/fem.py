@@ -136,6 +136,14 @@ def diagonal_elementwise(nx: int, ny: int, nz: int, Ee: np.ndarray, h: float, K0
     return np.bincount(edof.ravel(), weights=de.ravel(), minlength=ndof)
 
 
+def element_bilinear(nx: int, ny: int, nz: int, w: np.ndarray, u: np.ndarray, K0: np.ndarray,
+                     edof: np.ndarray | None = None) -> np.ndarray:
+    """w_e^T K0 u_e per element (unit modulus, unit size)."""
+    if edof is None:
+        edof = element_dofs(nx, ny, nz)
+    return np.einsum("ei,ij,ej->e", w[edof], K0, u[edof])
+
+
 def element_energy(nx: int, ny: int, nz: int, u: np.ndarray, K0: np.ndarray,
                    edof: np.ndarray | None = None) -> np.ndarray:
     """u_e^T K0 u_e per element (unit modulus, unit size)."""

@@ -7,6 +7,9 @@ infrastructure).
   is dc/drho_e = -p rho_e^(p-1) (E0 - Emin) h u_e^T K0 u_e.
 * Through the filter rho = P z: dc/dz = P^T dc/drho and dV/dz = P^T v (§III-D), v_e = h^3.
 * Loop (Algorithm 1 with every iteration exact): filter, solve, gradient, OC update.
+* General objective (Eq. 3): for J = l^T u (a linear functional of the state, dJ/dz = 0
+  explicitly), the adjoint lambda solves (dr/du)^T lambda = dJ/du, i.e. K lambda = l
+  (K symmetric), and g_i = -lambda^T (dK/dz_i) u; compliance is the case l = f, lambda = u.
 """
 from __future__ import annotations
 
@@ -80,6 +83,23 @@ class Model:
         dc = self.sensitivity(rho, u)
         return dict(rho=rho, E=E, u=u, c=c, dc_drho=dc, dcdz=self.filter_T(dc),
                     dvdz=self.filter_T(self.v), iters=it, rel_res=rel)
+
+    def adjoint_gradient(self, z, l, method="auto", tol=1e-12):
+        """Eq. 3 for J = l^T u: returns a dict with J, u, lam, dJ_drho, dJdz."""
+        rho = self.filter(z)
+        E = self.modulus(rho)
+        u, _, _ = self.solve(E, method, tol)
+        l = np.where(self.fixed, 0.0, np.asarray(l, np.float64))
+        saved = self.p.f
+        try:
+            self.p.f = l
+            lam, _, _ = self.solve(E, method, tol)
+        finally:
+            self.p.f = saved
+        p = self.p
+        be = fem.element_bilinear(self.nx, self.ny, self.nz, lam, u, self.K0, self.edof)
+        dj = -p.penal * np.power(rho, p.penal - 1.0) * (p.E0 - p.Emin) * p.h * be
+        return dict(J=float(l @ u), u=u, lam=lam, dJ_drho=dj, dJdz=self.filter_T(dj))
 
     def vmax(self):
         return self.p.volfrac * float(np.sum(self.v))
