@@ -49,6 +49,7 @@ extern "C" {
 #endif
 
 typedef struct tomo_grid tomo_grid; /* opaque, owned by the library */
+typedef struct tomo_batch tomo_batch; /* opaque: a set of grids evaluated together */
 
 typedef enum {
   TOMO_OK = 0,
@@ -118,6 +119,19 @@ tomo_status tomo_set_stream(tomo_grid* grid, void* stream);
  * element arrays; they must not overlap. */
 tomo_status tomo_filter(tomo_grid* grid, const float* in, float* out, int transpose);
 tomo_status tomo_filter_d(tomo_grid* grid, const double* in, double* out, int transpose);
+
+/* Two-scale coarse-graining (Section III-C; Algorithm 1, first step of every iteration):
+ * z_coarse[I + cx (J + cy K)] = mean of z over the block of elements
+ * [I*block, (I+1)*block) x [J*block, ...) x [K*block, ...), with cx = ceil(nx / block),
+ * cy = ceil(ny / block), cz = ceil(nz / block); a block cut by the domain boundary averages
+ * the elements it holds.  The coarse state of Algorithm 1 (K_C(z_C) u_C = f_C) is a
+ * tomo_solve on a grid created for the coarse mesh (element edge block*h) with rho = z_C.
+ * z: N_el elements of this grid; z_coarse: cx*cy*cz elements (caller-owned, host or
+ * device, must not overlap z).  block < 1 returns TOMO_EINVAL.  Sums are accumulated in
+ * double. */
+tomo_status tomo_coarse_grain(tomo_grid* grid, const float* z, int32_t block, float* z_coarse);
+tomo_status tomo_coarse_grain_d(tomo_grid* grid, const double* z, int32_t block,
+                                double* z_coarse);
 
 /* y = K(rho) x on the free DOFs (fixed rows and the fixed entries of x are zero), with
  * K(rho) = sum_e h E_e K0 and E_e = Emin + rho_e^p (E0 - Emin) (state equation of Eq. 4).
@@ -192,6 +206,27 @@ tomo_status tomo_gradient(tomo_grid* grid, const float* z, double* compliance, f
 tomo_status tomo_gradient_d(tomo_grid* grid, const double* z, double* compliance,
                             double* dcdz, double* dvdz, tomo_solve_info* info);
 
+/* General objective through the adjoint (Eq. 3), for a linear functional of the state,
+ * J = l^T u (e.g. a displacement or a weighted set of them; dJ/dz = 0 explicitly): solves
+ * K u = f and K lambda = l (dr/du = K is symmetric), then *J = l^T u and
+ * djdz = P^T dJ/drho with dJ/drho_e = -p rho_e^(p-1) (E0 - Emin) h lambda_e^T K0 u_e.
+ * Compliance is the case l = f (lambda = u).  z, djdz: N_el; l: 3*N_n SoA, its fixed
+ * entries are ignored.  info_u / info_l (may be NULL) report the two solves; both start
+ * from zero.  The state u stays in the handle (tomo_get_displacement). */
+tomo_status tomo_adjoint_gradient(tomo_grid* grid, const float* z, const float* l, double* J,
+                                  float* djdz, tomo_solve_info* info_u,
+                                  tomo_solve_info* info_l);
+tomo_status tomo_adjoint_gradient_d(tomo_grid* grid, const double* z, const double* l,
+                                    double* J, double* djdz, tomo_solve_info* info_u,
+                                    tomo_solve_info* info_l);
+
+/* on != 0: later tomo_gradient calls on this grid start CG from the displacement of the
+ * previous solve on the grid (when there is one) instead of zero; the starting residual
+ * f - K u is evaluated in FP64.  Useful along an optimisation run, where u changes little
+ * between iterations; the result is the same solve to the same tolerance.  on = 0 (the
+ * default) restores the zero start. */
+tomo_status tomo_set_warm_start(tomo_grid* grid, int32_t on);
+
 /* Copy the displacement of the last tomo_gradient / tomo_solve on this grid to u
  * (3*N_n, host or device). */
 tomo_status tomo_get_displacement(tomo_grid* grid, float* u);
@@ -224,6 +259,24 @@ tomo_status tomo_profile_phases(tomo_grid* grid, double* ms, int64_t* calls);
 tomo_status tomo_profile_levels(tomo_grid* grid, double* ms, int64_t* launches, int max_levels);
 tomo_status tomo_profile_read(tomo_grid* grid, int64_t* launches, double* total_ms,
                               double* algorithmic_bytes);
+
+/* Batches of independent grids (uneven sizes allowed), evaluated concurrently.  The paper
+ * optimises one design at a time; a batch serves many small problems at once on one GPU.
+ * tomo_batch_create: workers = number of concurrent host threads and CUDA streams (<= 0:
+ * 8, at most 64).  tomo_batch_append: adds a grid (not owned; it must outlive its use in
+ * the batch and must not be used elsewhere while a batch call runs).  tomo_batch_gradient:
+ * tomo_gradient on every grid i with z[i], &compliance[i], dcdz[i], dvdz[i] (dvdz or any
+ * dvdz[i] may be NULL), info[i] (info may be NULL); FP32 grids only.  Each grid's work runs
+ * in order on one of the batch's streams and touches only that grid, so each result is
+ * the one the grid gives alone.  Returns when all grids are done; on failure the first
+ * failing grid's status, described by tomo_batch_last_error. */
+tomo_status tomo_batch_create(int32_t workers, tomo_batch** out);
+tomo_status tomo_batch_append(tomo_batch* batch, tomo_grid* grid);
+tomo_status tomo_batch_size(const tomo_batch* batch, int32_t* count);
+tomo_status tomo_batch_gradient(tomo_batch* batch, const float* const* z, double* compliance,
+                                float* const* dcdz, float* const* dvdz, tomo_solve_info* info);
+tomo_status tomo_batch_destroy(tomo_batch* batch);
+const char* tomo_batch_last_error(const tomo_batch* batch);
 
 /* Description of the most recent error on grid (or of the last failed tomo_create_grid
  * in this thread when grid is NULL).  Never NULL; valid until the next call on grid. */

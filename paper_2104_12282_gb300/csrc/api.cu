@@ -7,6 +7,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -452,7 +453,7 @@ tomo_status enqueue_iteration(tomo_grid* G) {
     if constexpr (sizeof(T) == 8) {
       MarchArgs<T> rr{};
       rr.x = xhi;
-      rr.b = (const T*)G->f64;
+      rr.b = (const T*)G->rhs64;
       rr.y = r;
       rr.skip = &G->sc->done;
       rr.gate = G->sc;
@@ -463,7 +464,7 @@ tomo_status enqueue_iteration(tomo_grid* G) {
       MarchArgs<double> rr{};
       rr.xf_hi = xhi;
       rr.xf_lo = xlo;
-      rr.b = G->f64;
+      rr.b = G->rhs64;
       rr.yf = r;
       rr.skip = &G->sc->done;
       rr.gate = G->sc;
@@ -480,7 +481,7 @@ tomo_status enqueue_iteration(tomo_grid* G) {
 // Capture one iteration into the body of a conditional-while graph node; the body ends
 // with a kernel that clears the condition once CG has stopped.
 template <typename T>
-tomo_status build_loop_graph(tomo_grid* G) {
+tomo_status build_loop_graph(tomo_grid* G, cudaGraphExec_t* out) {
   if (!G->cap_stream) CK(cudaStreamCreateWithFlags(&G->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t graph;
   CK(cudaGraphCreate(&graph, 0));
@@ -527,7 +528,7 @@ tomo_status build_loop_graph(tomo_grid* G) {
     if (st != TOMO_OK) return st;
     CK(e);
   }
-  e = cudaGraphInstantiate(&G->loop_exec, graph, 0);
+  e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   CK(e);
   return TOMO_OK;
@@ -545,7 +546,7 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
   T* p = (T*)G->p;
   T* xhi = (T*)G->xhi;
   T* xlo = G->prec == TOMO_FP32 ? (T*)G->xlo : nullptr;
-  const double ff = G->ff;
+  const double ff = G->rhs_ff;
   const double rtol = G->d.rtol;
   CgScalars h{};
   h.ff = ff;
@@ -568,16 +569,30 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
     return TOMO_OK;
   }
   if (warm) {
-    MarchArgs<T> a{};
-    a.x = xhi;
-    a.xlo = xlo;
-    a.b = (const T*)G->f_T;
-    a.y = r;
-    TRY(march<T>(G, 0, M_RESID, a));
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (G->s64) {  // r = f - K x evaluated in FP64 from the float pair, rounded once
+        MarchArgs<double> rr{};
+        rr.xf_hi = xhi;
+        rr.xf_lo = xlo;
+        rr.b = G->rhs64;
+        rr.yf = r;
+        TRY(march<double>(G, 0, M_RESID, rr, G->s64));
+        done = true;
+      }
+    }
+    if (!done) {
+      MarchArgs<T> a{};
+      a.x = xhi;
+      a.xlo = xlo;
+      a.b = (const T*)G->rhs_T;
+      a.y = r;
+      TRY(march<T>(G, 0, M_RESID, a));
+    }
   } else {
     CK(cudaMemsetAsync(xhi, 0, sizeof(T) * n, G->stream));
     if (xlo) CK(cudaMemsetAsync(xlo, 0, sizeof(T) * n, G->stream));
-    CK(launch_mask_copy<T>(G->stream, g, (const T*)G->f_T, G->L[0].mask, r));
+    CK(launch_mask_copy<T>(G->stream, g, (const T*)G->rhs_T, G->L[0].mask, r));
     G->launches += 1;
   }
   CK(cudaMemsetAsync(p, 0, sizeof(T) * n, G->stream));
@@ -585,8 +600,9 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
   TRY(precond<T>(G, r, &z));
   CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
   G->launches += 1;
-  if (G->use_graph && !G->prof && !G->loop_exec) {
-    if (build_loop_graph<T>(G) != TOMO_OK) {
+  cudaGraphExec_t& exec = G->rhs_id == 0 ? G->loop_exec : G->loop_exec_adj;
+  if (G->use_graph && !G->prof && !exec) {
+    if (build_loop_graph<T>(G, &exec) != TOMO_OK) {
       // the device-side loop could not be captured: issue the iterations from the host
       cudaGetLastError();
       G->use_graph = false;
@@ -594,7 +610,7 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
     }
   }
   if (G->use_graph && !G->prof) {
-    CK(cudaGraphLaunch(G->loop_exec, G->stream));
+    CK(cudaGraphLaunch(exec, G->stream));
     CK(cudaMemcpyAsync(G->h_sc, G->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, G->stream));
     TRY(sync(G));
     G->launches += (int64_t)G->h_sc->loops * G->iter_launches;
@@ -679,6 +695,26 @@ tomo_status do_filter(tomo_grid* G, const T* in, T* out, int transpose) {
                       nullptr));
   G->launches += 1;
   TRY(copy_back(G, out, dout, bytes, hout));
+  if (hin || hout) TRY(sync(G));
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_coarse_grain(tomo_grid* G, const T* z, int nb, T* zc) {
+  if (!z || !zc) return fail(G, TOMO_EINVAL, "null array");
+  if (nb < 1) return fail(G, TOMO_EINVAL, "block size must be >= 1 (got %d)", nb);
+  const Geom& g = G->g;
+  const size_t nc = (size_t)((g.nx + nb - 1) / nb) * ((g.ny + nb - 1) / nb) *
+                    ((g.nz + nb - 1) / nb);
+  const void* dz;
+  void* dzc;
+  bool hin, hout;
+  TRY(stage_in(G, z, sizeof(T) * (size_t)g.nel, 0, &dz, &hin));
+  TRY(stage_out(G, zc, sizeof(T) * nc, 1, &dzc, &hout));
+  if (dz == dzc) return fail(G, TOMO_EINVAL, "z and z_coarse overlap");
+  CK(launch_coarse_grain<T>(G->stream, g, nb, (const T*)dz, (T*)dzc));
+  G->launches += 1;
+  TRY(copy_back(G, zc, dzc, sizeof(T) * nc, hout));
   if (hin || hout) TRY(sync(G));
   return TOMO_OK;
 }
@@ -789,7 +825,8 @@ tomo_status compliance_and_sens(tomo_grid* G, const T* drho, const T* du, const 
     G->launches += 1;
   }
   if (ddc) {
-    CK(launch_sensitivity<T>(G->stream, G->g, drho, du, dulo, elem_const<T>(G), (T)d.penal,
+    CK(launch_sensitivity<T>(G->stream, G->g, drho, du, dulo, nullptr, nullptr,
+                             elem_const<T>(G), (T)d.penal,
                              (T)d.E0, (T)d.Emin, (T)d.h, ddc));
     G->launches += 1;
   }
@@ -883,8 +920,8 @@ tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T
   // S2: coarse moduli, coarsest factorisation
   TRY(setup_levels<T>(G));
   TRY(pmark(G, 2));
-  // S3-S5: PCG from a zero start
-  tomo_status st = pcg<T>(G, false, info);
+  // S3-S5: PCG from a zero start (or from the previous solution, see tomo_set_warm_start)
+  tomo_status st = pcg<T>(G, G->warm_gradient && G->have_solution, info);
   if (st != TOMO_OK) return st;
   TRY(pmark(G, 3));
   // S6: compliance and dc/drho
@@ -903,6 +940,76 @@ tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T
   TRY(copy_back(G, dcdz, ddc, be, h2));
   if (dvdz) TRY(copy_back(G, dvdz, ddv, be, h3));
   TRY(write_scalar(G, compliance, G->dscal));
+  if (h1 || h2 || h3) TRY(sync(G));
+  return TOMO_OK;
+}
+
+// Eq. 3 for the objective J = l^T u: K lambda = l (K symmetric), then
+// dJ/drho_e = -p rho^(p-1) (E0-Emin) h lambda_e^T K0 u_e and dJ/dz = P^T dJ/drho.
+template <typename T>
+tomo_status do_adjoint(tomo_grid* G, const T* z, const T* l, double* J, T* djdz,
+                       tomo_solve_info* info_u, tomo_solve_info* info_l) {
+  if (!z || !l || !djdz) return fail(G, TOMO_EINVAL, "null array");
+  const Geom& g = G->g;
+  const int n = 3 * g.nn;
+  const size_t be = sizeof(T) * (size_t)g.nel, bn = sizeof(T) * (size_t)n;
+  const tomo_grid_desc& d = G->d;
+  const void *dz, *dl;
+  void* ddj;
+  bool h1, h2, h3;
+  TRY(stage_in(G, z, be, 0, &dz, &h1));
+  TRY(stage_in(G, l, bn, 2, &dl, &h2));
+  TRY(stage_out(G, djdz, be, 1, &ddj, &h3));
+  if (!G->adj_T) {
+    TRY(dalloc(G, &G->adj_T, bn));
+    TRY(dalloc(G, (void**)&G->adj64, sizeof(double) * (size_t)n));
+    TRY(dalloc(G, &G->adj_hi, bn));
+    if (G->prec == TOMO_FP32) TRY(dalloc(G, &G->adj_lo, bn));
+  }
+  // the adjoint load, masked like f, and its norm (tolerance of the adjoint solve)
+  CK(launch_mask_copy<T>(G->stream, g, (const T*)dl, G->L[0].mask, (T*)G->adj_T));
+  CK(launch_convert<double, T>(G->stream, n, (const T*)G->adj_T, nullptr, G->adj64));
+  CK(launch_dot<double, double>(G->stream, n, G->adj64, G->adj64, nullptr, G->partials,
+                                G->counter, G->dscal + 2));
+  G->launches += 3;
+  CK(cudaMemcpyAsync(G->h_scal, G->dscal + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                     G->stream));
+  TRY(sync(G));
+  const double lff = *G->h_scal;
+  T* rho = (T*)G->rho;
+  CK(launch_filter<T>(G->stream, g, G->d_taps, (const T*)G->d_tapw, G->ntaps, G->filter_radius,
+                      (const T*)dz, (const T*)G->Hs, rho, 0, 1, (T)d.E0, (T)d.Emin,
+                      (T)d.penal, (T)d.h, (T*)G->L[0].s));
+  G->launches += 1;
+  TRY(setup_levels<T>(G));
+  // adjoint solve, from zero, with its own right-hand side
+  G->rhs_T = G->adj_T;
+  G->rhs64 = G->adj64;
+  G->rhs_ff = lff;
+  G->rhs_id = 1;
+  tomo_status st = pcg<T>(G, false, info_l);
+  G->rhs_T = G->f_T;
+  G->rhs64 = G->f64;
+  G->rhs_ff = G->ff;
+  G->rhs_id = 0;
+  if (st != TOMO_OK) return st;
+  CK(cudaMemcpyAsync(G->adj_hi, G->xhi, bn, cudaMemcpyDeviceToDevice, G->stream));
+  if (G->adj_lo)
+    CK(cudaMemcpyAsync(G->adj_lo, G->xlo, bn, cudaMemcpyDeviceToDevice, G->stream));
+  // state solve (from zero: the iterate holds lambda)
+  st = pcg<T>(G, false, info_u);
+  if (st != TOMO_OK) return st;
+  CK(launch_dot<double, T>(G->stream, n, G->adj64, (const T*)G->xhi, (const T*)x_lo<T>(G),
+                           G->partials, G->counter, G->dscal));
+  CK(launch_sensitivity<T>(G->stream, g, rho, (const T*)G->xhi, (const T*)x_lo<T>(G),
+                           (const T*)G->adj_hi, (const T*)G->adj_lo, elem_const<T>(G),
+                           (T)d.penal, (T)d.E0, (T)d.Emin, (T)d.h, (T*)G->dcp));
+  CK(launch_filter<T>(G->stream, g, G->d_taps, (const T*)G->d_tapw, G->ntaps, G->filter_radius,
+                      (const T*)G->dcp, (const T*)G->Hs, (T*)ddj, 1, 0, T(0), T(0), T(0), T(0),
+                      nullptr));
+  G->launches += 3;
+  TRY(copy_back(G, djdz, ddj, be, h3));
+  TRY(write_scalar(G, J, G->dscal));
   if (h1 || h2 || h3) TRY(sync(G));
   return TOMO_OK;
 }
@@ -1009,6 +1116,11 @@ void free_grid(tomo_grid* G) {
   if (G->h_scal) cudaFreeHost(G->h_scal);
   for (void* s : G->stage) F(s);
   if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
+  if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
+  F(G->adj_T);
+  F(G->adj64);
+  F(G->adj_hi);
+  F(G->adj_lo);
   if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
   for (auto e : G->ev) cudaEventDestroy(e);
   for (auto e : G->phase_ev)
@@ -1102,6 +1214,10 @@ tomo_status create_impl(tomo_grid* G) {
     CK(cudaMemcpy(G->f_T, ft.data(), nv, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(G->f64, fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice));
   }
+  G->rhs_T = G->f_T;
+  G->rhs64 = G->f64;
+  G->rhs_ff = G->ff;
+  G->rhs_id = 0;
   // reductions
   G->partials_n = std::max(1 << 16, oc_partials_needed(g.nel));
   TRY(dalloc(G, (void**)&G->partials, sizeof(double) * (size_t)G->partials_n));
@@ -1246,6 +1362,12 @@ tomo_status tomo_destroy_grid(tomo_grid* G) {
   return TOMO_OK;
 }
 
+tomo_status tomo_set_warm_start(tomo_grid* G, int32_t on) {
+  if (!G) return TOMO_EINVAL;
+  G->warm_gradient = on != 0;
+  return TOMO_OK;
+}
+
 tomo_status tomo_set_stream(tomo_grid* G, void* stream) {
   if (!G) return TOMO_EINVAL;
   G->stream = (cudaStream_t)stream;
@@ -1268,6 +1390,27 @@ tomo_status tomo_filter(tomo_grid* G, const float* in, float* out, int transpose
 tomo_status tomo_filter_d(tomo_grid* G, const double* in, double* out, int transpose) {
   ENTER(G, true);
   return do_filter<double>(G, in, out, transpose);
+}
+tomo_status tomo_adjoint_gradient(tomo_grid* G, const float* z, const float* l, double* J,
+                                  float* djdz, tomo_solve_info* info_u,
+                                  tomo_solve_info* info_l) {
+  ENTER(G, false);
+  return do_adjoint<float>(G, z, l, J, djdz, info_u, info_l);
+}
+tomo_status tomo_adjoint_gradient_d(tomo_grid* G, const double* z, const double* l, double* J,
+                                    double* djdz, tomo_solve_info* info_u,
+                                    tomo_solve_info* info_l) {
+  ENTER(G, true);
+  return do_adjoint<double>(G, z, l, J, djdz, info_u, info_l);
+}
+tomo_status tomo_coarse_grain(tomo_grid* G, const float* z, int32_t block, float* z_coarse) {
+  ENTER(G, false);
+  return do_coarse_grain<float>(G, z, block, z_coarse);
+}
+tomo_status tomo_coarse_grain_d(tomo_grid* G, const double* z, int32_t block,
+                                double* z_coarse) {
+  ENTER(G, true);
+  return do_coarse_grain<double>(G, z, block, z_coarse);
 }
 tomo_status tomo_apply_stiffness(tomo_grid* G, const float* rho, const float* x, float* y) {
   ENTER(G, false);
@@ -1404,6 +1547,115 @@ tomo_status tomo_profile_read(tomo_grid* G, int64_t* launches, double* total_ms,
   G->prof_launches = 0;
   G->prof_bytes = 0.0;
   return TOMO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batches: many independent grids evaluated concurrently.  A small grid leaves most of the
+// GPU idle between its short launches, so the batch runs `workers` host threads, each with
+// its own stream, over the grids (round robin); each grid's work stays in order on one
+// stream and touches only that grid's buffers, so every result equals the grid's result
+// alone.
+// ---------------------------------------------------------------------------------------
+struct tomo_batch {
+  std::vector<tomo_grid*> grids;
+  std::vector<cudaStream_t> streams;
+  std::string err;
+};
+
+tomo_status tomo_batch_create(int32_t workers, tomo_batch** out) {
+  if (!out) return TOMO_EINVAL;
+  *out = nullptr;
+  if (workers <= 0) workers = 8;
+  if (workers > 64) workers = 64;
+  tomo_batch* B = new (std::nothrow) tomo_batch();
+  if (!B) return TOMO_ENOMEM;
+  for (int w = 0; w < workers; ++w) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto t : B->streams) cudaStreamDestroy(t);
+      delete B;
+      g_create_err = "tomo_batch_create: stream creation failed";
+      return TOMO_ECUDA;
+    }
+    B->streams.push_back(s);
+  }
+  *out = B;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_append(tomo_batch* B, tomo_grid* G) {
+  if (!B || !G) return TOMO_EINVAL;
+  for (auto* q : B->grids)
+    if (q == G) {
+      B->err = "grid appended twice";
+      return TOMO_EINVAL;
+    }
+  B->grids.push_back(G);
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_gradient(tomo_batch* B, const float* const* z, double* compliance,
+                                float* const* dcdz, float* const* dvdz, tomo_solve_info* info) {
+  if (!B || !z || !compliance || !dcdz) return TOMO_EINVAL;
+  B->err.clear();
+  const int n = (int)B->grids.size();
+  for (int i = 0; i < n; ++i)
+    if (B->grids[i]->prec != TOMO_FP32) {
+      B->err = "batch gradients take FP32 grids";
+      return TOMO_EINVAL;
+    }
+  const int W = std::min<int>((int)B->streams.size(), std::max(n, 1));
+  std::vector<tomo_status> st(n, TOMO_OK);
+  auto work = [&](int w) {
+    for (int i = w; i < n; i += W) {
+      tomo_grid* G = B->grids[i];
+      cudaStream_t own = G->stream;
+      G->stream = B->streams[w];
+      g_cur_err = &G->err;
+      G->err.clear();
+      st[i] = do_gradient<float>(G, z[i], compliance + i, dcdz[i], dvdz ? dvdz[i] : nullptr,
+                                 info ? info + i : nullptr);
+      if (st[i] == TOMO_OK && cudaStreamSynchronize(G->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st[i] = TOMO_ECUDA;
+      }
+      G->stream = own;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < W; ++w) pool.emplace_back(work, w);
+  work(0);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != TOMO_OK) {
+      char buf[64];
+      std::snprintf(buf, sizeof buf, "grid %d of the batch: ", i);
+      B->err = std::string(buf) + B->grids[i]->err;
+      return st[i];
+    }
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_size(const tomo_batch* B, int32_t* count) {
+  if (!B || !count) return TOMO_EINVAL;
+  *count = (int32_t)B->grids.size();
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_destroy(tomo_batch* B) {
+  if (!B) return TOMO_OK;
+  for (auto s : B->streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  delete B;
+  return TOMO_OK;
+}
+
+const char* tomo_batch_last_error(const tomo_batch* B) {
+  if (!B) return g_create_err.c_str();
+  return B->err.c_str();
 }
 
 const char* tomo_last_error(const tomo_grid* G) {

@@ -104,6 +104,87 @@ __global__ void __launch_bounds__(kFtX * kFtY)
   }
 }
 
+// The same tiling for radii 4..8 (rmin up to 9 elements; the paper's R = 0.08 on Mesh 3 is
+// 7.2 elements): radius at run time, tile and weight table in dynamic shared memory.
+constexpr int kFtMaxR = 8;
+template <int MODE, bool MAT>
+__global__ void __launch_bounds__(kFtX * kFtY)
+    k_filter_tiled_wide(Geom g, int R, const int4* __restrict__ taps,
+                        const float* __restrict__ tapw, int ntaps, const float* __restrict__ in,
+                        const float* __restrict__ Hs, float* __restrict__ out, float E0,
+                        float Emin, float penal, float h, float* __restrict__ s_out) {
+  extern __shared__ __align__(16) float ft_smem[];
+  const int W = 2 * R + 1;
+  const int SX = kFtX + 2 * R, SY = kFtY + 2 * R, SZ = kFtZ + 2 * R;
+  float* tile = ft_smem;                 // [SZ][SY][SX]
+  float* wt = ft_smem + SX * SY * SZ;    // [W][W][W]
+  PDL_ENTER();
+  const int tid = threadIdx.x + kFtX * threadIdx.y;
+  const int i0 = blockIdx.x * kFtX, j0 = blockIdx.y * kFtY, k0 = blockIdx.z * kFtZ;
+  for (int q = tid; q < W * W * W; q += kFtX * kFtY) wt[q] = 0.0f;
+  __syncthreads();
+  for (int t = tid; t < ntaps; t += kFtX * kFtY) {
+    const int4 d = taps[t];
+    wt[(d.z + R) * W * W + (d.y + R) * W + (d.x + R)] = tapw[t];
+  }
+  for (int q = tid; q < SX * SY * SZ; q += kFtX * kFtY) {
+    const int x = q % SX, y = (q / SX) % SY, z = q / (SX * SY);
+    const int i = i0 + x - R, j = j0 + y - R, k = k0 + z - R;
+    float v = 0.0f;
+    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) {
+      const int e = i + g.nx * (j + g.ny * k);
+      v = __ldg(in + e);
+      if (MODE == 1) v = v / __ldg(Hs + e);
+    }
+    tile[q] = v;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float acc[kFtZ];
+#pragma unroll
+  for (int z = 0; z < kFtZ; ++z) acc[z] = 0.0f;
+  for (int dj = 0; dj < W; ++dj) {
+    for (int di = 0; di < W; ++di) {
+      const float* col = tile + (ty + dj) * SX + (tx + di);
+      for (int dk = 0; dk < W; ++dk) {
+        const float w = wt[dk * W * W + dj * W + di];
+        if (w == 0.0f) continue;  // uniform over the CTA
+#pragma unroll
+        for (int z = 0; z < kFtZ; ++z) acc[z] = fmaf(w, col[(z + dk) * SX * SY], acc[z]);
+      }
+    }
+  }
+  const int i = i0 + tx, j = j0 + ty;
+  if (i >= g.nx || j >= g.ny) return;
+#pragma unroll
+  for (int z = 0; z < kFtZ; ++z) {
+    const int k = k0 + z;
+    if (k >= g.nz) break;
+    const int e = i + g.nx * (j + g.ny * k);
+    float v = acc[z];
+    if (MODE == 0) v = v / Hs[e];
+    out[e] = v;
+    if (MAT) s_out[e] = h * (Emin + powf(v, penal) * (E0 - Emin));
+  }
+}
+
+template <int MODE, bool MAT>
+cudaError_t launch_wide(dim3 grid, dim3 block, size_t smem, cudaStream_t st, Geom g, int R,
+                        const int4* taps, const float* tapw, int ntaps, const float* in,
+                        const float* Hs, float* out, float E0, float Emin, float penal, float h,
+                        float* s_out) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_filter_tiled_wide<MODE, MAT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return pdl_launch(k_filter_tiled_wide<MODE, MAT>, grid, block, smem, st, g, R, taps, tapw,
+                    ntaps, in, Hs, out, E0, Emin, penal, h, s_out);
+}
+
 template <typename T, int R>
 bool launch_filter_tiled(cudaStream_t st, Geom g, const int4* taps, const T* tapw, int ntaps,
                          const T* in, const T* Hs, T* out, int mode, int material, T E0,
@@ -143,6 +224,32 @@ cudaError_t launch_filter(cudaStream_t st, Geom g, const int4* taps, const T* ta
   else if (radius == 3 && sizeof(T) == 4)
     done = launch_filter_tiled<T, 3>(st, g, taps, tapw, ntaps, in, Hs, out, mode, material, E0,
                                      Emin, penal, h, s_out);
+  if constexpr (sizeof(T) == 4) {
+    if (!done && radius > 3 && radius <= kFtMaxR) {
+      const int W = 2 * radius + 1;
+      const size_t smem = sizeof(float) * ((size_t)(kFtX + 2 * radius) * (kFtY + 2 * radius) *
+                                               (kFtZ + 2 * radius) + (size_t)W * W * W);
+      const dim3 grid((g.nx + kFtX - 1) / kFtX, (g.ny + kFtY - 1) / kFtY,
+                      (g.nz + kFtZ - 1) / kFtZ);
+      const dim3 block(kFtX, kFtY);
+      if (smem <= 200 * 1024 && grid.y <= 65535 && grid.z <= 65535) {
+        cudaError_t e;
+        if (mode == 0 && material)
+          e = launch_wide<0, true>(grid, block, smem, st, g, radius, taps, tapw, ntaps, in, Hs,
+                                   out, E0, Emin, penal, h, s_out);
+        else if (mode == 0)
+          e = launch_wide<0, false>(grid, block, smem, st, g, radius, taps, tapw, ntaps, in, Hs,
+                                    out, E0, Emin, penal, h, s_out);
+        else if (mode == 1)
+          e = launch_wide<1, false>(grid, block, smem, st, g, radius, taps, tapw, ntaps, in, Hs,
+                                    out, E0, Emin, penal, h, s_out);
+        else
+          e = launch_wide<2, false>(grid, block, smem, st, g, radius, taps, tapw, ntaps, in, Hs,
+                                    out, E0, Emin, penal, h, s_out);
+        return e != cudaSuccess ? e : cudaGetLastError();
+      }
+    }
+  }
   if (done) return cudaGetLastError();
   int blocks = (g.nel + 255) / 256;
   if (blocks > 16384) blocks = 16384;
@@ -184,42 +291,58 @@ cudaError_t launch_material(cudaStream_t st, int n, const T* rho, T E0, T Emin, 
 // u_e^T K0 u_e = sum_k X_k^T blk_k X_k with X the per-component Walsh-Hadamard transform of
 // the element's node values minus local node 0 (differences first).
 // ---------------------------------------------------------------------------------------
+// Per-component Walsh-Hadamard modes of an element's node values minus local node 0 (the
+// differences first, so FP32 rounding stays relative to the differences), optionally of
+// the unevaluated pair v + vlo.
 template <typename T, bool PAIR>
+__device__ __forceinline__ void element_modes(const Geom& g, const T* __restrict__ v,
+                                              const T* __restrict__ vlo, int i, int j, int k,
+                                              T (&X)[3][8]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T w[8];
+    const T* vc = v + (size_t)c * g.nn;
+    const T* vlc = PAIR ? vlo + (size_t)c * g.nn : nullptr;
+    const int n0 = i + g.nxn * (j + g.nyn * k);
+    const T a0 = ldg(vc + n0);
+    const T al = PAIR ? ldg(vlc + n0) : T(0);
+#pragma unroll
+    for (int s = 1; s < 8; ++s) {
+      const int ns = (i + (s & 1)) + g.nxn * ((j + ((s >> 1) & 1)) + g.nyn * (k + (s >> 2)));
+      T d = ldg(vc + ns) - a0;
+      if (PAIR) d += ldg(vlc + ns) - al;
+      w[s] = d;
+    }
+    w[0] = T(0);
+#pragma unroll
+    for (int st = 1; st < 8; st <<= 1)
+#pragma unroll
+      for (int s = 0; s < 8; ++s)
+        if ((s & st) == 0) {
+          const T a = w[s], b = w[s + st];
+          w[s] = a + b;
+          w[s + st] = a - b;
+        }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) X[c][m] = w[m];
+  }
+}
+
+// dc_e = -p rho^(p-1) (E0-Emin) h w_e^T K0 u_e with w = u (compliance, Eq. 5) or w = the
+// adjoint state lambda (BILIN; the general objective of Eq. 3).  w_e^T K0 u_e = sum_k
+// Y_k^T blk_k X_k in the Hadamard basis (X, Y the modes of u, w).
+template <typename T, bool PAIR, bool BILIN>
 __global__ void k_sensitivity(Geom g, const T* __restrict__ rho, const T* __restrict__ u,
-                              const T* __restrict__ ulo, const __grid_constant__ ElemConst<T> C,
+                              const T* __restrict__ ulo, const T* __restrict__ w,
+                              const T* __restrict__ wlo, const __grid_constant__ ElemConst<T> C,
                               T penal, T E0, T Emin, T h, T* __restrict__ dc) {
   PDL_ENTER();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.nel; e += gridDim.x * blockDim.x) {
     const int i = e % g.nx, j = (e / g.nx) % g.ny, k = e / (g.nx * g.ny);
     T X[3][8];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T v[8];
-      const T* uc = u + (size_t)c * g.nn;
-      const T* ulc = PAIR ? ulo + (size_t)c * g.nn : nullptr;
-      const int n0 = i + g.nxn * (j + g.nyn * k);
-      const T a0 = ldg(uc + n0);
-      const T al = PAIR ? ldg(ulc + n0) : T(0);
-#pragma unroll
-      for (int s = 1; s < 8; ++s) {
-        const int ns = (i + (s & 1)) + g.nxn * ((j + ((s >> 1) & 1)) + g.nyn * (k + (s >> 2)));
-        T d = ldg(uc + ns) - a0;
-        if (PAIR) d += ldg(ulc + ns) - al;
-        v[s] = d;
-      }
-      v[0] = T(0);
-#pragma unroll
-      for (int st = 1; st < 8; st <<= 1)
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-          if ((s & st) == 0) {
-            const T a = v[s], b = v[s + st];
-            v[s] = a + b;
-            v[s + st] = a - b;
-          }
-#pragma unroll
-      for (int m = 0; m < 8; ++m) X[c][m] = v[m];
-    }
+    element_modes<T, PAIR>(g, u, ulo, i, j, k, X);
+    T Y[3][8];
+    if constexpr (BILIN) element_modes<T, PAIR>(g, w, wlo, i, j, k, Y);
     T ce = T(0);
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
@@ -229,7 +352,14 @@ __global__ void k_sensitivity(Geom g, const T* __restrict__ rho, const T* __rest
       const T y0 = C.blk[kk][0][0] * x0 + C.blk[kk][0][1] * x1 + C.blk[kk][0][2] * x2;
       const T y1 = C.blk[kk][1][0] * x0 + C.blk[kk][1][1] * x1 + C.blk[kk][1][2] * x2;
       const T y2 = C.blk[kk][2][0] * x0 + C.blk[kk][2][1] * x1 + C.blk[kk][2][2] * x2;
-      ce += x0 * y0 + x1 * y1 + x2 * y2;
+      if constexpr (BILIN) {
+        const T w0 = (kk ^ 1) ? Y[0][kk ^ 1] : T(0);
+        const T w1 = (kk ^ 2) ? Y[1][kk ^ 2] : T(0);
+        const T w2 = (kk ^ 4) ? Y[2][kk ^ 4] : T(0);
+        ce += w0 * y0 + w1 * y1 + w2 * y2;
+      } else {
+        ce += x0 * y0 + x1 * y1 + x2 * y2;
+      }
     }
     const T r = rho[e];
     dc[e] = -penal * pow(r, penal - T(1)) * (E0 - Emin) * h * ce;
@@ -238,17 +368,30 @@ __global__ void k_sensitivity(Geom g, const T* __restrict__ rho, const T* __rest
 
 template <typename T>
 cudaError_t launch_sensitivity(cudaStream_t st, Geom g, const T* rho, const T* u, const T* ulo,
-                               const ElemConst<T>& c, T penal, T E0, T Emin, T h, T* dc) {
+                               const T* w, const T* wlo, const ElemConst<T>& c, T penal, T E0,
+                               T Emin, T h, T* dc) {
   int blocks = (g.nel + 127) / 128;
   if (blocks > 16384) blocks = 16384;
+  if ((ulo != nullptr) != (w != nullptr && wlo != nullptr) && w != nullptr)
+    return cudaErrorInvalidValue;  // u and w must both be pairs or both plain
   if (ulo) {
     if constexpr (sizeof(T) == 4) {
-      pdl_launch(k_sensitivity<T, true>, blocks, 128, 0, st, g, rho, u, ulo, c, penal, E0, Emin, h, dc);
+      if (w)
+        pdl_launch(k_sensitivity<T, true, true>, blocks, 128, 0, st, g, rho, u, ulo, w, wlo, c,
+                   penal, E0, Emin, h, dc);
+      else
+        pdl_launch(k_sensitivity<T, true, false>, blocks, 128, 0, st, g, rho, u, ulo, w, wlo, c,
+                   penal, E0, Emin, h, dc);
       return cudaGetLastError();
     }
     return cudaErrorInvalidValue;
   }
-  pdl_launch(k_sensitivity<T, false>, blocks, 128, 0, st, g, rho, u, nullptr, c, penal, E0, Emin, h, dc);
+  if (w)
+    pdl_launch(k_sensitivity<T, false, true>, blocks, 128, 0, st, g, rho, u, nullptr, w, nullptr,
+               c, penal, E0, Emin, h, dc);
+  else
+    pdl_launch(k_sensitivity<T, false, false>, blocks, 128, 0, st, g, rho, u, nullptr, nullptr,
+               nullptr, c, penal, E0, Emin, h, dc);
   return cudaGetLastError();
 }
 
@@ -490,7 +633,8 @@ int oc_max_blocks(int n) {
                                         const T*, const T*, T*, int, int, T, T, T, T, T*);     \
   template cudaError_t launch_material<T>(cudaStream_t, int, const T*, T, T, T, T, T*);       \
   template cudaError_t launch_sensitivity<T>(cudaStream_t, Geom, const T*, const T*, const T*, \
-                                             const ElemConst<T>&, T, T, T, T, T*);            \
+                                             const T*, const T*, const ElemConst<T>&, T, T, T, \
+                                             T, T*);                                           \
   template cudaError_t launch_oc<T>(cudaStream_t, int, const T*, const T*, const T*, double,   \
                                     double, T*, double*, unsigned*, double*, double*, int);
 INST(float)

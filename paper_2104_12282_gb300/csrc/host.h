@@ -133,6 +133,10 @@ template <typename TO, typename TI>
 cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo, TO* out,
                            const CgScalars* gate = nullptr);
 
+// Two-scale coarse-graining: z_C = block means of z over N_B^3 element blocks.
+template <typename T>
+cudaError_t launch_coarse_grain(cudaStream_t st, Geom g, int nb, const T* z, T* zc);
+
 // Filter, material, sensitivity, OC.
 template <typename T>
 cudaError_t launch_filter(cudaStream_t st, Geom g, const int4* taps, const T* tapw, int ntaps,
@@ -143,7 +147,8 @@ cudaError_t launch_material(cudaStream_t st, int n, const T* rho, T E0, T Emin, 
                             T* s);
 template <typename T>
 cudaError_t launch_sensitivity(cudaStream_t st, Geom g, const T* rho, const T* u, const T* ulo,
-                               const ElemConst<T>& c, T penal, T E0, T Emin, T h, T* dc);
+                               const T* w, const T* wlo, const ElemConst<T>& c, T penal, T E0,
+                               T Emin, T h, T* dc);
 template <typename T>
 cudaError_t launch_oc(cudaStream_t st, int n, const T* z, const T* dc, const T* w, double vmax,
                       double move, T* znew, double* partials, unsigned* counter,
@@ -227,10 +232,22 @@ struct tomo_grid {
   double level_ms[16] = {};         // eager V-cycle time per level (all kernels), level 0..15
   int64_t level_n[16] = {};
   bool have_solution = false;
+  bool warm_gradient = false;  // tomo_gradient starts CG from the previous solution
   int partials_n = 0;
   double ff = 0.0;                  // ||f||^2 over free DOFs
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   cudaGraphExec_t loop_exec = nullptr;  // device-side PCG loop (conditional while)
+  // right-hand side of the next pcg: the load f (rhs_id 0) or an adjoint load (rhs_id 1);
+  // each has its own captured loop, since the FP64 residual replacement reads it
+  void* rhs_T = nullptr;
+  double* rhs64 = nullptr;
+  double rhs_ff = 0.0;
+  int rhs_id = 0;
+  cudaGraphExec_t loop_exec_adj = nullptr;
+  void* adj_T = nullptr;       // adjoint load l (masked), T and double
+  double* adj64 = nullptr;
+  void* adj_hi = nullptr;      // adjoint state lambda (pair on FP32 grids)
+  void* adj_lo = nullptr;
   bool use_graph = true;
   // phase timing (events at phase boundaries; the CG loop stays a graph)
   bool phase_prof = false;

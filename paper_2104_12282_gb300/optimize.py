@@ -1,0 +1,115 @@
+"""Optimisation runs on the GPU through the C ABI: Algorithm 1 with the exact gradient on
+every iteration (the optimiser the paper compares against), with the two-scale coarse
+step at the top of each iteration when a block size is given (coarse-grain z, solve the
+coarse state K_C(z_C) u_C = f_C).  The synthetic-gradient model of Algorithm 1 is not
+part of this package.
+
+    python -m paper_2104_12282_gb300.optimize --mesh 1 --iters 200 --block 5
+
+runs the cantilever of §IV on the Table 1 meshes (domain 2 x 1 x 1, element edge 1/ny,
+filter radius 0.08 in domain units, volume fraction 0.12) and prints one JSON line per
+iteration and a summary line.  p = 3, E0 = 1, Emin = 1e-9 and the OC constants (move 0.2,
+eta 1/2) are readings: the paper does not state them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import problems as P
+from . import tomo
+
+MESHES = {1: (70, 35, 35), 2: (100, 50, 50), 3: (180, 90, 90)}
+
+
+def paper_cantilever(mesh: int, volfrac: float = 0.12, radius: float = 0.08) -> P.Problem:
+    """Cantilever Mesh 1-3 of Table 1 in domain units: h = 1/ny, rmin = radius / h."""
+    nx, ny, nz = MESHES[mesh]
+    h = 1.0 / ny
+    return P.cantilever(nx, ny, nz, h=h, volfrac=volfrac, rmin=radius / h)
+
+
+def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo.FP32,
+        rtol: float = 1e-6, warm: bool = True, maxit: int = 5000, z0=None, callback=None):
+    """Exact-gradient OC loop on the GPU.  Returns (z, history); history holds one dict per
+    iteration: compliance, design change, CG iterations, wall time of the gradient and of
+    the coarse step (ms)."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dt = torch.float32 if precision == tomo.FP32 else torch.float64
+    z = torch.tensor(np.asarray(problem.z0 if z0 is None else z0), dtype=dt, device=dev)
+    zn = torch.empty_like(z)
+    dc = torch.empty_like(z)
+    dv = torch.empty_like(z)
+    hist = []
+    with tomo.Grid.from_problem(problem, precision=precision, rtol=rtol, maxit=maxit) as g:
+        g.set_warm_start(warm)
+        gc = None
+        if block:
+            q = P.coarse_problem(problem, block)
+            gc = tomo.Grid.from_problem(q, precision=precision, rtol=rtol, maxit=maxit)
+            gc.set_warm_start(warm)
+            zc = torch.empty(q.n_el, dtype=dt, device=dev)
+            uc = torch.zeros(q.dims.n_dof, dtype=dt, device=dev)
+        try:
+            for k in range(iters):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                coarse = None
+                if gc is not None:   # Algorithm 1: coarse-grain z, solve the coarse state
+                    g.coarse_grain(z, block, zc)
+                    ci = gc.solve(zc, uc)
+                    coarse = ci.iters
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                c, info = g.gradient(z, dc, dv)
+                change = g.oc_step(z, dc, dv, problem.volfrac, problem.move, zn)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                rec = dict(it=k, c=c, change=change, cg_iters=info.iters,
+                           ms=(t2 - t1) * 1e3, coarse_ms=(t1 - t0) * 1e3,
+                           coarse_cg_iters=coarse)
+                hist.append(rec)
+                if callback:
+                    callback(rec)
+                z, zn = zn, z
+        finally:
+            if gc is not None:
+                gc.close()
+    return z, hist
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--mesh", type=int, choices=sorted(MESHES), default=1)
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--block", type=int, default=5, help="two-scale block size N_B (0: off)")
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--cold", action="store_true", help="start every solve from zero")
+    ap.add_argument("--quiet", action="store_true")
+    a = ap.parse_args(argv)
+    p = paper_cantilever(a.mesh)
+    prec = tomo.FP64 if a.fp64 else tomo.FP32
+
+    def show(rec):
+        if not a.quiet:
+            print(json.dumps(rec), flush=True)
+
+    t = time.perf_counter()
+    _, hist = run(p, a.iters, block=a.block, precision=prec, warm=not a.cold, callback=show)
+    wall = time.perf_counter() - t
+    d = p.dims
+    print(json.dumps({"mesh": a.mesh, "dims": [d.nx, d.ny, d.nz], "h": p.h, "rmin": p.rmin,
+                      "block": a.block, "iters": a.iters, "final_c": hist[-1]["c"],
+                      "wall_s": wall, "cg_iters_total": sum(r["cg_iters"] for r in hist),
+                      "precision": "fp64" if a.fp64 else "fp32-mixed",
+                      "warm_start": not a.cold}), flush=True)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

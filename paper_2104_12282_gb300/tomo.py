@@ -61,8 +61,22 @@ def _load():
         "tomo_create_grid": (st, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_void_p)]),
         "tomo_destroy_grid": (st, [G]),
         "tomo_set_stream": (st, [G, P]),
+        "tomo_set_warm_start": (st, [G, ctypes.c_int32]),
+        "tomo_batch_create": (st, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+        "tomo_batch_append": (st, [P, G]),
+        "tomo_batch_size": (st, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "tomo_batch_gradient": (st, [P, P, ctypes.POINTER(ctypes.c_double), P, P,
+                                     ctypes.POINTER(SolveInfo)]),
+        "tomo_batch_destroy": (st, [P]),
+        "tomo_batch_last_error": (ctypes.c_char_p, [P]),
         "tomo_filter": (st, [G, P, P, ctypes.c_int]),
         "tomo_filter_d": (st, [G, P, P, ctypes.c_int]),
+        "tomo_adjoint_gradient": (st, [G, P, P, ctypes.POINTER(ctypes.c_double), P,
+                                       ctypes.POINTER(SolveInfo), ctypes.POINTER(SolveInfo)]),
+        "tomo_adjoint_gradient_d": (st, [G, P, P, ctypes.POINTER(ctypes.c_double), P,
+                                         ctypes.POINTER(SolveInfo), ctypes.POINTER(SolveInfo)]),
+        "tomo_coarse_grain": (st, [G, P, ctypes.c_int32, P]),
+        "tomo_coarse_grain_d": (st, [G, P, ctypes.c_int32, P]),
         "tomo_apply_stiffness": (st, [G, P, P, P]),
         "tomo_apply_stiffness_d": (st, [G, P, P, P]),
         "tomo_residual": (st, [G, P, P, P, P]),
@@ -102,6 +116,13 @@ def _load():
 _lib = None
 
 
+def coarse_dims(nx, ny, nz, block):
+    """Elements per axis of the two-scale coarse grid: ceil(n / block)."""
+    if block < 1:
+        raise ValueError("block must be >= 1")
+    return (-(-nx // block), -(-ny // block), -(-nz // block))
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -112,7 +133,11 @@ def lib():
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["tomo_default_desc", "tomo_create_grid", "tomo_destroy_grid", "tomo_set_stream",
-            "tomo_filter", "tomo_filter_d", "tomo_apply_stiffness", "tomo_apply_stiffness_d",
+            "tomo_set_warm_start", "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
+            "tomo_batch_gradient", "tomo_batch_destroy", "tomo_batch_last_error",
+            "tomo_filter", "tomo_filter_d", "tomo_coarse_grain", "tomo_coarse_grain_d",
+            "tomo_adjoint_gradient", "tomo_adjoint_gradient_d",
+            "tomo_apply_stiffness", "tomo_apply_stiffness_d",
             "tomo_residual", "tomo_residual_d", "tomo_solve", "tomo_solve_d", "tomo_sensitivity", "tomo_sensitivity_d",
             "tomo_oc_step", "tomo_oc_step_d", "tomo_oc_step_noalloc", "tomo_gradient",
             "tomo_gradient_d",
@@ -246,8 +271,25 @@ class Grid:
         if st != 0:
             raise TomoError(st, lib().tomo_last_error(self._h).decode())
 
+    def set_warm_start(self, on=True):
+        """Start later gradient solves from the previous displacement (tomo_set_warm_start)."""
+        st = lib().tomo_set_warm_start(self._h, int(bool(on)))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
     def filter(self, x, out, transpose=False):
         self._call("tomo_filter", self._e(x, "in"), self._e(out, "out"), int(bool(transpose)))
+
+    def coarse_grain(self, z, block, out):
+        """Two-scale coarse design: out = block means of z over block^3 element blocks
+        (``coarse_dims`` gives the coarse grid)."""
+        if block >= 1:
+            cx, cy, cz = coarse_dims(self.nx, self.ny, self.nz, block)
+            count = cx * cy * cz
+        else:   # the library rejects the block size (TOMO_EINVAL)
+            count = int(out.numel() if hasattr(out, "numel") else np.asarray(out).size)
+        self._call("tomo_coarse_grain", self._e(z, "z"), int(block),
+                   _ptr(out, self.dtype, count, "z_coarse"))
 
     def apply_stiffness(self, rho, x, y):
         self._call("tomo_apply_stiffness", self._e(rho, "rho"), self._n(x, "x"), self._n(y, "y"))
@@ -290,6 +332,15 @@ class Grid:
         self._call("tomo_gradient", self._e(z, "z"), ctypes.byref(c), self._e(dcdz, "dcdz"),
                    self._e(dvdz, "dvdz") if dvdz is not None else None, ctypes.byref(info))
         return c.value, Info(info.iters, info.rel_res, info.status, info.mg_levels)
+
+    def adjoint_gradient(self, z, l, djdz):
+        """J = l^T u and dJ/dz through the adjoint (Eq. 3); returns (J, info_u, info_l)."""
+        J = ctypes.c_double()
+        iu, il = SolveInfo(), SolveInfo()
+        self._call("tomo_adjoint_gradient", self._e(z, "z"), self._n(l, "l"), ctypes.byref(J),
+                   self._e(djdz, "djdz"), ctypes.byref(iu), ctypes.byref(il))
+        mk = lambda i: Info(i.iters, i.rel_res, i.status, i.mg_levels)  # noqa: E731
+        return J.value, mk(iu), mk(il)
 
     def get_displacement(self, u):
         self._call("tomo_get_displacement", self._n(u, "u"))
@@ -342,6 +393,65 @@ class Grid:
     def close(self):
         if getattr(self, "_h", None):
             lib().tomo_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """A set of FP32 grids evaluated concurrently (``tomo_batch_*``): ``workers`` host
+    threads, one CUDA stream each.  The batch does not own its grids."""
+
+    def __init__(self, workers=8):
+        h = ctypes.c_void_p()
+        st = lib().tomo_batch_create(int(workers), ctypes.byref(h))
+        if st != 0:
+            raise TomoError(st, lib().tomo_batch_last_error(None).decode())
+        self._h = h
+        self.grids = []
+
+    def append(self, grid):
+        st = lib().tomo_batch_append(self._h, grid._h)
+        if st != 0:
+            raise TomoError(st, lib().tomo_batch_last_error(self._h).decode())
+        self.grids.append(grid)
+
+    def __len__(self):
+        n = ctypes.c_int32()
+        lib().tomo_batch_size(self._h, ctypes.byref(n))
+        return n.value
+
+    def gradient(self, zs, dcdzs, dvdzs=None):
+        """tomo_gradient on every grid; returns (compliances, infos)."""
+        n = len(self.grids)
+        if len(zs) != n or len(dcdzs) != n or (dvdzs is not None and len(dvdzs) != n):
+            raise ValueError("one array per grid")
+        arr = ctypes.c_void_p * n
+        z = arr(*[g._e(a, "z") for g, a in zip(self.grids, zs)])
+        dc = arr(*[g._e(a, "dcdz") for g, a in zip(self.grids, dcdzs)])
+        dv = arr(*[g._e(a, "dvdz") for g, a in zip(self.grids, dvdzs)]) if dvdzs else None
+        c = (ctypes.c_double * n)()
+        info = (SolveInfo * n)()
+        st = lib().tomo_batch_gradient(self._h, ctypes.cast(z, ctypes.c_void_p), c,
+                                       ctypes.cast(dc, ctypes.c_void_p),
+                                       ctypes.cast(dv, ctypes.c_void_p) if dv else None, info)
+        if st != 0:
+            raise TomoError(st, lib().tomo_batch_last_error(self._h).decode())
+        return list(c), [Info(i.iters, i.rel_res, i.status, i.mg_levels) for i in info]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tomo_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):
