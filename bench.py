@@ -286,6 +286,7 @@ def extras(args, dev, stream):
 
             def step():
                 g.coarse_grain(zb, nb, zc)
+                uc.zero_()   # tomo_solve starts from u: cold start, as the fine gradient
                 return gc.solve(zc, uc)
             step()
             ms, info = timed(step, 3)
