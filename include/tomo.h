@@ -278,6 +278,53 @@ tomo_status tomo_batch_gradient(tomo_batch* batch, const float* const* z, double
 tomo_status tomo_batch_destroy(tomo_batch* batch);
 const char* tomo_batch_last_error(const tomo_batch* batch);
 
+/* Request loop (serving): gradient requests on design domains of different sizes, run
+ * by `workers` threads with one CUDA stream each, with grids kept resident on the device
+ * per session and admission by device memory.  The paper has no counterpart (it optimises
+ * one design at a time); the arithmetic of each request is tomo_gradient's.
+ * tomo_server_create: budget_bytes = device memory the resident grids may hold (their
+ *   estimated footprint, tomo_estimate_device_bytes).
+ * tomo_server_submit: desc (FP32; fixed_dof, f and z are copied), session >= 0 keeps the
+ *   grid resident for later requests of that session with the same descriptor (< 0: a
+ *   grid for this request only).  dcdz (N_el) and dvdz (N_el, may be NULL) are host
+ *   arrays owned by the caller, written before tomo_server_wait returns the ticket.
+ *   TOMO_ENOMEM if the request alone exceeds the budget.
+ * tomo_server_wait: blocks until the ticket is done, fills *result, forgets the ticket.
+ * Requests start in arrival order among those whose memory can be found (idle resident
+ * grids of other sessions are evicted least recently used first); a request starts as
+ * soon as a worker is free, while others run.  Each request runs in order on one stream
+ * on its own grid, so its result is the one it gives alone.
+ * tomo_server_destroy: stops the workers after their running requests; requests still
+ * queued are dropped (wait for every ticket first). */
+typedef struct tomo_server tomo_server;
+typedef struct {
+  int64_t ticket;
+  int32_t status;          /* tomo_status of the request */
+  double compliance;       /* f^T u */
+  tomo_solve_info info;
+  double queue_ms;         /* submission to start */
+  double run_ms;           /* start to completion (grid creation included when new) */
+  int32_t message_len;
+  char message[256];       /* error text when status != TOMO_OK */
+} tomo_result;
+typedef struct {
+  int64_t submitted, completed, grids_created, evictions;
+  uint64_t resident_bytes, peak_bytes;  /* estimated footprints of the resident grids */
+  int32_t resident_grids, queued;
+} tomo_server_stats;
+tomo_status tomo_server_create(int32_t workers, uint64_t budget_bytes, tomo_server** out);
+tomo_status tomo_server_submit(tomo_server* server, const tomo_grid_desc* desc, int64_t session,
+                               const float* z, float* dcdz, float* dvdz, int64_t* ticket);
+tomo_status tomo_server_wait(tomo_server* server, int64_t ticket, tomo_result* result);
+tomo_status tomo_server_get_stats(tomo_server* server, tomo_server_stats* stats);
+tomo_status tomo_server_destroy(tomo_server* server);
+const char* tomo_server_last_error(const tomo_server* server);
+
+/* Device memory held by a grid, and an upper estimate of it for a descriptor before the
+ * grid exists (host staging of z, dc/dz and dV/dz included). */
+tomo_status tomo_grid_device_bytes(const tomo_grid* grid, size_t* bytes);
+tomo_status tomo_estimate_device_bytes(const tomo_grid_desc* desc, size_t* bytes);
+
 /* Description of the most recent error on grid (or of the last failed tomo_create_grid
  * in this thread when grid is NULL).  Never NULL; valid until the next call on grid. */
 const char* tomo_last_error(const tomo_grid* grid);

@@ -14,7 +14,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "libtomo.so")
 SOURCES = ["api.cu", "element.cu", "matvec.cu", "matvec2.cu", "vec.cu", "filt.cu",
-           "twoscale.cu", "noalloc.cu"]
+           "twoscale.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

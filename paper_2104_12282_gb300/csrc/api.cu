@@ -78,6 +78,7 @@ tomo_status dalloc(tomo_grid* G, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
   CK(cudaMalloc(p, bytes));
+  if (G) G->dev_bytes += bytes;
   return TOMO_OK;
 }
 
@@ -105,6 +106,7 @@ tomo_status stage_in(tomo_grid* G, const void* p, size_t bytes, int slot, const 
   }
   if (G->stage_size[slot] < bytes) {
     if (G->stage[slot]) cudaFree(G->stage[slot]);
+    G->dev_bytes -= G->stage_size[slot];
     G->stage[slot] = nullptr;
     G->stage_size[slot] = 0;
     TRY(dalloc(G, &G->stage[slot], bytes));
@@ -128,6 +130,7 @@ tomo_status stage_out(tomo_grid* G, void* p, size_t bytes, int slot, void** out,
   }
   if (G->stage_size[slot] < bytes) {
     if (G->stage[slot]) cudaFree(G->stage[slot]);
+    G->dev_bytes -= G->stage_size[slot];
     G->stage[slot] = nullptr;
     G->stage_size[slot] = 0;
     TRY(dalloc(G, &G->stage[slot], bytes));
@@ -1128,6 +1131,54 @@ void free_grid(tomo_grid* G) {
   delete G;
 }
 
+// Multigrid level grids: ceil-halving until the coarsest has 3 N_n <= 192 (or mg_levels
+// levels, when set, with a coarsest of at most kMaxDenseDofs), at least two levels.
+std::vector<Geom> plan_levels(const tomo_grid_desc& d) {
+  std::vector<Geom> v{make_geom(d.nx, d.ny, d.nz)};
+  if (d.precond != TOMO_PRECOND_MG) return v;
+  const int want = d.mg_levels;
+  while (true) {
+    const Geom gf = v.back();
+    const int nl = (int)v.size();
+    const bool small = 3 * gf.nn <= 192;
+    const bool can = std::max(gf.nx, std::max(gf.ny, gf.nz)) > 1;
+    if (!can) break;
+    if (want > 0 && nl >= want && 3 * gf.nn <= kMaxDenseDofs) break;
+    if (want <= 0 && small) break;
+    v.push_back(make_geom((gf.nx + 1) / 2, (gf.ny + 1) / 2, (gf.nz + 1) / 2));
+  }
+  if (v.size() < 2) {
+    // a single-level grid: the dense solve of the grid itself would be the whole solve;
+    // keep one coarse level so that the V-cycle structure holds
+    const Geom gf = v.back();
+    v.push_back(make_geom((gf.nx + 1) / 2, (gf.ny + 1) / 2, (gf.nz + 1) / 2));
+  }
+  return v;
+}
+
+// Upper estimate of the device bytes a grid with this descriptor allocates, host staging
+// of z, dc/dz and dV/dz included (the allocations of create_impl plus 25 % and 4 MiB for
+// allocation granularity and the captured CG loop).
+size_t estimate_device_bytes(const tomo_grid_desc& d) {
+  const size_t T = d.precision == TOMO_FP64 ? 8 : 4;
+  const std::vector<Geom> lv = plan_levels(d);
+  const Geom& g = lv[0];
+  size_t b = 0;
+  for (size_t l = 0; l < lv.size(); ++l) {
+    const size_t nv = 3 * (size_t)lv[l].nn * T;
+    b += (size_t)lv[l].nel * T + (size_t)lv[l].nn + (l > 0 ? 4 : 3) * nv;
+  }
+  if (d.precond == TOMO_PRECOND_MG) {
+    const size_t nc = 3 * (size_t)lv.back().nn;
+    b += nc * nc * T + nc * T;
+  }
+  const size_t nv = 3 * (size_t)g.nn * T, ne = (size_t)g.nel * T;
+  b += nv + 3 * (size_t)g.nn * 8 + 4 * nv + 4 * ne + 3 * ne;
+  if (d.precision == TOMO_FP32) b += nv + (size_t)g.nel * 8;
+  b += sizeof(double) * (size_t)std::max(1 << 16, oc_partials_needed(g.nel));
+  return b + b / 4 + (4u << 20);
+}
+
 template <typename T>
 tomo_status create_impl(tomo_grid* G) {
   const Geom g = G->g;
@@ -1144,29 +1195,12 @@ tomo_status create_impl(tomo_grid* G) {
     G->L.push_back(std::move(L0));
   }
   if (G->d.precond == TOMO_PRECOND_MG) {
-    const int want = G->d.mg_levels;
-    while (true) {
-      const Geom& gf = G->L.back().g;
-      const int nl = (int)G->L.size();
-      const bool small = 3 * gf.nn <= 192;
-      const bool can = std::max(gf.nx, std::max(gf.ny, gf.nz)) > 1;
-      if (!can) break;
-      if (want > 0 && nl >= want && 3 * gf.nn <= kMaxDenseDofs) break;
-      if (want <= 0 && small) break;
+    const std::vector<Geom> dims = plan_levels(G->d);
+    for (size_t l = 1; l < dims.size(); ++l) {
       tomo_level Lc;
-      Lc.g = make_geom((gf.nx + 1) / 2, (gf.ny + 1) / 2, (gf.nz + 1) / 2);
+      Lc.g = dims[l];
       Lc.h = G->L.back().h * 2.0;
-      Lc.hmask = coarse_mask(gf, G->L.back().hmask, Lc.g);
-      G->L.push_back(std::move(Lc));
-    }
-    if (G->L.size() < 2) {
-      // a single-level grid: the dense solve of the grid itself would be the whole solve;
-      // keep one coarse level so that the V-cycle structure holds
-      const Geom& gf = G->L.back().g;
-      tomo_level Lc;
-      Lc.g = make_geom((gf.nx + 1) / 2, (gf.ny + 1) / 2, (gf.nz + 1) / 2);
-      Lc.h = G->L.back().h * 2.0;
-      Lc.hmask = coarse_mask(gf, G->L.back().hmask, Lc.g);
+      Lc.hmask = coarse_mask(G->L.back().g, G->L.back().hmask, Lc.g);
       G->L.push_back(std::move(Lc));
     }
     G->coarse_n = 3 * G->L.back().g.nn;
@@ -1359,6 +1393,18 @@ tomo_status tomo_destroy_grid(tomo_grid* G) {
   if (!G) return TOMO_OK;
   cudaStreamSynchronize(G->stream);
   free_grid(G);
+  return TOMO_OK;
+}
+
+tomo_status tomo_grid_device_bytes(const tomo_grid* G, size_t* bytes) {
+  if (!G || !bytes) return TOMO_EINVAL;
+  *bytes = G->dev_bytes;
+  return TOMO_OK;
+}
+
+tomo_status tomo_estimate_device_bytes(const tomo_grid_desc* d, size_t* bytes) {
+  if (!d || !bytes || d->nx < 1 || d->ny < 1 || d->nz < 1) return TOMO_EINVAL;
+  *bytes = estimate_device_bytes(*d);
   return TOMO_OK;
 }
 

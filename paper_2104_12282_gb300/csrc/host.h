@@ -231,6 +231,7 @@ struct tomo_grid {
   std::vector<int> ev_tag;          // per event pair: -1 fine-level product, else level + 1
   double level_ms[16] = {};         // eager V-cycle time per level (all kernels), level 0..15
   int64_t level_n[16] = {};
+  size_t dev_bytes = 0;        // device memory held by this grid (cudaMalloc through dalloc)
   bool have_solution = false;
   bool warm_gradient = false;  // tomo_gradient starts CG from the previous solution
   int partials_n = 0;

@@ -1,0 +1,326 @@
+// Request loop for gradient requests on design domains of different sizes.
+//
+// The paper optimises one design at a time; serving many designs at once needs a runtime
+// around the exact-gradient path.  This one is built on the public C ABI only:
+//  * W worker threads, each with its own CUDA stream, take requests as soon as they are
+//    free (continuous batching: a request that arrives while others run starts as soon as a
+//    worker and memory are free, and its kernels overlap theirs on the GPU);
+//  * grids stay resident on the device between requests of the same session (density,
+//    displacement and multigrid state), and are evicted least-recently-used when memory
+//    is needed;
+//  * admission is by device memory: a request is started only when its grid is resident
+//    or its estimated footprint fits the budget after evicting idle grids;
+//  * the queue is served in arrival order among the requests that can be admitted.
+// Each request's work runs in order on one stream and touches only its own grid, so its
+// result is the one it gives alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tomo.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Request {
+  int64_t ticket = 0;
+  int64_t session = -1;
+  tomo_grid_desc desc{};
+  std::vector<uint8_t> fixed;
+  std::vector<double> f;
+  std::vector<float> z;
+  float* dcdz = nullptr;  // caller-owned host outputs
+  float* dvdz = nullptr;
+  size_t est_bytes = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  tomo_result res{};
+  Clock::time_point t_submit, t_start, t_done;
+};
+
+struct Slot {
+  tomo_grid* grid = nullptr;
+  int64_t session = -1;
+  tomo_grid_desc desc{};  // dims and parameters the grid was created with
+  size_t bytes = 0;       // reserved (estimate) or held (measured) device bytes
+  bool busy = false;
+  Clock::time_point last_used;
+};
+
+bool same_problem(const tomo_grid_desc& a, const tomo_grid_desc& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.h == b.h && a.E0 == b.E0 &&
+         a.Emin == b.Emin && a.nu == b.nu && a.penal == b.penal && a.rmin == b.rmin &&
+         a.precision == b.precision && a.precond == b.precond && a.rtol == b.rtol &&
+         a.maxit == b.maxit && a.mg_levels == b.mg_levels &&
+         a.smoother_degree == b.smoother_degree && a.coarse_degree == b.coarse_degree &&
+         a.cheb_ratio == b.cheb_ratio && a.cheb_lmax == b.cheb_lmax && a.rr_every == b.rr_every;
+}
+
+}  // namespace
+
+struct tomo_server {
+  size_t budget = 0;
+  std::vector<std::thread> threads;
+  std::vector<cudaStream_t> streams;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  int64_t next_ticket = 1;
+  std::deque<int64_t> queue;
+  std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
+  std::vector<std::unique_ptr<Slot>> slots;
+  size_t resident = 0;
+  tomo_server_stats stats{};
+  std::string err;
+
+  // Under mu: a slot for request r (resident idle grid of its session, or room for a new
+  // one after evicting idle grids), or nullptr.  Evicted grids are handed back in `dead`.
+  Slot* admit(Request& r, std::vector<tomo_grid*>& dead) {
+    if (r.session >= 0)
+      for (auto& s : slots)
+        if (s->session == r.session && same_problem(s->desc, r.desc)) {
+          if (s->busy) return nullptr;  // the session's grid is in use (or being created)
+          return s.get();
+        }
+    while (resident + r.est_bytes > budget) {
+      Slot* lru = nullptr;
+      for (auto& s : slots)
+        if (!s->busy && (!lru || s->last_used < lru->last_used)) lru = s.get();
+      if (!lru) return nullptr;
+      resident -= lru->bytes;
+      if (lru->grid) dead.push_back(lru->grid);
+      stats.evictions += 1;
+      slots.erase(std::find_if(slots.begin(), slots.end(),
+                               [&](const std::unique_ptr<Slot>& p) { return p.get() == lru; }));
+    }
+    auto s = std::make_unique<Slot>();
+    s->session = r.session;
+    s->desc = r.desc;
+    s->bytes = r.est_bytes;
+    resident += s->bytes;
+    slots.push_back(std::move(s));
+    return slots.back().get();
+  }
+
+  void work(int w) {
+    cudaStream_t st = streams[w];
+    for (;;) {
+      Request* r = nullptr;
+      Slot* slot = nullptr;
+      std::vector<tomo_grid*> dead;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+          if (stop) return;
+          for (auto it = queue.begin(); it != queue.end(); ++it) {
+            Request& q = *reqs[*it];
+            slot = admit(q, dead);
+            if (slot) {
+              r = &q;
+              queue.erase(it);
+              break;
+            }
+          }
+          if (r) break;
+          cv_work.wait(lk);
+        }
+        slot->busy = true;
+        r->state = 1;
+        r->t_start = Clock::now();
+        stats.peak_bytes = std::max<uint64_t>(stats.peak_bytes, resident);
+      }
+      for (tomo_grid* e : dead) {  // evicted idle grids: quiesce on this worker's stream
+        tomo_set_stream(e, st);
+        tomo_destroy_grid(e);
+      }
+      dead.clear();
+      auto note = [&](const char* m) {
+        const size_t n = std::min<size_t>(std::strlen(m), sizeof(r->res.message) - 1);
+        std::memcpy(r->res.message, m, n);
+        r->res.message[n] = 0;
+        r->res.message_len = (int32_t)n;
+      };
+      tomo_status s = TOMO_OK;
+      // the slot is busy: this worker alone touches its grid until it is released below
+      tomo_grid* g = slot->grid;
+      if (!g) {  // create the session's grid on this worker's stream
+        tomo_grid_desc d = r->desc;
+        d.fixed_dof = r->fixed.data();
+        d.f = r->f.data();
+        d.stream = st;
+        s = tomo_create_grid(&d, &g);
+        if (s != TOMO_OK) note(tomo_last_error(nullptr));
+        std::lock_guard<std::mutex> lk(mu);
+        slot->grid = g;
+        if (s == TOMO_OK) stats.grids_created += 1;
+      } else {
+        tomo_set_stream(g, st);
+      }
+      if (s == TOMO_OK) {
+        s = tomo_gradient(g, r->z.data(), &r->res.compliance, r->dcdz, r->dvdz, &r->res.info);
+        if (s == TOMO_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+          cudaGetLastError();
+          s = TOMO_ECUDA;
+        }
+        if (s != TOMO_OK) note(tomo_last_error(g));
+      }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        r->t_done = Clock::now();
+        r->res.status = s;
+        r->res.queue_ms = ms_between(r->t_submit, r->t_start);
+        r->res.run_ms = ms_between(r->t_start, r->t_done);
+        r->state = 2;
+        stats.completed += 1;
+        slot->busy = false;
+        slot->last_used = r->t_done;
+        if (s != TOMO_OK || r->session < 0) {  // no session (or a failure): free at once
+          if (slot->grid) dead.push_back(slot->grid);
+          resident -= slot->bytes;
+          slots.erase(std::find_if(slots.begin(), slots.end(),
+                                   [&](const std::unique_ptr<Slot>& p) {
+                                     return p.get() == slot;
+                                   }));
+        }
+      }
+      for (tomo_grid* e : dead) {
+        tomo_set_stream(e, st);
+        tomo_destroy_grid(e);
+      }
+      dead.clear();
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+  }
+};
+
+extern "C" {
+
+tomo_status tomo_server_create(int32_t workers, uint64_t budget_bytes, tomo_server** out) {
+  if (!out || budget_bytes == 0) return TOMO_EINVAL;
+  *out = nullptr;
+  if (workers <= 0) workers = 8;
+  if (workers > 64) workers = 64;
+  std::unique_ptr<tomo_server> S(new (std::nothrow) tomo_server());
+  if (!S) return TOMO_ENOMEM;
+  S->budget = (size_t)budget_bytes;
+  for (int w = 0; w < workers; ++w) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto t : S->streams) cudaStreamDestroy(t);
+      return TOMO_ECUDA;
+    }
+    S->streams.push_back(s);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int w = 0; w < workers; ++w)
+    S->threads.emplace_back([srv = S.get(), w, dev] {
+      cudaSetDevice(dev);
+      srv->work(w);
+    });
+  *out = S.release();
+  return TOMO_OK;
+}
+
+tomo_status tomo_server_submit(tomo_server* S, const tomo_grid_desc* desc, int64_t session,
+                               const float* z, float* dcdz, float* dvdz, int64_t* ticket) {
+  if (!S || !desc || !z || !dcdz || !ticket || !desc->fixed_dof || !desc->f) return TOMO_EINVAL;
+  if (desc->precision != TOMO_FP32) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->err = "the request loop serves FP32 grids";
+    return TOMO_EINVAL;
+  }
+  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1) return TOMO_EINVAL;
+  auto r = std::make_unique<Request>();
+  r->session = session;
+  r->desc = *desc;
+  const size_t nn = (size_t)(desc->nx + 1) * (desc->ny + 1) * (desc->nz + 1);
+  const size_t ne = (size_t)desc->nx * desc->ny * desc->nz;
+  r->fixed.assign(desc->fixed_dof, desc->fixed_dof + 3 * nn);
+  r->f.assign(desc->f, desc->f + 3 * nn);
+  r->z.assign(z, z + ne);
+  r->desc.fixed_dof = nullptr;
+  r->desc.f = nullptr;
+  r->desc.stream = nullptr;
+  r->dcdz = dcdz;
+  r->dvdz = dvdz;
+  size_t est = 0;
+  tomo_estimate_device_bytes(desc, &est);
+  r->est_bytes = est;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (est > S->budget) {
+    S->err = "request needs more device memory than the server's budget";
+    return TOMO_ENOMEM;
+  }
+  r->t_submit = Clock::now();
+  r->ticket = S->next_ticket++;
+  *ticket = r->ticket;
+  S->queue.push_back(r->ticket);
+  S->reqs[r->ticket] = std::move(r);
+  S->stats.submitted += 1;
+  S->cv_work.notify_one();
+  return TOMO_OK;
+}
+
+tomo_status tomo_server_wait(tomo_server* S, int64_t ticket, tomo_result* result) {
+  if (!S || !result) return TOMO_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) {
+    S->err = "unknown ticket";
+    return TOMO_EINVAL;
+  }
+  S->cv_done.wait(lk, [&] { return it->second->state == 2; });
+  *result = it->second->res;
+  result->ticket = ticket;
+  S->reqs.erase(it);
+  return TOMO_OK;
+}
+
+tomo_status tomo_server_get_stats(tomo_server* S, tomo_server_stats* st) {
+  if (!S || !st) return TOMO_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  *st = S->stats;
+  st->resident_bytes = S->resident;
+  st->resident_grids = (int32_t)S->slots.size();
+  st->queued = (int32_t)S->queue.size();
+  return TOMO_OK;
+}
+
+tomo_status tomo_server_destroy(tomo_server* S) {
+  if (!S) return TOMO_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->threads) t.join();
+  for (auto& s : S->slots)
+    if (s->grid) tomo_destroy_grid(s->grid);
+  for (auto s : S->streams) cudaStreamDestroy(s);
+  delete S;
+  return TOMO_OK;
+}
+
+const char* tomo_server_last_error(const tomo_server* S) {
+  if (!S) return "";
+  return S->err.c_str();
+}
+
+}  // extern "C"

@@ -238,6 +238,30 @@ def uneven_cantilever_batch(seed: int = 0, count: int = 64) -> List[Problem]:
     return out
 
 
+def served_request(seed: int, index: int, n_range=(12, 64)) -> Problem:
+    """One request of a served stream: a 2n x n x n domain, n ~ U{n_range}, either the
+    cantilever with one loaded node drawn on the face x = nx or the MBB-type block; volume
+    fraction ~ U[0.1, 0.4], rmin ~ U[1.2, 2.5]; design field U[0.05, 1]."""
+    rng = np.random.default_rng([seed, index])
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    vf = float(rng.uniform(0.1, 0.4))
+    rm = float(rng.uniform(1.2, 2.5))
+    if rng.uniform() < 0.5:
+        p = cantilever(2 * n, n, n, volfrac=vf, rmin=rm)
+        d = p.dims
+        p.f[:] = 0.0
+        jj = int(rng.integers(0, n + 1))
+        kk = int(rng.integers(0, n + 1))
+        p.f[2 * d.n_nodes + d.node(2 * n, jj, kk)] = -1.0
+        p.name = f"served_cantilever_{index}"
+    else:
+        p = mbb_block(2 * n, n, n, volfrac=vf, rmin=rm)
+        p.name = f"served_mbb_{index}"
+    p.z0 = random_field(p.dims, int(rng.integers(0, 2 ** 31)), 0.05, 1.0)
+    p.meta["request"] = index
+    return p
+
+
 def table1_meshes():
     """Cantilever meshes of Table 1 on a 2:1:1 domain: (fine dims, N_B)."""
     return [((70, 35, 35), 5), ((100, 50, 50), 5), ((180, 90, 90), 5)]

@@ -1,0 +1,85 @@
+"""A served request stream through the request loop (``tomo.Server``): Poisson arrivals of
+gradient requests on 2n x n x n domains of different sizes (seeded supports, loads and
+density fields), device-resident grids, admission under a device-memory budget; reports
+p50/p99 latency and throughput, next to serial FP64 GPU gradients on a sample of the same
+requests.
+
+    python -m paper_2104_12282_gb300.serve --requests 1000 --rate 200 --budget-gb 150
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+import sys
+import time
+
+import numpy as np
+
+from . import problems as P
+from . import tomo
+
+
+def percentile(xs, q):
+    s = sorted(xs)
+    return s[min(len(s) - 1, int(round(q * (len(s) - 1))))]
+
+
+def run_stream(n_requests=1000, rate=200.0, seed=0, workers=16, budget_bytes=150 << 30,
+               n_range=(12, 64), serial_sample=12):
+    reqs = [P.served_request(seed, i, n_range) for i in range(n_requests)]
+    gaps = np.random.default_rng([seed, 1]).exponential(1.0 / rate, size=n_requests)
+    arrive = np.cumsum(gaps)
+    lat, qms = [], []
+    with tomo.Server(workers=workers, budget_bytes=budget_bytes) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for p, ta in zip(reqs, arrive):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(p))
+        for t in tickets:
+            r, _, _ = srv.wait(t)
+            if r.status != 0:
+                raise RuntimeError(f"request {t} failed: {r.message.decode()}")
+            lat.append(r.queue_ms + r.run_ms)
+            qms.append(r.queue_ms)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    # serial FP64 GPU gradients on a sample of the same requests (one at a time)
+    import torch
+    ser = []
+    for p in reqs[:serial_sample]:
+        with tomo.Grid.from_problem(p, precision=tomo.FP64) as g:
+            z = torch.tensor(p.z0, dtype=torch.float64, device="cuda")
+            dc = torch.empty_like(z)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            g.gradient(z, dc)
+            torch.cuda.synchronize()
+            ser.append((time.perf_counter() - t) * 1e3)
+    return {
+        "requests": n_requests, "rate_per_s": rate, "workers": workers,
+        "budget_gb": budget_bytes / 2 ** 30, "sizes": f"2n x n x n, n ~ U{{{n_range[0]}..{n_range[1]}}}",
+        "throughput_per_s": n_requests / wall, "p50_ms": percentile(lat, 0.5),
+        "p99_ms": percentile(lat, 0.99), "queue_p99_ms": percentile(qms, 0.99),
+        "serial_fp64_ms_mean": statistics.mean(ser), "serial_fp64_per_s": 1e3 / statistics.mean(ser),
+        "grids_created": st["grids_created"], "evictions": st["evictions"],
+        "peak_resident_gb": st["peak_bytes"] / 2 ** 30}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    out = run_stream(a.requests, a.rate, a.seed, a.workers, int(a.budget_gb * 2 ** 30))
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

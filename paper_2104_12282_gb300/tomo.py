@@ -48,6 +48,20 @@ class SolveInfo(ctypes.Structure):
                 ("status", ctypes.c_int32), ("mg_levels", ctypes.c_int32)]
 
 
+class Result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("compliance", ctypes.c_double), ("info", SolveInfo),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("message_len", ctypes.c_int32), ("message", ctypes.c_char * 256)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("grids_created", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("resident_bytes", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("resident_grids", ctypes.c_int32), ("queued", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libtomo.so is not built ({LIB_PATH}); run "
@@ -62,6 +76,17 @@ def _load():
         "tomo_destroy_grid": (st, [G]),
         "tomo_set_stream": (st, [G, P]),
         "tomo_set_warm_start": (st, [G, ctypes.c_int32]),
+        "tomo_server_create": (st, [ctypes.c_int32, ctypes.c_uint64,
+                                    ctypes.POINTER(ctypes.c_void_p)]),
+        "tomo_server_submit": (st, [P, ctypes.POINTER(GridDesc), ctypes.c_int64, P, P, P,
+                                    ctypes.POINTER(ctypes.c_int64)]),
+        "tomo_server_wait": (st, [P, ctypes.c_int64, ctypes.POINTER(Result)]),
+        "tomo_server_get_stats": (st, [P, ctypes.POINTER(ServerStats)]),
+        "tomo_server_destroy": (st, [P]),
+        "tomo_server_last_error": (ctypes.c_char_p, [P]),
+        "tomo_grid_device_bytes": (st, [G, ctypes.POINTER(ctypes.c_size_t)]),
+        "tomo_estimate_device_bytes": (st, [ctypes.POINTER(GridDesc),
+                                            ctypes.POINTER(ctypes.c_size_t)]),
         "tomo_batch_create": (st, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
         "tomo_batch_append": (st, [P, G]),
         "tomo_batch_size": (st, [P, ctypes.POINTER(ctypes.c_int32)]),
@@ -133,7 +158,10 @@ def lib():
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["tomo_default_desc", "tomo_create_grid", "tomo_destroy_grid", "tomo_set_stream",
-            "tomo_set_warm_start", "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
+            "tomo_set_warm_start", "tomo_server_create", "tomo_server_submit",
+            "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
+            "tomo_server_last_error", "tomo_grid_device_bytes", "tomo_estimate_device_bytes",
+            "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
             "tomo_batch_gradient", "tomo_batch_destroy", "tomo_batch_last_error",
             "tomo_filter", "tomo_filter_d", "tomo_coarse_grain", "tomo_coarse_grain_d",
             "tomo_adjoint_gradient", "tomo_adjoint_gradient_d",
@@ -342,6 +370,14 @@ class Grid:
         mk = lambda i: Info(i.iters, i.rel_res, i.status, i.mg_levels)  # noqa: E731
         return J.value, mk(iu), mk(il)
 
+    def device_bytes(self) -> int:
+        """Device memory held by this grid (tomo_grid_device_bytes)."""
+        n = ctypes.c_size_t()
+        st = lib().tomo_grid_device_bytes(self._h, ctypes.byref(n))
+        if st != 0:
+            raise TomoError(st, "tomo_grid_device_bytes")
+        return n.value
+
     def get_displacement(self, u):
         self._call("tomo_get_displacement", self._n(u, "u"))
 
@@ -452,6 +488,96 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().tomo_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _problem_desc(p, precision=FP32, **kw):
+    """A filled GridDesc for problem p (arrays referenced, not copied: keep p alive)."""
+    L = lib()
+    d = GridDesc()
+    L.tomo_default_desc(ctypes.byref(d))
+    dims = p.dims
+    d.nx, d.ny, d.nz = dims.nx, dims.ny, dims.nz
+    d.h, d.E0, d.Emin, d.nu, d.penal, d.rmin = p.h, p.E0, p.Emin, p.nu, p.penal, p.rmin
+    fixed = np.ascontiguousarray(p.fixed.astype(np.uint8))
+    f = np.ascontiguousarray(p.f.astype(np.float64))
+    d.fixed_dof = fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    d.f = f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.precision = precision
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d, (fixed, f)
+
+
+def estimate_device_bytes(p, precision=FP32):
+    d, keep = _problem_desc(p, precision)
+    n = ctypes.c_size_t()
+    st = lib().tomo_estimate_device_bytes(ctypes.byref(d), ctypes.byref(n))
+    if st != 0:
+        raise TomoError(st, "tomo_estimate_device_bytes")
+    return n.value
+
+
+class Server:
+    """The request loop (``tomo_server_*``): gradient requests on grids of different sizes,
+    ``workers`` threads with a stream each, grids resident per session, admission under a
+    device-memory budget (bytes)."""
+
+    def __init__(self, workers=8, budget_bytes=8 << 30):
+        h = ctypes.c_void_p()
+        st = lib().tomo_server_create(int(workers), int(budget_bytes), ctypes.byref(h))
+        if st != 0:
+            raise TomoError(st, "tomo_server_create")
+        self._h = h
+        self._pending = {}
+
+    def submit(self, p, z=None, session=-1, dvdz=True):
+        """Queue tomo_gradient for problem p (FP32) with design z (default p.z0); returns a
+        ticket.  Outputs are host arrays held until ``wait``."""
+        d, keep = _problem_desc(p, FP32)
+        zz = np.ascontiguousarray(np.asarray(p.z0 if z is None else z, np.float32))
+        dc = np.empty(p.n_el, np.float32)
+        dv = np.empty(p.n_el, np.float32) if dvdz else None
+        t = ctypes.c_int64()
+        st = lib().tomo_server_submit(self._h, ctypes.byref(d), int(session),
+                                      zz.ctypes.data_as(ctypes.c_void_p),
+                                      dc.ctypes.data_as(ctypes.c_void_p),
+                                      dv.ctypes.data_as(ctypes.c_void_p) if dv is not None
+                                      else None, ctypes.byref(t))
+        if st != 0:
+            raise TomoError(st, lib().tomo_server_last_error(self._h).decode())
+        self._pending[t.value] = (dc, dv, keep, zz)
+        return t.value
+
+    def wait(self, ticket):
+        """Returns (Result, dcdz, dvdz) for a ticket."""
+        r = Result()
+        st = lib().tomo_server_wait(self._h, int(ticket), ctypes.byref(r))
+        if st != 0:
+            raise TomoError(st, lib().tomo_server_last_error(self._h).decode())
+        dc, dv, _, _ = self._pending.pop(ticket)
+        return r, dc, dv
+
+    def stats(self):
+        s = ServerStats()
+        lib().tomo_server_get_stats(self._h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tomo_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,75 @@
+"""The request loop (tomo_server_*): each result in the mix equals the request's result
+alone, under eviction pressure; admission respects the memory budget."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_2104_12282_gb300 import problems as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+from paper_2104_12282_gb300 import tomo  # noqa: E402
+
+
+def _alone(p):
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        z = np.asarray(p.z0, np.float32)
+        dc = np.empty(p.n_el, np.float32)
+        dv = np.empty(p.n_el, np.float32)
+        c, info = g.gradient(z, dc, dv)
+    return c, dc, dv
+
+
+def test_results_in_the_mix_equal_results_alone():
+    reqs = [P.served_request(3, i, (6, 16)) for i in range(14)]
+    # three sessions repeat their problem (device-resident grids reused)
+    sessions = [i % 3 if i < 9 else -1 for i in range(len(reqs))]
+    for i in range(3, 9):
+        reqs[i] = reqs[i % 3]
+    budget = 3 * max(tomo.estimate_device_bytes(p) for p in reqs)  # forces evictions
+    with tomo.Server(workers=4, budget_bytes=budget) as srv:
+        tickets = [srv.submit(p, session=s) for p, s in zip(reqs, sessions)]
+        got = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["peak_bytes"] <= budget
+    assert st["grids_created"] < len(reqs)          # sessions reused their grids
+    for p, (r, dc, dv) in zip(reqs, got):
+        assert r.status == 0, r.message
+        c, dc0, dv0 = _alone(p)
+        assert r.compliance == c
+        assert np.array_equal(dc, dc0) and np.array_equal(dv, dv0)
+
+
+def test_eviction_under_a_tight_budget():
+    reqs = [P.served_request(4, i, (8, 14)) for i in range(8)]
+    budget = max(tomo.estimate_device_bytes(p) for p in reqs) + (1 << 20)
+    with tomo.Server(workers=3, budget_bytes=budget) as srv:
+        tickets = [srv.submit(p, session=i) for i, p in enumerate(reqs)]
+        res = [srv.wait(t)[0] for t in tickets]
+        st = srv.stats()
+    assert all(r.status == 0 for r in res)
+    assert st["evictions"] >= len(reqs) - 1 and st["peak_bytes"] <= budget
+
+
+def test_oversized_request_is_rejected():
+    p = P.served_request(5, 0, (20, 20))
+    with tomo.Server(workers=2, budget_bytes=1 << 20) as srv:
+        with pytest.raises(tomo.TomoError):
+            srv.submit(p)
+
+
+def test_estimate_bounds_the_device_memory_of_a_grid():
+    for p in (P.cantilever(24, 12, 12), P.mbb_block(33, 17, 9), P.served_request(6, 2, (30, 30))):
+        est = tomo.estimate_device_bytes(p)
+        with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+            z = np.asarray(p.z0, np.float32)
+            dc = np.empty(p.n_el, np.float32)
+            dv = np.empty(p.n_el, np.float32)
+            g.gradient(z, dc, dv)       # host arrays: staging buffers allocated
+            held = g.device_bytes()
+        assert held <= est <= 2 * held + (8 << 20), (p.name, held, est)

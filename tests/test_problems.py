@@ -91,3 +91,15 @@ def test_batch_generator_ranges():
         assert 16 <= d.nx <= 64 and 16 <= d.ny <= 32 and 16 <= d.nz <= 32
         assert 0.2 <= p.volfrac <= 0.5 and 1.2 <= p.rmin <= 2.0
         assert np.isclose(p.f.sum(), -1.0) and np.count_nonzero(p.f) == 1
+
+
+def test_served_requests_are_seeded_and_shaped():
+    a = [P.served_request(7, i) for i in range(20)]
+    b = [P.served_request(7, i) for i in range(20)]
+    for p, q in zip(a, b):
+        d = p.dims
+        assert d.nx == 2 * d.ny == 2 * d.nz and 12 <= d.ny <= 64
+        assert np.array_equal(p.z0, q.z0) and np.array_equal(p.f, q.f)
+        assert abs(p.f.sum() + 1.0) <= 1e-12
+        assert 0.05 <= p.z0.min() and p.z0.max() <= 1.0
+    assert len({p.dims.ny for p in a}) > 5
