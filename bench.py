@@ -122,6 +122,24 @@ def cpu_baseline(seed, reps=3):
                        f"(flatters the CPU: Jacobi-PCG iteration counts grow with the grid)")}
 
 
+def cpu_baseline_one_core(seed):
+    """The same oracle sample with every BLAS/OpenMP pool held to one thread (a child
+    process, so the setting takes effect before numpy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(%d)))" % (ROOT, seed))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"unavailable": r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
+    dt, cores, n_sample = json.loads(r.stdout.strip().splitlines()[-1])
+    from paper_2104_12282_gb300 import problems as P
+    full = P.GridDims(192, 96, 76).n_el
+    return {"value": (n_sample / full) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"as cpu_baseline, one run with thread pools held to 1 ({dt:.2f} s)"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -488,6 +506,7 @@ def run_ours(args):
     }
     if world == 1:
         out["cpu_baseline"] = cpu_baseline(args.seed)
+        out["cpu_baseline_one_core"] = cpu_baseline_one_core(args.seed)
         out.update(extras(args, dev, stream))
     print(json.dumps(out), flush=True)
     if dist is not None:

@@ -242,36 +242,51 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(Geom g, const T* __restr
   extern __shared__ unsigned char smem_raw[];
   T* col = reinterpret_cast<T*>(smem_raw);  // 4n: pivot column and row snapshots
   T* M = SMEM ? col + 4 * n : A;            // the working matrix: shared memory when it fits
-  for (int q = tid; q < n * n; q += nt) M[q] = T(0);
+  T* s_sm = SMEM ? M + (size_t)n * n : col + 4 * n;           // element moduli
+  uint8_t* m_sm = reinterpret_cast<uint8_t*>(s_sm + g.nel);  // fixed bits per node
+  for (int e = tid; e < g.nel; e += nt) s_sm[e] = s[e];
+  for (int q = tid; q < g.nn; q += nt) m_sm[q] = mask[q];
   __syncthreads();
-  for (int e = 0; e < g.nel; ++e) {
-    const int ei = e % g.nx, ej = (e / g.nx) % g.ny, ek = e / (g.nx * g.ny);
-    const T se = s[e];
-    for (int pq = tid; pq < 576; pq += nt) {
-      const int p = pq / 24, q = pq % 24;
-      const int a = p / 3, c = p % 3, b = q / 3, d = q % 3;
-      const int na = (ei + (a & 1)) + g.nxn * ((ej + ((a >> 1) & 1)) + g.nyn * (ek + (a >> 2)));
-      const int nb = (ei + (b & 1)) + g.nxn * ((ej + ((b >> 1) & 1)) + g.nyn * (ek + (b >> 2)));
-      if (((mask[na] >> c) & 1u) || ((mask[nb] >> d) & 1u)) continue;
-      M[(size_t)(c * g.nn + na) * n + d * g.nn + nb] += se * K0.k[pq];
+  // Entry (r, c), r = cr N_n + nr: sum over the elements shared by nodes nr and nc of
+  // s_e K0[(a_r, cr), (a_c, cc)]; rows and columns of fixed DOFs are those of the identity.
+  for (int q = tid; q < n * n; q += nt) {
+    const int r = q / n, c = q - (q / n) * n;
+    const int cr = r / g.nn, nr = r - cr * g.nn, cc = c / g.nn, nc = c - cc * g.nn;
+    T v = T(0);
+    if (((m_sm[nr] >> cr) & 1u) || ((m_sm[nc] >> cc) & 1u)) {
+      v = (r == c) ? T(1) : T(0);
+    } else {
+      const int ir = nr % g.nxn, jr = (nr / g.nxn) % g.nyn, kr = nr / (g.nxn * g.nyn);
+      const int ic = nc % g.nxn, jc = (nc / g.nxn) % g.nyn, kc = nc / (g.nxn * g.nyn);
+      const int x0 = max(max(ir, ic) - 1, 0), x1 = min(min(ir, ic), g.nx - 1);
+      const int y0 = max(max(jr, jc) - 1, 0), y1 = min(min(jr, jc), g.ny - 1);
+      const int z0 = max(max(kr, kc) - 1, 0), z1 = min(min(kr, kc), g.nz - 1);
+      for (int ez = z0; ez <= z1; ++ez)
+        for (int ey = y0; ey <= y1; ++ey)
+          for (int ex = x0; ex <= x1; ++ex) {
+            const int ar = (ir - ex) + 2 * (jr - ey) + 4 * (kr - ez);
+            const int ac = (ic - ex) + 2 * (jc - ey) + 4 * (kc - ez);
+            v += s_sm[ex + g.nx * (ey + g.ny * ez)] * K0.k[(3 * ar + cr) * 24 + 3 * ac + cc];
+          }
     }
-    __syncthreads();
+    M[q] = v;
   }
+  __syncthreads();
+  T* ds = col;  // D^-1/2 (the snapshot buffers are free until the elimination)
   for (int q = tid; q < n; q += nt) {
-    const int node = q % g.nn, c = q / g.nn;
-    if ((mask[node] >> c) & 1u) M[(size_t)q * n + q] = T(1);
     T dv = M[(size_t)q * n + q];
     if (!(dv > T(0))) {
       atomicOr(status, DEV_BREAKDOWN);
       dv = T(1);
       M[(size_t)q * n + q] = T(1);
     }
-    dscale[q] = T(1) / sqrt(dv);
+    ds[q] = T(1) / sqrt(dv);
+    dscale[q] = ds[q];
   }
   __syncthreads();
   for (int q = tid; q < n * n; q += nt) {
-    const int a = q / n, b = q % n;
-    M[q] *= dscale[a] * dscale[b];
+    const int a = q / n, b = q - (q / n) * n;
+    M[q] *= ds[a] * ds[b];
   }
   __syncthreads();
   // In-place Gauss-Jordan inversion of the scaled SPD matrix (no pivoting).  Each thread
@@ -324,7 +339,8 @@ template <typename T>
 cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint8_t* mask,
                                  const DenseK0<T>& K0, T* A, T* dscale, unsigned* status) {
   const int n = 3 * g.nn;
-  const size_t full = sizeof(T) * ((size_t)n * n + 4 * n);
+  const size_t extra = sizeof(T) * (size_t)g.nel + (size_t)g.nn + 16;
+  const size_t full = sizeof(T) * ((size_t)n * n + 4 * n) + extra;
   if (full <= 200 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_coarse_factor<T, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -332,7 +348,8 @@ cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint
     if (e != cudaSuccess) return e;
     pdl_launch(k_coarse_factor<T, true>, 1, 1024, full, st, g, s, mask, K0, A, dscale, status);
   } else {
-    pdl_launch(k_coarse_factor<T, false>, 1, 1024, sizeof(T) * 4 * (size_t)n, st, g, s, mask, K0, A, dscale,
+    pdl_launch(k_coarse_factor<T, false>, 1, 1024, sizeof(T) * 4 * (size_t)n + extra, st, g, s,
+               mask, K0, A, dscale,
                                                                       status);
   }
   return cudaGetLastError();

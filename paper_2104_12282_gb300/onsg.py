@@ -1,0 +1,199 @@
+"""Online neural synthetic gradients (Algorithm 1) on top of the exact-gradient library.
+
+Algorithm 1 alternates exact gradients (this library's tomo_gradient) with gradients
+predicted by a model trained online on the exact ones.  Two-scale features (§III-C): the
+design is cut into N_B x N_B x N_B blocks; one training sample per block holds the block's
+design values and the coarse-scale displacements u_C at the 8 corners of its coarse
+element (the coarse state of Algorithm 1, solved with this library on the coarse grid),
+and its target is the exact gradient on the block's elements.  Schedule: exact gradients
+on the first N_I iterations and then every N_F-th (§IV: N_I = N_F = 10).  Model: a
+fully-connected network with 4 hidden layers of width 1000 (the cantilever setting of §IV;
+with 125 + 24 inputs and 125 outputs it has the 3.3M parameters of Table 3), Adam at
+learning rate 5e-4 halved every 500 optimiser steps.
+
+Readings (the paper does not state them): ReLU activations; plain (not concatenated)
+layers, which is what Table 3's parameter count implies; targets are g / s with s the
+iteration's mean |g| (the OC update is invariant to a positive scale of the gradient, so
+only the pattern has to be learned; log(-g / s) targets measured worse); corner displacements taken relative to the coarse element's mean
+(rigid translation removed) and scaled by their RMS; 70 optimiser steps of batch 4096 per
+exact iteration (about 2000 in a 200-iteration run, §IV); TF32 matrix products.  One more
+input per block, the log of the coarse-scale sensitivity of its coarse element (from u_C,
+normalised like the targets): u_C is what §III-C feeds the model, and this is the part of
+it that the compliance gradient depends on.
+
+The model runs in PyTorch (cuBLAS GEMMs); it is outside the exact-gradient path.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import problems as P
+from . import tomo
+
+
+def block_features(z, dims, nb, uc, cdims):
+    """Per-block inputs (blocks x (nb^3 + 24)): the block's z values in x-fastest order and
+    u_C at the coarse element's 8 corners (corner s = sx + 2 sy + 4 sz, components x,y,z).
+    Requires dims divisible by nb.  Works on torch tensors or numpy arrays."""
+    import torch
+    nx, ny, nz = dims
+    cx, cy, cz = cdims
+    Z = z.reshape(cz, nb, cy, nb, cx, nb).permute(0, 2, 4, 1, 3, 5).reshape(cz * cy * cx, -1)
+    nn = (cx + 1) * (cy + 1) * (cz + 1)
+    K, J, I = torch.meshgrid(torch.arange(cz, device=z.device), torch.arange(cy, device=z.device),
+                             torch.arange(cx, device=z.device), indexing="ij")
+    I, J, K = I.reshape(-1), J.reshape(-1), K.reshape(-1)
+    cols = []
+    for s in range(8):
+        n = (I + (s & 1)) + (cx + 1) * ((J + ((s >> 1) & 1)) + (cy + 1) * (K + (s >> 2)))
+        for c in range(3):
+            cols.append(uc[c * nn + n])
+    U = torch.stack(cols, dim=1)
+    return torch.cat([Z, U], dim=1)
+
+
+def block_gradient(g, dims, nb, cdims):
+    """Targets (blocks x nb^3) in the same block order as block_features."""
+    cx, cy, cz = cdims
+    return g.reshape(cz, nb, cy, nb, cx, nb).permute(0, 2, 4, 1, 3, 5).reshape(cz * cy * cx, -1)
+
+
+def scatter_blocks(gb, dims, nb, cdims):
+    """Inverse of block_gradient: element array from per-block values."""
+    cx, cy, cz = cdims
+    return gb.reshape(cz, cy, cx, nb, nb, nb).permute(0, 3, 1, 4, 2, 5).reshape(-1)
+
+
+def make_model(n_in, n_out, width=1000, depth=4):
+    import torch.nn as nn
+    layers, d = [], n_in
+    for _ in range(depth):
+        layers += [nn.Linear(d, width), nn.ReLU()]
+        d = width
+    layers.append(nn.Linear(d, n_out))
+    return nn.Sequential(*layers)
+
+
+def run(problem, iters, *, block=5, n_init=10, n_every=10, width=1000, lr=5e-4,
+        steps_per_update=70, batch=4096, seed=0, exact_only=False, callback=None,
+        log_targets=False, relative_u=True, tf32=True, coarse_sens=True):
+    """Algorithm 1 on the GPU (exact_only: the exact-gradient optimiser, no coarse step).
+    Returns (z, history, final compliance); each record holds the compliance of the design
+    the step started from when the step was exact (else None), whether the gradient was
+    exact, and the time of the iteration."""
+    import torch
+
+    d = problem.dims
+    if d.nx % block or d.ny % block or d.nz % block:
+        raise ValueError("ONSG blocks need dimensions divisible by the block size")
+    torch.manual_seed(seed)
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    dev = torch.device("cuda", torch.cuda.current_device())
+    q = P.coarse_problem(problem, block)
+    cdims = (q.dims.nx, q.dims.ny, q.dims.nz)
+    nb3 = block ** 3
+    z = torch.tensor(np.asarray(problem.z0), dtype=torch.float32, device=dev)
+    zn, dc, dv = torch.empty_like(z), torch.empty_like(z), torch.empty_like(z)
+    zc = torch.empty(q.n_el, dtype=torch.float32, device=dev)
+    uc = torch.zeros(q.dims.n_dof, dtype=torch.float32, device=dev)
+    n_in = nb3 + 24 + (1 if coarse_sens else 0)
+    model = make_model(n_in, nb3, width).to(dev)
+    dcC = torch.empty(q.n_el, dtype=torch.float32, device=dev)
+    opt = torch.optim.Adam(model.parameters(), lr=lr)
+    sched = torch.optim.lr_scheduler.StepLR(opt, step_size=500, gamma=0.5)
+    X_all, Y_all = [], []
+    hist = []
+    with tomo.Grid.from_problem(problem, precision=tomo.FP32) as g, \
+            tomo.Grid.from_problem(q, precision=tomo.FP32) as gc:
+        g.set_warm_start(True)
+        gc.set_warm_start(True)
+        for k in range(iters):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            exact = exact_only or k < n_init or (k - n_init) % n_every == n_every - 1
+            if not exact_only:   # coarse-grain, coarse state (Algorithm 1, first two steps)
+                g.coarse_grain(z, block, zc)
+                gc.solve(zc, uc)
+                feats = block_features(z, (d.nx, d.ny, d.nz), block, uc, cdims)
+                U = feats[:, nb3:].reshape(-1, 8, 3)
+                if relative_u:   # corner displacements relative to the element's mean
+                    U = U - U.mean(dim=1, keepdim=True)
+                U = U / torch.sqrt(torch.mean(U * U)).clamp_min(1e-30)
+                parts = [feats[:, :nb3], U.reshape(-1, 24)]
+                if coarse_sens:   # the coarse-scale sensitivity of the block's coarse element
+                    gc.sensitivity(zc, uc, dcC)
+                    sC = (-dcC / dcC.abs().mean().clamp_min(1e-30)).clamp_min(1e-12)
+                    parts.append(torch.log(sC)[:, None])
+                feats = torch.cat(parts, dim=1)
+            c = None
+            if exact:
+                c, info = g.gradient(z, dc, dv)
+                gb = block_gradient(dc, (d.nx, d.ny, d.nz), block, cdims)
+                scale = gb.abs().mean().clamp_min(1e-30)
+                if not exact_only:
+                    X_all.append(feats)
+                    if log_targets:   # compliance gradients are <= 0: learn log of -g/scale
+                        Y_all.append(torch.log((-gb / scale).clamp_min(1e-12)))
+                    else:
+                        Y_all.append(gb / scale)
+                    X = torch.cat(X_all)
+                    Y = torch.cat(Y_all)
+                    model.train()
+                    for _ in range(steps_per_update):
+                        idx = torch.randint(0, X.shape[0], (min(batch, X.shape[0]),),
+                                            device=dev)
+                        loss = torch.mean((model(X[idx]) - Y[idx]) ** 2)
+                        opt.zero_grad(set_to_none=True)
+                        loss.backward()
+                        opt.step()
+                        sched.step()
+            else:
+                model.eval()
+                with torch.no_grad():
+                    pred = model(feats)
+                    if log_targets:
+                        pred = -torch.exp(pred.clamp(max=30.0))
+                # dV/dz is design independent: the first (exact) iteration computed it
+                dc.copy_(scatter_blocks(pred, (d.nx, d.ny, d.nz), block, cdims))
+            change = g.oc_step(z, dc, dv, problem.volfrac, problem.move, zn)
+            torch.cuda.synchronize()
+            rec = dict(it=k, exact=exact, c=c, change=change,
+                       ms=(time.perf_counter() - t0) * 1e3)
+            hist.append(rec)
+            if callback:
+                callback(rec)
+            z, zn = zn, z
+        # compliance of the final design (one exact evaluation, not part of the run)
+        c_final, _ = g.gradient(z, dc, dv)
+    return z, hist, c_final
+
+
+def main(argv=None):
+    import argparse
+    import json
+
+    from .optimize import paper_cantilever
+    ap = argparse.ArgumentParser(description="Algorithm 1 (ONSG) against exact gradients on "
+                                             "the cantilever meshes of Table 1")
+    ap.add_argument("--mesh", type=int, default=1)
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--block", type=int, default=5)
+    a = ap.parse_args(argv)
+    p = paper_cantilever(a.mesh)
+    out = {"mesh": a.mesh, "dims": [p.dims.nx, p.dims.ny, p.dims.nz], "iters": a.iters,
+           "block": a.block}
+    run(p, 12, block=a.block)  # warm-up: CUDA context, cuBLAS, captured CG loops
+    for name, kw in (("exact", dict(exact_only=True)), ("onsg", {})):
+        t = time.perf_counter()
+        _, hist, c = run(p, a.iters, block=a.block, **kw)
+        out[name] = {"final_c": c, "wall_s": time.perf_counter() - t,
+                     "exact_gradients": sum(r["exact"] for r in hist)}
+    out["speedup"] = out["exact"]["wall_s"] / out["onsg"]["wall_s"]
+    out["c_difference"] = out["onsg"]["final_c"] / out["exact"]["final_c"] - 1.0
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -142,3 +142,20 @@ def test_optimisation_driver_follows_the_oracle():
     _, hist32 = optimize.run(p, 6, block=4, precision=tomo.FP32)
     for r, ref in zip(hist32, hist_ref):
         assert abs(r["c"] / ref["c"] - 1.0) <= 1e-5, (r, ref)
+
+
+def test_synthetic_gradients_follow_the_exact_optimiser():
+    """Algorithm 1 (ONSG) on a small cantilever: exact gradients on iterations 0-9 and every
+    10th after, synthetic ones (model trained online) in between.  The run completes with a
+    design whose compliance is finite and of the exact optimiser's order: the quality of
+    the synthetic gradients depends on readings the paper leaves open (features, training),
+    and measured at the paper's meshes it stays 11-38 % above the exact optimiser."""
+    from paper_2104_12282_gb300 import onsg
+
+    p = P.cantilever(40, 20, 20, volfrac=0.12, rmin=2.0)
+    _, h_ex, c_ex = onsg.run(p, 40, block=5, exact_only=True)
+    _, h_sg, c_sg = onsg.run(p, 40, block=5)
+    assert sum(r["exact"] for r in h_ex) == 40
+    assert sum(r["exact"] for r in h_sg) == 10 + 3
+    assert all(r["c"] is not None for r in h_sg if r["exact"])
+    assert np.isfinite(c_sg) and 0.5 * c_ex <= c_sg <= 10.0 * c_ex
