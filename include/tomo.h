@@ -30,9 +30,10 @@
  * Precision: a grid is created in one precision.  TOMO_FP64 grids take the *_d entry
  * points (double arrays) and compute everything in FP64.  TOMO_FP32 grids take the float
  * entry points: matrix-free products and multigrid smoothing in FP32, the CG iterate kept
- * as an unevaluated float pair (about 48 significant bits), inner products, residual
- * replacement, the compliance and the OC volume sums in FP64.  Calling an entry point of the
- * other precision returns TOMO_EINVAL.
+ * as an unevaluated float pair (about 48 significant bits), inner products as per-thread
+ * float pairs (TwoSum) summed in FP64 across threads, residual replacement, the compliance
+ * and the OC volume sums in FP64.  Calling an entry point of the other precision returns
+ * TOMO_EINVAL.
  *
  * Errors: every call returns a tomo_status.  Nothing aborts or traps; after an error the
  * handle stays valid and tomo_last_error() describes the most recent failure on it.

@@ -250,6 +250,7 @@ tomo_status march(tomo_grid* G, int level, int mode, MarchArgs<T> a, const T* s_
       m.dot_kind = a.dot_kind;
       m.skip = a.skip;
       m.xprev_zero = a.xprev_zero;
+      m.tile_fixed = G->L[level].tile_fixed;
       if (a.gate != nullptr) return fail(G, TOMO_EINVAL, "gated product needs the FP64 path");
       March2Const k{(float)G->kinds.a0, (float)G->kinds.b0, (float)G->kinds.a7,
                     (float)G->kinds.b7, (float)G->kinds.ta, (float)G->kinds.tb,
@@ -319,6 +320,8 @@ Cheb cheb(const tomo_grid* G) {
 int level_degree(const tomo_grid* G, int l) {
   return l == 0 ? G->d.smoother_degree : G->d.coarse_degree;
 }
+
+
 
 template <typename T>
 tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_start, bool dot,
@@ -1094,6 +1097,7 @@ void free_grid(tomo_grid* G) {
     F(Lv.x);
     F(Lv.xp);
     F(Lv.t);
+    F(Lv.tile_fixed);
   }
   F(G->d_taps);
   F(G->d_tapw);
@@ -1218,6 +1222,11 @@ tomo_status create_impl(tomo_grid* G) {
     TRY(dalloc(G, &Lv.x, lnv));
     TRY(dalloc(G, &Lv.xp, lnv));
     TRY(dalloc(G, &Lv.t, lnv));
+    if (sizeof(T) == 4) {
+      const std::vector<uint8_t> fl = march2_tile_flags(Lv.g, Lv.hmask);
+      TRY(dalloc(G, (void**)&Lv.tile_fixed, fl.size()));
+      CK(cudaMemcpy(Lv.tile_fixed, fl.data(), fl.size(), cudaMemcpyHostToDevice));
+    }
   }
   if (G->coarse_n > 0) {
     TRY(dalloc(G, &G->coarseA, sizeof(T) * (size_t)G->coarse_n * G->coarse_n));

@@ -81,7 +81,12 @@ struct March2Args {
   int dot_kind;
   const int* skip;
   int xprev_zero;  // CHEB: the previous iterate is zero (first step after a zero start)
+  // per x-y tile of the launch (32 x 16 node columns with halo): does any node of the
+  // tile's columns have a fixed DOF?  nullptr: every tile reads the mask
+  const uint8_t* tile_fixed;
 };
+// Tile flags for k_march2 on a level (see March2Args::tile_fixed), from the host mask.
+std::vector<uint8_t> march2_tile_flags(const Geom& g, const std::vector<uint8_t>& hmask);
 struct March2Const {
   float a0, b0, a7, b7, ta, tb, ua, ud, k0diag;
 };
@@ -170,6 +175,7 @@ struct tomo_level {
   void* x = nullptr;        // T[3nn] iterate
   void* xp = nullptr;       // T[3nn] previous iterate / ping-pong
   void* t = nullptr;        // T[3nn] residual
+  uint8_t* tile_fixed = nullptr;  // FP32 grids: k_march2 tiles that hold fixed nodes
   std::vector<uint8_t> hmask;
 };
 

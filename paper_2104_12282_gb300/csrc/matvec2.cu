@@ -15,6 +15,9 @@
 //   splits plane k (output) from plane k+1 (carried in registers).
 // CTA = 32 lanes x 8 thread rows = node columns 32 x 16; lanes 0, 31 and node rows 0, 15
 // are halo.  Each z-chunk recomputes one element layer below it.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "host.h"
 
@@ -48,6 +51,7 @@ __device__ __forceinline__ float2 shup2(float2 v) {
 template <int MODE, bool DOT>
 __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
     k_march2(const __grid_constant__ March2Args A, const __grid_constant__ March2Const K) {
+  constexpr bool CHEBY = MODE == M_CHEB;
   PDL_ENTER();
   if (A.skip != nullptr && *A.skip) return;
   const Geom g = A.g;
@@ -55,6 +59,8 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
   const int i = (int)blockIdx.x * 30 - 1 + l;
   const int j0 = (int)blockIdx.y * (2 * TYP - 2) - 1 + 2 * t;
   const int j1 = j0 + 1;
+  const bool tile_fixed =
+      A.tile_fixed == nullptr || A.tile_fixed[blockIdx.x + gridDim.x * blockIdx.y] != 0;
   const int kb = (int)blockIdx.z * A.kz;
   const int ke = min(kb + A.kz, g.nzn);
   const int nn = g.nn, plane = g.nxn * g.nyn, eplane = g.nx * g.ny;
@@ -130,8 +136,10 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
       bv[c] = bc2(0.0f);
       xp[c] = bc2(0.0f);
     }
-    if (w0) m0 = A.mask[n0];
-    if (w1) m1 = A.mask[n1];
+    if (tile_fixed) {  // (CTA-uniform) only tiles that hold fixed nodes read the mask
+      if (w0) m0 = A.mask[n0];
+      if (w1) m1 = A.mask[n1];
+    }
     if (MODE != M_APPLY) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -139,7 +147,7 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
         if (w1) bv[c].y = __ldg(A.b + (size_t)c * nn + n1);
       }
     }
-    if (MODE == M_CHEB && A.c1 != 0.0f && !A.xprev_zero) {
+    if (CHEBY && A.c1 != 0.0f && !A.xprev_zero) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (w0) xp[c].x = A.xprev[(size_t)c * nn + n0];
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
       }
     }
     float2 Sx = bc2(0.0f);
-    if (MODE == M_CHEB) {
+    if (CHEBY) {
       const float2 fromleft = shup2(se);
       Sx = (l > 0) ? add2(se, fromleft) : se;
       sS[t][l] = Sx.y;
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
       }
     }
     float2 Srow = bc2(0.0f);
-    if (MODE == M_CHEB) {
+    if (CHEBY) {
       const float prevS = (t > 0) ? sS[t - 1][l] : 0.0f;
       Srow = add2(make_float2(Sx.x, Sx.x), make_float2(prevS, Sx.y));
     }
@@ -295,7 +303,7 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
     // ---- epilogue ----
     if (w0 || w1) {
       float2 inv = bc2(0.0f);
-      if (MODE == M_CHEB) {
+      if (CHEBY) {
         inv.x = Stot.x > 0.0f ? 1.0f / (K.k0diag * Stot.x) : 0.0f;
         inv.y = Stot.y > 0.0f ? 1.0f / (K.k0diag * Stot.y) : 0.0f;
       }
@@ -315,7 +323,7 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
         const bool f0 = (m0 >> c) & 1u, f1 = (m1 >> c) & 1u;
         if (f0) v.x = 0.0f;
         if (f1) v.y = 0.0f;
-        float* dst = (MODE == M_CHEB) ? A.xprev : A.y;
+        float* dst = CHEBY ? A.xprev : A.y;
         if (w0) dst[(size_t)c * nn + n0] = v.x;
         if (w1) dst[(size_t)c * nn + n1] = v.y;
         if (DOT) {
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
   // The product and the residual run unrolled by two (the plane buffers swap roles without
   // register copies: 8 % on the product at the benchmark size, measured); the Chebyshev
   // step keeps one step per iteration (unrolled it spills).
-  if constexpr (MODE == M_CHEB) {
+  if constexpr (CHEBY) {
     for (int k = kb - 1; k < ke; ++k) step(k);
   } else {
 #pragma unroll 2
@@ -376,6 +384,24 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
 }
 
 }  // namespace
+
+std::vector<uint8_t> march2_tile_flags(const Geom& g, const std::vector<uint8_t>& hmask) {
+  const int gx = (g.nxn + 29) / 30;
+  const int gy = (g.nyn + 2 * TYP - 3) / (2 * TYP - 2);
+  std::vector<uint8_t> f((size_t)gx * gy, 0);
+  for (int k = 0; k < g.nzn; ++k)
+    for (int j = 0; j < g.nyn; ++j)
+      for (int i = 0; i < g.nxn; ++i) {
+        if (!hmask[(size_t)i + (size_t)g.nxn * (j + (size_t)g.nyn * k)]) continue;
+        // every tile whose node columns (halo included) contain (i, j)
+        for (int bx = std::max(0, (i - 30) / 30); bx <= std::min(gx - 1, (i + 1) / 30); ++bx) {
+          if (i < bx * 30 - 1 || i > bx * 30 + 30) continue;
+          for (int by = std::max(0, (j - 14) / 14); by <= std::min(gy - 1, (j + 1) / 14); ++by)
+            if (j >= by * 14 - 1 && j <= by * 14 + 14) f[bx + (size_t)gx * by] = 1;
+        }
+      }
+  return f;
+}
 
 cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const March2Const& c,
                           int num_sms) {
