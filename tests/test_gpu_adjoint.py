@@ -77,3 +77,16 @@ def test_gradient_after_adjoint_uses_the_load_again():
         g.adjoint_gradient(_t(z, torch.float32), _t(l, torch.float32), torch.empty_like(dc))
         c1, _ = g.gradient(_t(z, torch.float32), dc)
     assert c0 == c1
+
+
+def test_zero_adjoint_load_gives_zero_gradient():
+    p = P.cantilever(8, 4, 4)
+    z = P.random_field(p.dims, 6, 0.2, 1.0).astype(np.float32)
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        dj = torch.full((p.n_el,), 7.0, dtype=torch.float32, device=DEV)
+        J, iu, il = g.adjoint_gradient(_t(z, torch.float32),
+                                       torch.zeros(p.dims.n_dof, dtype=torch.float32, device=DEV),
+                                       dj)
+        torch.cuda.synchronize()
+    assert J == 0.0 and il.iters == 0 and iu.status == 0
+    assert torch.count_nonzero(dj).item() == 0

@@ -111,3 +111,28 @@ def test_batch_rejects_fp64_grids():
         z = torch.full((p.n_el,), 0.5, dtype=torch.float64, device=DEV)
         with pytest.raises((tomo.TomoError, TypeError)):
             b.gradient([z], [torch.empty_like(z)])
+
+
+def test_batch_reports_the_failing_grid_and_finishes_the_others():
+    ps = P.uneven_cantilever_batch(9, 4)
+    zs = _fields(ps, 50)
+    grids = [tomo.Grid.from_problem(p, precision=tomo.FP32, maxit=(1 if i == 2 else 2000))
+             for i, p in enumerate(ps)]
+    try:
+        with tomo.Batch(workers=2) as b:
+            for g in grids:
+                b.append(g)
+            dcs = [torch.empty_like(z) for z in zs]
+            with pytest.raises(tomo.TomoError) as ei:
+                b.gradient(zs, dcs)
+            assert "grid 2" in str(ei.value)
+        torch.cuda.synchronize()
+        # the grids that converged hold their results
+        for i in (0, 1, 3):
+            with tomo.Grid.from_problem(ps[i], precision=tomo.FP32) as g:
+                dc = torch.empty_like(zs[i])
+                g.gradient(zs[i], dc)
+            assert torch.equal(dc, dcs[i])
+    finally:
+        for g in grids:
+            g.close()

@@ -73,3 +73,20 @@ def test_estimate_bounds_the_device_memory_of_a_grid():
             g.gradient(z, dc, dv)       # host arrays: staging buffers allocated
             held = g.device_bytes()
         assert held <= est <= 2 * held + (8 << 20), (p.name, held, est)
+
+
+def test_a_failing_request_does_not_disturb_the_others():
+    good = [P.served_request(8, i, (6, 10)) for i in range(4)]
+    bad = P.served_request(8, 9, (6, 10))
+    bad.nu = 0.7          # rejected at grid creation (Poisson ratio out of range)
+    with tomo.Server(workers=2, budget_bytes=1 << 30) as srv:
+        tickets = [srv.submit(p) for p in good[:2]] + [srv.submit(bad)] + \
+                  [srv.submit(p) for p in good[2:]]
+        res = [srv.wait(t) for t in tickets]
+    statuses = [r.status for r, _, _ in res]
+    assert statuses[2] != 0 and len(res[2][0].message) > 0
+    for k, p in zip((0, 1, 3, 4), good):
+        r, dc, _ = res[k]
+        assert r.status == 0
+        c, dc0, _ = _alone(p)
+        assert r.compliance == c and np.array_equal(dc, dc0)
