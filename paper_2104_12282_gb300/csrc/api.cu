@@ -1,6 +1,7 @@
 // C ABI of the tomo library: grid handle, multigrid hierarchy, preconditioned CG driver and
 // the exact-gradient evaluation (Algorithm 1, exact branch; Eq. 4-5, Section III-D).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -1662,8 +1663,18 @@ tomo_status tomo_batch_gradient(tomo_batch* B, const float* const* z, double* co
     }
   const int W = std::min<int>((int)B->streams.size(), std::max(n, 1));
   std::vector<tomo_status> st(n, TOMO_OK);
+  // largest grids first, each taken by the next free worker (longest-processing-time order
+  // balances uneven sizes); a grid's work stays on one stream, so its result does not
+  // depend on which worker ran it
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return B->grids[a]->g.nel > B->grids[b]->g.nel;
+  });
+  std::atomic<int> next{0};
   auto work = [&](int w) {
-    for (int i = w; i < n; i += W) {
+    for (int k = next++; k < n; k = next++) {
+      const int i = order[k];
       tomo_grid* G = B->grids[i];
       cudaStream_t own = G->stream;
       G->stream = B->streams[w];
