@@ -329,6 +329,7 @@ def extras(args, dev, stream):
                 cs, infos = b.gradient(zs, dcs)
             torch.cuda.synchronize()
             batch_s = (time.perf_counter() - t0) / 3
+            mode = "lockstep" if b.lockstep_runs > 0 else "one grid per stream"
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for gg, zz, dd in zip(grids, zs, dcs):
@@ -337,7 +338,7 @@ def extras(args, dev, stream):
         seq_s = time.perf_counter() - t0
         out["batch_64_uneven"] = {
             "grad_evals_per_s": 64 / batch_s, "sequential_grad_evals_per_s": 64 / seq_s,
-            "workers": 16, "elements": sum(q.n_el for q in ps),
+            "workers": 16, "mode": mode, "elements": sum(q.n_el for q in ps),
             "cg_iters_mean": statistics.mean(i.iters for i in infos)}
     finally:
         for gg in grids:

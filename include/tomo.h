@@ -261,19 +261,34 @@ tomo_status tomo_profile_levels(tomo_grid* grid, double* ms, int64_t* launches, 
 tomo_status tomo_profile_read(tomo_grid* grid, int64_t* launches, double* total_ms,
                               double* algorithmic_bytes);
 
-/* Batches of independent grids (uneven sizes allowed), evaluated concurrently.  The paper
+/* Batches of independent grids (uneven sizes allowed), evaluated together.  The paper
  * optimises one design at a time; a batch serves many small problems at once on one GPU.
  * tomo_batch_create: workers = number of concurrent host threads and CUDA streams (<= 0:
  * 8, at most 64).  tomo_batch_append: adds a grid (not owned; it must outlive its use in
  * the batch and must not be used elsewhere while a batch call runs).  tomo_batch_gradient:
  * tomo_gradient on every grid i with z[i], &compliance[i], dcdz[i], dvdz[i] (dvdz or any
- * dvdz[i] may be NULL), info[i] (info may be NULL); FP32 grids only.  Each grid's work runs
- * in order on one of the batch's streams and touches only that grid, so each result is
- * the one the grid gives alone.  Returns when all grids are done; on failure the first
- * failing grid's status, described by tomo_batch_last_error. */
+ * dvdz[i] may be NULL), info[i] (info may be NULL); FP32 grids only.
+ * Lockstep mode (the default): filtering and level setup run per grid on the worker
+ * streams, then one CG loop advances all grids together, every phase of an iteration (the
+ * product, the vector updates, each multigrid level's smoothing, transfers and coarsest
+ * solve) one launch for all grids, captured once as a device-side graph loop and reused
+ * until the next tomo_batch_append; then the sensitivities run per grid.  It needs grids
+ * with the multigrid preconditioner, the same smoother degrees, residual-replacement
+ * interval and Poisson ratio, and profiling off; other batches, and batches with lockstep
+ * off (tomo_batch_set_lockstep(batch, 0)), run each grid in order on one worker stream.
+ * One grid per stream, each grid runs exactly the launches of its own tomo_gradient and
+ * its result is bitwise the one it gives alone.  In lockstep the products' z-chunks are
+ * chosen for the batch as a whole (one wave of CTAs for all grids), which changes only the
+ * order in which the fused CG dots add their block partials: results agree with the grid
+ * alone to rounding (same tolerance as any two runs to rtol) and are reproducible for the
+ * same batch.  Returns when all grids are done; on failure the first failing grid's status, described by
+ * tomo_batch_last_error.  tomo_batch_lockstep_runs: the number of tomo_batch_gradient calls
+ * that ran in lockstep. */
 tomo_status tomo_batch_create(int32_t workers, tomo_batch** out);
 tomo_status tomo_batch_append(tomo_batch* batch, tomo_grid* grid);
 tomo_status tomo_batch_size(const tomo_batch* batch, int32_t* count);
+tomo_status tomo_batch_set_lockstep(tomo_batch* batch, int32_t on);
+tomo_status tomo_batch_lockstep_runs(const tomo_batch* batch, int64_t* runs);
 tomo_status tomo_batch_gradient(tomo_batch* batch, const float* const* z, double* compliance,
                                 float* const* dcdz, float* const* dvdz, tomo_solve_info* info);
 tomo_status tomo_batch_destroy(tomo_batch* batch);

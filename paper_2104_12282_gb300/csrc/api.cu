@@ -545,8 +545,11 @@ tomo_status build_loop_graph(tomo_grid* G, cudaGraphExec_t* out) {
 // zeroed (cold).  The iteration loop runs on the device (conditional-while graph); with
 // profiling enabled it is issued from the host in batches instead, so that every launch
 // can be bracketed by events.
+// pcg up to the loop: scalars, start iterate, r = f - K x (or f), p = 0.  *trivial: the
+// load is zero, the solution (0) and info are already final.
 template <typename T>
-tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
+tomo_status pcg_start(tomo_grid* G, bool warm, tomo_solve_info* info, bool* trivial) {
+  *trivial = false;
   const Geom g = G->g;
   const int n = 3 * g.nn;
   T* r = (T*)G->r;
@@ -573,6 +576,7 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
       info->mg_levels = (int)G->L.size();
     }
     G->have_solution = true;
+    *trivial = true;
     return TOMO_OK;
   }
   if (warm) {
@@ -603,6 +607,40 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
     G->launches += 1;
   }
   CK(cudaMemsetAsync(p, 0, sizeof(T) * n, G->stream));
+  return TOMO_OK;
+}
+
+// Status and info of a finished loop from the host copy of the scalars (G->h_sc).
+tomo_status pcg_result(tomo_grid* G, tomo_solve_info* info) {
+  const double ff = G->rhs_ff;
+  const CgScalars& hs = *G->h_sc;
+  tomo_status st = TOMO_OK;
+  if (hs.status & DEV_NAN) st = TOMO_ENAN;
+  else if (hs.status & DEV_BREAKDOWN) st = TOMO_ENOCONV;
+  else if (hs.rr > hs.tol2) st = TOMO_ENOCONV;
+  if (info) {
+    info->iters = hs.it;
+    info->rel_res = std::sqrt(std::max(hs.rr, 0.0) / ff);
+    info->status = st;
+    info->mg_levels = (int)G->L.size();
+  }
+  G->have_solution = true;
+  if (st == TOMO_ENAN) return fail(G, st, "NaN/Inf in the CG iteration at iteration %d", hs.it);
+  if (st == TOMO_ENOCONV)
+    return fail(G, st, "CG stopped after %d iterations at relative residual %.3e%s", hs.it,
+                std::sqrt(std::max(hs.rr, 0.0) / ff),
+                (hs.status & DEV_BREAKDOWN) ? " (breakdown)" : "");
+  return TOMO_OK;
+}
+
+template <typename T>
+tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
+  bool trivial = false;
+  TRY(pcg_start<T>(G, warm, info, &trivial));
+  if (trivial) return TOMO_OK;
+  const int n = 3 * G->g.nn;
+  T* r = (T*)G->r;
+  T* p = (T*)G->p;
   T* z = nullptr;
   TRY(precond<T>(G, r, &z));
   CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
@@ -633,24 +671,7 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
       if (it > G->d.maxit + batch) done = true;
     }
   }
-  const CgScalars& hs = *G->h_sc;
-  tomo_status st = TOMO_OK;
-  if (hs.status & DEV_NAN) st = TOMO_ENAN;
-  else if (hs.status & DEV_BREAKDOWN) st = TOMO_ENOCONV;
-  else if (hs.rr > hs.tol2) st = TOMO_ENOCONV;
-  if (info) {
-    info->iters = hs.it;
-    info->rel_res = std::sqrt(std::max(hs.rr, 0.0) / ff);
-    info->status = st;
-    info->mg_levels = (int)G->L.size();
-  }
-  G->have_solution = true;
-  if (st == TOMO_ENAN) return fail(G, st, "NaN/Inf in the CG iteration at iteration %d", hs.it);
-  if (st == TOMO_ENOCONV)
-    return fail(G, st, "CG stopped after %d iterations at relative residual %.3e%s", hs.it,
-                std::sqrt(std::max(hs.rr, 0.0) / ff),
-                (hs.status & DEV_BREAKDOWN) ? " (breakdown)" : "");
-  return TOMO_OK;
+  return pcg_result(G, info);
 }
 
 // dV/dz = P^T v with v_e = h^3 (Section III-D), written to out.
@@ -903,18 +924,25 @@ tomo_status do_oc(tomo_grid* G, const T* z, const T* dcdz, const T* dvdz, double
   return TOMO_OK;
 }
 
+// Arrays of one gradient evaluation (device pointers of staged host arrays).
+struct GradIO {
+  const void* dz = nullptr;
+  void* ddc = nullptr;
+  void* ddv = nullptr;
+  bool h1 = false, h2 = false, h3 = false;
+};
+
+// S1-S2 of a gradient: stage the arrays, rho = P z, s = h E(rho), coarse moduli and the
+// coarsest factorisation.
 template <typename T>
-tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T* dvdz,
-                        tomo_solve_info* info) {
+tomo_status gradient_begin(tomo_grid* G, const T* z, T* dcdz, T* dvdz, GradIO* io) {
   if (!z || !dcdz) return fail(G, TOMO_EINVAL, "null array");
   const size_t be = sizeof(T) * (size_t)G->g.nel;
   const tomo_grid_desc& d = G->d;
-  const void* dz;
-  void *ddc, *ddv = nullptr;
-  bool h1, h2, h3 = false;
-  TRY(stage_in(G, z, be, 0, &dz, &h1));
-  TRY(stage_out(G, dcdz, be, 1, &ddc, &h2));
-  if (dvdz) TRY(stage_out(G, dvdz, be, 4, &ddv, &h3));
+  TRY(stage_in(G, z, be, 0, &io->dz, &io->h1));
+  TRY(stage_out(G, dcdz, be, 1, &io->ddc, &io->h2));
+  if (dvdz) TRY(stage_out(G, dvdz, be, 4, &io->ddv, &io->h3));
+  const void* dz = io->dz;
   T* rho = (T*)G->rho;
   TRY(pmark(G, 0));
   // S1: rho = P z, s = h (Emin + rho^p (E0 - Emin))
@@ -927,10 +955,16 @@ tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T
   // S2: coarse moduli, coarsest factorisation
   TRY(setup_levels<T>(G));
   TRY(pmark(G, 2));
-  // S3-S5: PCG from a zero start (or from the previous solution, see tomo_set_warm_start)
-  tomo_status st = pcg<T>(G, G->warm_gradient && G->have_solution, info);
-  if (st != TOMO_OK) return st;
-  TRY(pmark(G, 3));
+  return TOMO_OK;
+}
+
+// S6-S7 of a gradient after the solve: compliance, dc/drho, dc/dz = P^T dc/drho, dV/dz.
+template <typename T>
+tomo_status gradient_end(tomo_grid* G, const GradIO& io, double* compliance, T* dcdz, T* dvdz) {
+  const size_t be = sizeof(T) * (size_t)G->g.nel;
+  T* rho = (T*)G->rho;
+  void* ddc = io.ddc;
+  void* ddv = io.ddv;
   // S6: compliance and dc/drho
   TRY(compliance_and_sens<T>(G, rho, (const T*)G->xhi, (const T*)x_lo<T>(G), compliance,
                              (T*)G->dcp));
@@ -944,11 +978,23 @@ tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T
   if (ddv) TRY(volume_gradient<T>(G, (T*)ddv));
   TRY(pmark(G, 5));
   TRY(pcollect(G, 0, 5));
-  TRY(copy_back(G, dcdz, ddc, be, h2));
-  if (dvdz) TRY(copy_back(G, dvdz, ddv, be, h3));
+  TRY(copy_back(G, dcdz, ddc, be, io.h2));
+  if (dvdz) TRY(copy_back(G, dvdz, ddv, be, io.h3));
   TRY(write_scalar(G, compliance, G->dscal));
-  if (h1 || h2 || h3) TRY(sync(G));
+  if (io.h1 || io.h2 || io.h3) TRY(sync(G));
   return TOMO_OK;
+}
+
+template <typename T>
+tomo_status do_gradient(tomo_grid* G, const T* z, double* compliance, T* dcdz, T* dvdz,
+                        tomo_solve_info* info) {
+  GradIO io;
+  TRY(gradient_begin<T>(G, z, dcdz, dvdz, &io));
+  // S3-S5: PCG from a zero start (or from the previous solution, see tomo_set_warm_start)
+  tomo_status st = pcg<T>(G, G->warm_gradient && G->have_solution, info);
+  if (st != TOMO_OK) return st;
+  TRY(pmark(G, 3));
+  return gradient_end<T>(G, io, compliance, dcdz, dvdz);
 }
 
 // Eq. 3 for the objective J = l^T u: K lambda = l (K symmetric), then
@@ -1605,18 +1651,529 @@ tomo_status tomo_profile_read(tomo_grid* G, int64_t* launches, double* total_ms,
   return TOMO_OK;
 }
 
+}  // extern "C"
+
 // ---------------------------------------------------------------------------------------
-// Batches: many independent grids evaluated concurrently.  A small grid leaves most of the
-// GPU idle between its short launches, so the batch runs `workers` host threads, each with
-// its own stream, over the grids (round robin); each grid's work stays in order on one
-// stream and touches only that grid's buffers, so every result equals the grid's result
-// alone.
+// Batches: many independent grids evaluated together.  Small grids leave most of the GPU
+// idle, and their CG loops are bound by the launch rate (a V-cycle is ~6 short launches per
+// level), so a batch runs in lockstep: per-grid setup on `workers` host threads with a
+// stream each (largest grids first), then ONE CG loop for all grids in which every phase of
+// an iteration (the product, the vector updates, each level's smoothing, transfer and
+// coarse solve) is one launch covering every grid, captured once as a conditional-while
+// graph; then per-grid sensitivities on the worker streams.  Each grid gets the tiles and
+// blocks of its own single-grid launches; only the z-chunks of the products are chosen for
+// the batch (one wave for all grids together), which changes the order in which the fused
+// dots (p.q, r.z) add their block partials, so a grid's result agrees with its result alone
+// to rounding (and is reproducible for the same batch).  Grids that cannot share a loop (FP64, Jacobi preconditioner, profiling,
+// different smoother settings or Poisson ratios) run one per worker stream instead.
 // ---------------------------------------------------------------------------------------
 struct tomo_batch {
   std::vector<tomo_grid*> grids;
   std::vector<cudaStream_t> streams;
   std::string err;
+  bool lockstep = true;
+  int64_t lockstep_runs = 0;
+  // captured lockstep loop of the active grid set `plan`
+  std::vector<tomo_grid*> plan;
+  cudaStream_t bst = nullptr;  // stream of the batched launches
+  cudaStream_t cap = nullptr;  // capture stream
+  cudaGraphExec_t loop = nullptr;
+  CgScalars** d_scs = nullptr;
+  int d_scs_n = 0;
+  int64_t iter_launches = 0;  // batched launches per loop iteration
+  std::vector<cudaEvent_t> wev;
+  cudaEvent_t bev = nullptr;
 };
+
+namespace {
+
+#define BK(...)                                                                      \
+  do {                                                                               \
+    cudaError_t _e = (__VA_ARGS__);                                                  \
+    if (_e != cudaSuccess) {                                                         \
+      char _b[256];                                                                  \
+      std::snprintf(_b, sizeof _b, "CUDA error %d (%s) in %s", (int)_e,              \
+                    cudaGetErrorString(_e), #__VA_ARGS__);                           \
+      B->err = _b;                                                                   \
+      return TOMO_ECUDA;                                                             \
+    }                                                                                \
+  } while (0)
+
+March2Const march2_const(const tomo_grid* G) {
+  return March2Const{(float)G->kinds.a0, (float)G->kinds.b0, (float)G->kinds.a7,
+                     (float)G->kinds.b7, (float)G->kinds.ta, (float)G->kinds.tb,
+                     (float)G->kinds.ua, (float)G->kinds.ud, (float)G->k0diag};
+}
+
+// the k_march2 arguments march() would build for this grid and level
+March2Args march2_args(const tomo_grid* G, int level, const float* x, const float* b,
+                       float* xprev, float* y, float c1, float c2, int dot_kind,
+                       int xprev_zero) {
+  const tomo_level& Lv = G->L[level];
+  March2Args m{};
+  m.g = Lv.g;
+  m.s = (const float*)Lv.s;
+  m.mask = Lv.mask;
+  m.x = x;
+  m.b = b;
+  m.xprev = xprev;
+  m.y = y;
+  m.c1 = c1;
+  m.c2 = c2;
+  m.partials = G->partials;
+  m.counter = G->counter;
+  m.sc = G->sc;
+  m.dot_kind = dot_kind;
+  m.skip = &G->sc->done;
+  m.xprev_zero = xprev_zero;
+  m.tile_fixed = Lv.tile_fixed;
+  return m;
+}
+
+// Can these grids share one lockstep loop?  (Same launch sequence and shared constants.)
+bool lockstep_compatible(const std::vector<tomo_grid*>& Gs) {
+  if (Gs.empty()) return false;
+  const tomo_grid* A = Gs[0];
+  for (const tomo_grid* G : Gs) {
+    if (G->prec != TOMO_FP32 || G->d.precond != TOMO_PRECOND_MG || !G->use_graph || G->prof ||
+        G->phase_prof || G->rhs_id != 0 || G->L.size() < 2)
+      return false;
+    if (G->d.smoother_degree != A->d.smoother_degree ||
+        G->d.coarse_degree != A->d.coarse_degree || G->d.rr_every != A->d.rr_every ||
+        G->k0diag != A->k0diag || std::memcmp(G->blk, A->blk, sizeof G->blk) != 0 ||
+        std::memcmp(&G->kinds, &A->kinds, sizeof G->kinds) != 0)
+      return false;
+    if (G->d.rr_every > 0 && !G->s64) return false;
+  }
+  return true;
+}
+
+// z-chunk length (node planes per CTA) for the grids P of a batched product on `level`:
+// the shortest chunks whose CTAs across the batch still fit in one wave of resident CTAs
+// (2 per SM).  A grid alone chunks for the GPU it fills by itself; in a batch the grids
+// together fill it, and short chunks would only add halo layers and waves.
+int lockstep_kz(const std::vector<tomo_grid*>& Gs, const std::vector<int>& P, int level) {
+  const int target = 2 * (Gs[0]->num_sms > 0 ? Gs[0]->num_sms : 152);
+  int kmax = 1;
+  for (int q : P) kmax = std::max(kmax, Gs[q]->L[level].g.nzn);
+  for (int kz = 1; kz < kmax; ++kz) {
+    long long ctas = 0;
+    for (int q : P) {
+      const Geom& g = Gs[q]->L[level].g;
+      const long long tiles = (long long)((g.nxn + 29) / 30) * ((g.nyn + 13) / 14);
+      ctas += tiles * ((g.nzn + kz - 1) / kz);
+    }
+    if (ctas <= target) return kz;
+  }
+  return kmax;
+}
+
+struct ChebCoef {
+  float c1, c2;
+};
+
+// Chebyshev coefficients of steps 0..K-1 of one grid (as smooth() computes them)
+std::vector<ChebCoef> cheb_steps(const tomo_grid* G, int K) {
+  const Cheb cb = cheb(G);
+  std::vector<ChebCoef> v(K);
+  double rho_prev = 1.0 / cb.sigma;
+  for (int s = 0; s < K; ++s) {
+    double c1, c2;
+    if (s == 0) {
+      c1 = 0.0;
+      c2 = 1.0 / cb.theta;
+    } else {
+      const double rho = 1.0 / (2.0 * cb.sigma - rho_prev);
+      c1 = rho * rho_prev;
+      c2 = 2.0 * rho / cb.delta;
+      rho_prev = rho;
+    }
+    v[s] = ChebCoef{(float)c1, (float)c2};
+  }
+  return v;
+}
+
+// z = V-cycle(r) for every grid of Gs, the same sequence vcycle() issues per grid, with each
+// operation issued once for all grids that have it (a grid's coarsest solve after the
+// batch's down-sweep: nothing of that grid runs in between).  dot: the last smoothing step
+// on level 0 computes r.z (beta).  *launches counts the batched launches issued.
+tomo_status batch_vcycle(tomo_batch* B, cudaStream_t st, const std::vector<tomo_grid*>& Gs,
+                         const std::vector<const float*>& rin, bool dot,
+                         std::vector<float*>* zout, int64_t* launches) {
+  const int n = (int)Gs.size();
+  const tomo_grid* G0 = Gs[0];
+  const March2Const kc = march2_const(G0);
+  const int num_sms = G0->num_sms;
+  int Lmax = 0;
+  for (auto* G : Gs) Lmax = std::max(Lmax, (int)G->L.size());
+  std::vector<std::vector<float*>> X(n), Y(n);
+  for (int q = 0; q < n; ++q) {
+    const int nl = (int)Gs[q]->L.size();
+    X[q].resize(nl);
+    Y[q].resize(nl);
+    for (int l = 0; l < nl; ++l) {
+      X[q][l] = (float*)Gs[q]->L[l].x;
+      Y[q][l] = (float*)Gs[q]->L[l].xp;
+    }
+  }
+  auto rhs = [&](int q, int l) -> const float* {
+    return l == 0 ? rin[q] : (const float*)Gs[q]->L[l].b;
+  };
+  std::vector<int> P;
+  std::vector<March2Args> ma;
+  auto part = [&](int l) {  // grids for which level l is not the coarsest
+    P.clear();
+    for (int q = 0; q < n; ++q)
+      if (l < (int)Gs[q]->L.size() - 1) P.push_back(q);
+  };
+  auto cheb_step = [&](int l, int s, const std::vector<std::vector<ChebCoef>>& cf,
+                       bool zero_start, int dk) -> tomo_status {
+    ma.clear();
+    const int kz = lockstep_kz(Gs, P, l);
+    for (int q : P) {
+      ma.push_back(march2_args(Gs[q], l, X[q][l], rhs(q, l), Y[q][l], nullptr, cf[q][s].c1,
+                               cf[q][s].c2, dk, (s == 1 && zero_start) ? 1 : 0));
+      ma.back().kz = kz;
+    }
+    BK(launch_march2_batch(st, M_CHEB, ma.data(), (int)ma.size(), kc, num_sms));
+    *launches += 1;
+    for (int q : P) std::swap(X[q][l], Y[q][l]);
+    return TOMO_OK;
+  };
+  // down-sweep
+  for (int l = 0; l + 1 < Lmax; ++l) {
+    part(l);
+    if (P.empty()) continue;
+    const int K = level_degree(G0, l);
+    std::vector<std::vector<ChebCoef>> cf(n);
+    for (int q : P) cf[q] = cheb_steps(Gs[q], K);
+    for (int s = 0; s < K; ++s) {
+      if (s == 0) {
+        if (l == 0) {  // (levels >= 1: the restriction that produced b wrote x1)
+          std::vector<JacobiItem> ja;
+          for (int q : P) {
+            const tomo_level& Lv = Gs[q]->L[0];
+            ja.push_back(JacobiItem{Lv.g, (const float*)Lv.s, Lv.mask, rhs(q, 0), cf[q][0].c2,
+                                    (float)Gs[q]->k0diag, X[q][0], &Gs[q]->sc->done});
+          }
+          BK(launch_jacobi_batch(st, ja.data(), (int)ja.size()));
+          *launches += 1;
+        }
+        continue;
+      }
+      TRY(cheb_step(l, s, cf, true, 0));
+    }
+    ma.clear();
+    const int kz = lockstep_kz(Gs, P, l);
+    for (int q : P) {
+      ma.push_back(march2_args(Gs[q], l, X[q][l], rhs(q, l), nullptr,
+                               (float*)Gs[q]->L[l].t, 0.0f, 0.0f, 0, 0));
+      ma.back().kz = kz;
+    }
+    BK(launch_march2_batch(st, M_RESID, ma.data(), (int)ma.size(), kc, num_sms));
+    *launches += 1;
+    std::vector<RestrictItem> ra;
+    for (int q : P) {
+      const tomo_grid* G = Gs[q];
+      const tomo_level& Lv = G->L[l];
+      const tomo_level& Lc = G->L[l + 1];
+      const bool fuse = l + 1 < (int)G->L.size() - 1;
+      ra.push_back(RestrictItem{Lv.g, Lc.g, (const float*)Lv.t, (float*)Lc.b, Lc.mask,
+                                &G->sc->done, fuse ? (float*)Lc.x : nullptr,
+                                (const float*)Lc.s, (float)(1.0 / cheb(G).theta),
+                                (float)G->k0diag});
+    }
+    BK(launch_restrict_batch(st, ra.data(), (int)ra.size()));
+    *launches += 1;
+  }
+  // coarsest levels
+  std::vector<float*> zc(n);
+  {
+    std::vector<CoarseItem> ca;
+    for (int q = 0; q < n; ++q) {
+      const tomo_grid* G = Gs[q];
+      const int lc = (int)G->L.size() - 1;
+      zc[q] = (float*)G->L[lc].x;
+      ca.push_back(CoarseItem{G->coarse_n, (const float*)G->coarseA, (const float*)G->coarseD,
+                              rhs(q, lc), zc[q], &G->sc->done});
+    }
+    BK(launch_coarse_apply_batch(st, ca.data(), n));
+    *launches += 1;
+  }
+  // up-sweep
+  for (int l = Lmax - 2; l >= 0; --l) {
+    part(l);
+    if (P.empty()) continue;
+    std::vector<ProlongItem> pa;
+    for (int q : P) {
+      const tomo_level& Lv = Gs[q]->L[l];
+      pa.push_back(ProlongItem{Lv.g, Gs[q]->L[l + 1].g, zc[q], X[q][l], Lv.mask,
+                               &Gs[q]->sc->done});
+    }
+    BK(launch_prolong_batch(st, pa.data(), (int)pa.size()));
+    *launches += 1;
+    const int K = level_degree(G0, l);
+    std::vector<std::vector<ChebCoef>> cf(n);
+    for (int q : P) cf[q] = cheb_steps(Gs[q], K);
+    for (int s = 0; s < K; ++s)
+      TRY(cheb_step(l, s, cf, false, (dot && l == 0 && s == K - 1) ? 2 : 0));
+    for (int q : P) zc[q] = X[q][l];
+  }
+  *zout = zc;
+  return TOMO_OK;
+}
+
+tomo_status batch_cg_p(tomo_batch* B, cudaStream_t st, const std::vector<tomo_grid*>& Gs,
+                       const std::vector<float*>& z, int64_t* launches) {
+  std::vector<CgPItem> pa;
+  for (size_t q = 0; q < Gs.size(); ++q)
+    pa.push_back(CgPItem{3 * Gs[q]->g.nn, (float*)Gs[q]->p, z[q], Gs[q]->sc});
+  BK(launch_cg_p_batch(st, pa.data(), (int)pa.size()));
+  *launches += 1;
+  return TOMO_OK;
+}
+
+// One CG iteration for every grid (enqueue_iteration's sequence, batched).
+tomo_status batch_iteration(tomo_batch* B, cudaStream_t st, const std::vector<tomo_grid*>& Gs,
+                            int64_t* launches) {
+  const int n = (int)Gs.size();
+  const tomo_grid* G0 = Gs[0];
+  std::vector<March2Args> ma;
+  std::vector<int> all(n);
+  for (int q = 0; q < n; ++q) all[q] = q;
+  const int kz = lockstep_kz(Gs, all, 0);
+  for (auto* G : Gs) {
+    ma.push_back(march2_args(G, 0, (const float*)G->p, nullptr, nullptr, (float*)G->q, 0.0f,
+                             0.0f, 1, 0));
+    ma.back().kz = kz;
+  }
+  BK(launch_march2_batch(st, M_APPLY, ma.data(), n, march2_const(G0), G0->num_sms));
+  *launches += 1;
+  std::vector<CgXrItem> xa;
+  for (auto* G : Gs)
+    xa.push_back(CgXrItem{3 * G->g.nn, (float*)G->xhi, (float*)G->xlo, (float*)G->r,
+                          (const float*)G->p, (const float*)G->q, G->partials, G->counter,
+                          G->sc});
+  BK(launch_cg_xr_batch(st, xa.data(), n));
+  *launches += 1;
+  if (G0->d.rr_every > 0) {
+    std::vector<MarchArgs<double>> ra;
+    for (auto* G : Gs) {
+      MarchArgs<double> rr{};
+      rr.g = G->L[0].g;
+      rr.s = G->s64;
+      rr.mask = G->L[0].mask;
+      rr.partials = G->partials;
+      rr.counter = G->counter;
+      rr.xf_hi = (const float*)G->xhi;
+      rr.xf_lo = (const float*)G->xlo;
+      rr.b = G->rhs64;
+      rr.yf = (float*)G->r;
+      rr.skip = &G->sc->done;
+      rr.gate = G->sc;
+      ra.push_back(rr);
+    }
+    BK(launch_march_rr_batch(st, ra.data(), n, elem_const<double>(G0), G0->num_sms));
+    *launches += 1;
+  }
+  std::vector<const float*> r(n);
+  for (int q = 0; q < n; ++q) r[q] = (const float*)Gs[q]->r;
+  std::vector<float*> z;
+  TRY(batch_vcycle(B, st, Gs, r, true, &z, launches));
+  return batch_cg_p(B, st, Gs, z, launches);
+}
+
+tomo_status batch_build_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs) {
+  if (B->loop) {
+    cudaGraphExecDestroy(B->loop);
+    B->loop = nullptr;
+  }
+  const int n = (int)Gs.size();
+  if (B->d_scs_n < n) {
+    if (B->d_scs) cudaFree(B->d_scs);
+    B->d_scs = nullptr;
+    B->d_scs_n = 0;
+    BK(cudaMalloc(&B->d_scs, sizeof(CgScalars*) * (size_t)n));
+    B->d_scs_n = n;
+  }
+  std::vector<CgScalars*> h(n);
+  for (int q = 0; q < n; ++q) h[q] = Gs[q]->sc;
+  BK(cudaMemcpy(B->d_scs, h.data(), sizeof(CgScalars*) * (size_t)n, cudaMemcpyHostToDevice));
+  if (!B->cap) BK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  BK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle hc;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    BK(e);
+  }
+  e = cudaStreamBeginCaptureToGraph(B->cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  tomo_status st = TOMO_OK;
+  int64_t launches = 0;
+  if (e == cudaSuccess) {
+    st = batch_iteration(B, B->cap, Gs, &launches);
+    if (st == TOMO_OK) {
+      cudaError_t e2 = launch_loop_cond_batch(B->cap, hc, B->d_scs, n);
+      launches += 1;
+      if (e2 != cudaSuccess) {
+        B->err = std::string("loop control launch failed: ") + cudaGetErrorString(e2);
+        st = TOMO_ECUDA;
+      }
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(B->cap, &captured);
+    if (st == TOMO_OK && e3 != cudaSuccess) e = e3;
+  }
+  if (e != cudaSuccess || st != TOMO_OK) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != TOMO_OK) return st;
+    BK(e);
+  }
+  e = cudaGraphInstantiate(&B->loop, graph, 0);
+  cudaGraphDestroy(graph);
+  BK(e);
+  B->plan = Gs;
+  B->iter_launches = launches;
+  return TOMO_OK;
+}
+
+// Run fn(w, i) for every grid index i on W worker threads, largest grids first, each grid
+// taken by the next free worker.
+template <class Fn>
+void for_grids_lpt(tomo_batch* B, int W, Fn fn) {
+  const int n = (int)B->grids.size();
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return B->grids[a]->g.nel > B->grids[b]->g.nel;
+  });
+  std::atomic<int> next{0};
+  auto work = [&](int w) {
+    for (int k = next++; k < n; k = next++) fn(w, order[k]);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < W; ++w) pool.emplace_back(work, w);
+  work(0);
+  for (auto& t : pool) t.join();
+}
+
+tomo_status batch_first_error(tomo_batch* B, const std::vector<tomo_status>& st) {
+  for (size_t i = 0; i < st.size(); ++i)
+    if (st[i] != TOMO_OK) {
+      char buf[64];
+      std::snprintf(buf, sizeof buf, "grid %d of the batch: ", (int)i);
+      B->err = std::string(buf) + B->grids[i]->err;
+      return st[i];
+    }
+  return TOMO_OK;
+}
+
+tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* compliance,
+                           float* const* dcdz, float* const* dvdz, tomo_solve_info* info) {
+  const int n = (int)B->grids.size();
+  const int W = std::min<int>((int)B->streams.size(), std::max(n, 1));
+  if (!B->bst) BK(cudaStreamCreateWithFlags(&B->bst, cudaStreamNonBlocking));
+  while ((int)B->wev.size() < W) {
+    cudaEvent_t e;
+    BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    B->wev.push_back(e);
+  }
+  if (!B->bev) BK(cudaEventCreateWithFlags(&B->bev, cudaEventDisableTiming));
+  std::vector<tomo_status> st(n, TOMO_OK);
+  std::vector<GradIO> io(n);
+  std::vector<char> trivial(n, 0);
+  std::vector<cudaStream_t> own(n);
+  for (int i = 0; i < n; ++i) own[i] = B->grids[i]->stream;
+  // phase A: S1-S2 and the CG start of every grid, on the worker streams
+  for_grids_lpt(B, W, [&](int w, int i) {
+    tomo_grid* G = B->grids[i];
+    G->stream = B->streams[w];
+    g_cur_err = &G->err;
+    G->err.clear();
+    st[i] = gradient_begin<float>(G, z[i], dcdz[i], dvdz ? dvdz[i] : nullptr, &io[i]);
+    bool tv = false;
+    if (st[i] == TOMO_OK)
+      st[i] = pcg_start<float>(G, G->warm_gradient && G->have_solution,
+                               info ? info + i : nullptr, &tv);
+    trivial[i] = tv ? 1 : 0;
+  });
+  for (int w = 0; w < W; ++w) {
+    BK(cudaEventRecord(B->wev[w], B->streams[w]));
+    BK(cudaStreamWaitEvent(B->bst, B->wev[w], 0));
+  }
+  // phase B: one CG loop for the grids that have a system to solve
+  std::vector<tomo_grid*> act;
+  for (int i = 0; i < n; ++i)
+    if (st[i] == TOMO_OK && !trivial[i]) act.push_back(B->grids[i]);
+  tomo_status bs = TOMO_OK;
+  if (!act.empty()) {
+    int64_t launches = 0;
+    std::vector<const float*> r(act.size());
+    for (size_t q = 0; q < act.size(); ++q) r[q] = (const float*)act[q]->r;
+    std::vector<float*> zz;
+    bs = batch_vcycle(B, B->bst, act, r, true, &zz, &launches);
+    if (bs == TOMO_OK) bs = batch_cg_p(B, B->bst, act, zz, &launches);
+    if (bs == TOMO_OK && (!B->loop || B->plan != act)) bs = batch_build_loop(B, act);
+    if (bs == TOMO_OK) {
+      cudaError_t e = cudaGraphLaunch(B->loop, B->bst);
+      for (size_t q = 0; q < act.size() && e == cudaSuccess; ++q)
+        e = cudaMemcpyAsync(act[q]->h_sc, act[q]->sc, sizeof(CgScalars),
+                            cudaMemcpyDeviceToHost, B->bst);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(B->bst);
+      if (e != cudaSuccess) {
+        B->err = std::string("lockstep CG loop: ") + cudaGetErrorString(e);
+        bs = TOMO_ECUDA;
+      }
+    }
+    if (bs == TOMO_OK)
+      for (auto* G : act) G->launches += launches + (int64_t)G->h_sc->loops * B->iter_launches;
+  }
+  if (bs == TOMO_OK) {
+    BK(cudaEventRecord(B->bev, B->bst));
+    // phase C: results, S6-S7 on the worker streams
+    for_grids_lpt(B, W, [&](int w, int i) {
+      if (st[i] != TOMO_OK) return;
+      tomo_grid* G = B->grids[i];
+      G->stream = B->streams[w];
+      g_cur_err = &G->err;
+      // after every grid's phase A (the batch stream waited for all of it) and the loop
+      if (cudaStreamWaitEvent(G->stream, B->bev, 0) != cudaSuccess) {
+        cudaGetLastError();
+        st[i] = fail(G, TOMO_ECUDA, "stream wait failed");
+        return;
+      }
+      if (!trivial[i]) st[i] = pcg_result(G, info ? info + i : nullptr);
+      if (st[i] == TOMO_OK)
+        st[i] = gradient_end<float>(G, io[i], compliance + i, dcdz[i], dvdz ? dvdz[i] : nullptr);
+      if (st[i] == TOMO_OK && cudaStreamSynchronize(G->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st[i] = TOMO_ECUDA;
+      }
+    });
+  }
+  // the worker streams must not run ahead of anything still queued on the batch stream
+  cudaStreamSynchronize(B->bst);
+  for (int i = 0; i < n; ++i) B->grids[i]->stream = own[i];
+  if (bs != TOMO_OK) return bs;
+  B->lockstep_runs += 1;
+  return batch_first_error(B, st);
+}
+
+}  // namespace
+
+extern "C" {
 
 tomo_status tomo_batch_create(int32_t workers, tomo_batch** out) {
   if (!out) return TOMO_EINVAL;
@@ -1648,6 +2205,19 @@ tomo_status tomo_batch_append(tomo_batch* B, tomo_grid* G) {
       return TOMO_EINVAL;
     }
   B->grids.push_back(G);
+  B->plan.clear();  // the captured lockstep loop no longer covers the batch
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_set_lockstep(tomo_batch* B, int32_t on) {
+  if (!B) return TOMO_EINVAL;
+  B->lockstep = on != 0;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_lockstep_runs(const tomo_batch* B, int64_t* runs) {
+  if (!B || !runs) return TOMO_EINVAL;
+  *runs = B->lockstep_runs;
   return TOMO_OK;
 }
 
@@ -1661,20 +2231,15 @@ tomo_status tomo_batch_gradient(tomo_batch* B, const float* const* z, double* co
       B->err = "batch gradients take FP32 grids";
       return TOMO_EINVAL;
     }
+  if (B->lockstep && lockstep_compatible(B->grids))
+    return batch_lockstep(B, z, compliance, dcdz, dvdz, info);
   const int W = std::min<int>((int)B->streams.size(), std::max(n, 1));
   std::vector<tomo_status> st(n, TOMO_OK);
-  // largest grids first, each taken by the next free worker (longest-processing-time order
-  // balances uneven sizes); a grid's work stays on one stream, so its result does not
-  // depend on which worker ran it
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return B->grids[a]->g.nel > B->grids[b]->g.nel;
-  });
-  std::atomic<int> next{0};
-  auto work = [&](int w) {
-    for (int k = next++; k < n; k = next++) {
-      const int i = order[k];
+  // one grid per worker stream at a time, largest grids first, each taken by the next free
+  // worker (longest-processing-time order balances uneven sizes); a grid's work stays on
+  // one stream, so its result does not depend on which worker ran it
+  for_grids_lpt(B, W, [&](int w, int i) {
+    {
       tomo_grid* G = B->grids[i];
       cudaStream_t own = G->stream;
       G->stream = B->streams[w];
@@ -1688,19 +2253,8 @@ tomo_status tomo_batch_gradient(tomo_batch* B, const float* const* z, double* co
       }
       G->stream = own;
     }
-  };
-  std::vector<std::thread> pool;
-  for (int w = 1; w < W; ++w) pool.emplace_back(work, w);
-  work(0);
-  for (auto& t : pool) t.join();
-  for (int i = 0; i < n; ++i)
-    if (st[i] != TOMO_OK) {
-      char buf[64];
-      std::snprintf(buf, sizeof buf, "grid %d of the batch: ", i);
-      B->err = std::string(buf) + B->grids[i]->err;
-      return st[i];
-    }
-  return TOMO_OK;
+  });
+  return batch_first_error(B, st);
 }
 
 tomo_status tomo_batch_size(const tomo_batch* B, int32_t* count) {
@@ -1715,6 +2269,15 @@ tomo_status tomo_batch_destroy(tomo_batch* B) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   }
+  if (B->bst) {
+    cudaStreamSynchronize(B->bst);
+    cudaStreamDestroy(B->bst);
+  }
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->loop) cudaGraphExecDestroy(B->loop);
+  if (B->d_scs) cudaFree(B->d_scs);
+  for (auto e : B->wev) cudaEventDestroy(e);
+  if (B->bev) cudaEventDestroy(B->bev);
   delete B;
   return TOMO_OK;
 }

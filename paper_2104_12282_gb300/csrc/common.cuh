@@ -144,12 +144,15 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Sum NV doubles over the block, then over the grid: every block writes its partial to
-// partials[NV*blockIdx + v]; the last block to finish adds the partials in block order
-// (deterministic) and calls fin(totals) with thread 0.  counter must start at 0 and is
-// reset by the last block.  All threads of the block must call this.
+// Sum NV doubles over the block, then over the blocks of one grid's work: block b of nb
+// writes its partial to partials[NV*b + v]; the last block to finish adds the partials in
+// block order (deterministic) and calls fin(totals) with thread 0.  counter must start at 0
+// and is reset by the last block.  All threads of the block must call this.  (b, nb) are
+// the launch's own block index and count, or a block's place within one grid of a batched
+// launch.
 template <int NV, class Fin>
-__device__ void grid_reduce(double (&v)[NV], double* partials, unsigned* counter, Fin fin) {
+__device__ void grid_reduce_at(double (&v)[NV], double* partials, unsigned* counter, Fin fin,
+                               unsigned b_self, unsigned nb) {
   __shared__ double s_red[32][NV];
   __shared__ bool s_last;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
@@ -166,11 +169,10 @@ __device__ void grid_reduce(double (&v)[NV], double* partials, unsigned* counter
     for (int q = 0; q < NV; ++q) {
       double s = lane < nw ? s_red[lane][q] : 0.0;
       s = warp_sum(s);
-      if (lane == 0) partials[(size_t)NV * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) + q] = s;
+      if (lane == 0) partials[(size_t)NV * b_self + q] = s;
     }
     if (lane == 0) {
       __threadfence();
-      unsigned nb = gridDim.x * gridDim.y * gridDim.z;
       unsigned t = atomicAdd(counter, 1u);
       s_last = (t == nb - 1);
     }
@@ -178,7 +180,6 @@ __device__ void grid_reduce(double (&v)[NV], double* partials, unsigned* counter
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
@@ -206,6 +207,30 @@ __device__ void grid_reduce(double (&v)[NV], double* partials, unsigned* counter
   }
 }
 
+template <int NV, class Fin>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], double* partials,
+                                            unsigned* counter, Fin fin) {
+  grid_reduce_at<NV>(v, partials, counter, fin,
+                     blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                     gridDim.x * gridDim.y * gridDim.z);
+}
+
+// Batched launches: one launch runs the same operation for up to kBatchMax grids; grid q
+// owns the launch's blocks [cta0[q], cta0[q+1]).  Returns q for block `cta` (binary search;
+// cta0 is non-decreasing, cta0[0] = 0, cta < cta0[n]).
+__device__ __forceinline__ int batch_owner(const int* cta0, int n, int cta) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta0[mid] <= cta) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 #endif  // __CUDACC__
+
+// Grids per batched launch (bounded by the kernel parameter space the tables use).
+constexpr int kBatchMax = 64;
 
 }  // namespace tomo

@@ -64,6 +64,88 @@ struct MarchArgs {
   float* yf;
 };
 
+// Table of a batched FP64 residual launch (gated residual replacement of several FP32
+// grids: float-pair input joined in double, residual rounded to float): grid q owns the
+// launch's blocks [cta0[q], cta0[q+1]) laid out as its own (gx, gy, z-chunk) grid.
+struct MarchRrBatch {
+  int n;
+  int cta0[kBatchMax + 1];
+  short gx[kBatchMax], gy[kBatchMax];
+  MarchArgs<double> a[kBatchMax];
+};
+cudaError_t launch_march_rr_batch(cudaStream_t st, const MarchArgs<double>* a, int n,
+                                  const ElemConst<double>& c, int num_sms);
+
+// Batched pointwise/vector kernels (vec.cu) for FP32 grids: one entry per grid, the grid
+// owning the launch's blocks [cta0[q], cta0[q+1]).
+struct JacobiItem {  // zero-start first Chebyshev step x1 = c2 D^-1 b
+  Geom g;
+  const float* s;
+  const uint8_t* mask;
+  const float* b;
+  float c2, k0diag;
+  float* x1;
+  const int* skip;
+};
+struct RestrictItem {  // r_c = P^T r_f (+ fused zero-start step on the coarse level)
+  Geom gf, gc;
+  const float* rf;
+  float* rc;
+  const uint8_t* mask_c;
+  const int* skip;
+  float* x1;  // nullptr: no fused step
+  const float* sc;
+  float c2, k0diag;
+};
+struct ProlongItem {  // x_f += P x_c
+  Geom gf, gc;
+  const float* xc;
+  float* xf;
+  const uint8_t* mask_f;
+  const int* skip;
+};
+struct CoarseItem {  // z = D^-1/2 Ainv D^-1/2 r on the coarsest level
+  int n;
+  const float* Ainv;
+  const float* dsc;
+  const float* r;
+  float* z;
+  const int* skip;
+};
+struct CgXrItem {  // x += alpha p (float pair), r -= alpha q, r.r -> convergence
+  int n;
+  float* xhi;
+  float* xlo;
+  float* r;
+  const float* p;
+  const float* q;
+  double* partials;
+  unsigned* counter;
+  CgScalars* sc;
+};
+struct CgPItem {  // p = z + beta p
+  int n;
+  float* p;
+  const float* z;
+  CgScalars* sc;
+};
+template <class Item>
+struct FlatBatch {
+  int n;
+  int cta0[kBatchMax + 1];
+  Item a[kBatchMax];
+};
+cudaError_t launch_jacobi_batch(cudaStream_t st, const JacobiItem* a, int n);
+cudaError_t launch_restrict_batch(cudaStream_t st, const RestrictItem* a, int n);
+cudaError_t launch_prolong_batch(cudaStream_t st, const ProlongItem* a, int n);
+cudaError_t launch_coarse_apply_batch(cudaStream_t st, const CoarseItem* a, int n);
+cudaError_t launch_cg_xr_batch(cudaStream_t st, const CgXrItem* a, int n);
+cudaError_t launch_cg_p_batch(cudaStream_t st, const CgPItem* a, int n);
+// conditional-while control of a batched CG loop: continue while any of the n grids whose
+// scalars scs[0..n) (device array) point to has not stopped
+cudaError_t launch_loop_cond_batch(cudaStream_t st, cudaGraphConditionalHandle h,
+                                   CgScalars* const* scs, int n);
+
 // FP32 two-rows-per-thread product (matvec2.cu); same modes as k_march, no pair input.
 struct March2Args {
   Geom g;
@@ -90,6 +172,20 @@ std::vector<uint8_t> march2_tile_flags(const Geom& g, const std::vector<uint8_t>
 struct March2Const {
   float a0, b0, a7, b7, ta, tb, ua, ud, k0diag;
 };
+// Table of a batched k_march2 launch (a kernel parameter): grid q owns the launch's blocks
+// [cta0[q], cta0[q+1]) laid out as its own (gx, gy, z-chunk) grid.
+struct March2Batch {
+  int n;
+  int cta0[kBatchMax + 1];
+  short gx[kBatchMax], gy[kBatchMax];
+  March2Args a[kBatchMax];
+};
+// The same k_march2 operation on n grids (all with the same mode and dot flag) in
+// ceil(n / kBatchMax) launches; each grid gets the tiles of its own launch and z-chunks of
+// a[q].kz node planes (kz <= 0: the chunks of its own launch).  Only the fused dot depends
+// on the chunking (its per-block partials); the products themselves do not.
+cudaError_t launch_march2_batch(cudaStream_t st, int mode, const March2Args* a, int n,
+                                const March2Const& c, int num_sms);
 cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const March2Const& c,
                           int num_sms);
 

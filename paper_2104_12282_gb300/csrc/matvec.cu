@@ -13,6 +13,8 @@
 // +y corners through shared memory, +z corners carried in registers to the next plane.
 // Lanes 0 and 31 and rows 0 and kTY-1 are halo (their outputs are not written); each
 // z-chunk recomputes one element layer below it.
+#include <algorithm>
+
 #include "common.cuh"
 #include "host.h"
 
@@ -80,18 +82,20 @@ __device__ __forceinline__ void block_apply(const ElemConst<T>& C, T se, const T
   }
 }
 
+// One CTA: tile (bx, by), z-chunk bz; blin / nblk: the CTA's linear index and the CTA count
+// of this grid's launch (for the fused dot).
 template <typename T, int MODE, bool PAIR, bool DOT>
-__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
-    k_march(const __grid_constant__ MarchArgs<T> A, const __grid_constant__ ElemConst<T> C) {
+__device__ __forceinline__ void march_body(const MarchArgs<T>& A, const ElemConst<T>& C, int bx,
+                                           int by, int bz, unsigned blin, unsigned nblk) {
   PDL_ENTER();
   if (A.skip != nullptr && *A.skip) return;
   if (A.gate != nullptr && (A.gate->rr_every <= 0 || (A.gate->it % A.gate->rr_every) != 0))
     return;
   const Geom g = A.g;
   const int l = threadIdx.x, r = threadIdx.y;
-  const int i = (int)blockIdx.x * 30 - 1 + l;
-  const int j = (int)blockIdx.y * (kTY - 2) - 1 + r;
-  const int kb = (int)blockIdx.z * A.kz;
+  const int i = bx * 30 - 1 + l;
+  const int j = by * (kTY - 2) - 1 + r;
+  const int kb = bz * A.kz;
   const int ke = min(kb + A.kz, g.nzn);
   const int nn = g.nn;
   const bool col_in = (i >= 0 && i < g.nxn && j >= 0 && j < g.nyn);
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
     double v[1] = {dot};
     CgScalars* sc = A.sc;
     const int kind = A.dot_kind;
-    grid_reduce<1>(v, A.partials, A.counter, [sc, kind](const double* tot) {
+    grid_reduce_at<1>(v, A.partials, A.counter, [sc, kind](const double* tot) {
       if (kind == 1) {
         sc->pq = tot[0];
         if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
@@ -320,8 +324,78 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
         sc->beta = sc->rz != 0.0 ? tot[0] / sc->rz : 0.0;
         sc->rz = tot[0];
       }
-    });
+    }, blin, nblk);
   }
+}
+
+template <typename T, int MODE, bool PAIR, bool DOT>
+__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 2 : 1)
+    k_march(const __grid_constant__ MarchArgs<T> A, const __grid_constant__ ElemConst<T> C) {
+  march_body<T, MODE, PAIR, DOT>(A, C, blockIdx.x, blockIdx.y, blockIdx.z,
+                                 blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                                 gridDim.x * gridDim.y * gridDim.z);
+}
+
+// The FP64 residual of a float pair (r = f - K (x_hi + x_lo), gated residual replacement)
+// for several grids in one launch; block b belongs to grid q with cta0[q] <= b < cta0[q+1].
+__global__ void __launch_bounds__(32 * kTY, 1)
+    k_march_rr_batch(const __grid_constant__ MarchRrBatch B,
+                     const __grid_constant__ ElemConst<double> C) {
+  const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
+  const int loc = (int)blockIdx.x - B.cta0[q];
+  const int gx = B.gx[q], gy = B.gy[q];
+  march_body<double, M_RESID, true, false>(B.a[q], C, loc % gx, (loc / gx) % gy,
+                                           loc / (gx * gy), (unsigned)loc,
+                                           (unsigned)(B.cta0[q + 1] - B.cta0[q]));
+}
+
+namespace {
+
+struct MarchShape {
+  int gx, gy, kz, nzc;
+};
+
+template <typename T>
+MarchShape march_shape(const Geom& g, int num_sms) {
+  MarchShape m;
+  m.gx = (g.nxn + 29) / 30;
+  m.gy = (g.nyn + kTY - 3) / (kTY - 2);
+  // z-chunks: about one full wave of resident CTAs (2 per SM), chunks of >= 4 planes
+  const int tiles = m.gx * m.gy;
+  const int target = (sizeof(T) == 4 ? 2 : 1) * (num_sms > 0 ? num_sms : 152);
+  int nzc = target / tiles;
+  if (nzc < 1) nzc = 1;
+  int kz = (g.nzn + nzc - 1) / nzc;
+  if (kz < 4) kz = 4;
+  if (kz > g.nzn) kz = g.nzn;
+  m.kz = kz;
+  m.nzc = (g.nzn + kz - 1) / kz;
+  return m;
+}
+
+}  // namespace
+
+cudaError_t launch_march_rr_batch(cudaStream_t st, const MarchArgs<double>* a, int n,
+                                  const ElemConst<double>& c, int num_sms) {
+  for (int q0 = 0; q0 < n; q0 += kBatchMax) {
+    MarchRrBatch B{};
+    B.n = std::min(kBatchMax, n - q0);
+    int ctas = 0;
+    for (int q = 0; q < B.n; ++q) {
+      const MarchShape m = march_shape<double>(a[q0 + q].g, num_sms);
+      B.a[q] = a[q0 + q];
+      B.a[q].kz = m.kz;
+      B.gx[q] = m.gx;
+      B.gy[q] = m.gy;
+      B.cta0[q] = ctas;
+      ctas += m.gx * m.gy * m.nzc;
+    }
+    B.cta0[B.n] = ctas;
+    pdl_launch(k_march_rr_batch, dim3(ctas), dim3(32, kTY), 0, st, B, c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -329,18 +403,9 @@ cudaError_t launch_march(cudaStream_t st, int mode, const MarchArgs<T>& a, const
                          int num_sms, int* grid_ctas) {
   const Geom& g = a.g;
   MarchArgs<T> args = a;
-  const int gx = (g.nxn + 29) / 30;
-  const int gy = (g.nyn + kTY - 3) / (kTY - 2);
-  // z-chunks: about one full wave of resident CTAs (2 per SM), chunks of >= 4 planes
-  const int tiles = gx * gy;
-  const int target = (sizeof(T) == 4 ? 2 : 1) * (num_sms > 0 ? num_sms : 152);
-  int nzc = target / tiles;
-  if (nzc < 1) nzc = 1;
-  int kz = (g.nzn + nzc - 1) / nzc;
-  if (kz < 4) kz = 4;
-  if (kz > g.nzn) kz = g.nzn;
-  nzc = (g.nzn + kz - 1) / kz;
-  args.kz = kz;
+  const MarchShape m = march_shape<T>(g, num_sms);
+  const int gx = m.gx, gy = m.gy, nzc = m.nzc;
+  args.kz = m.kz;
   dim3 grid(gx, gy, nzc), block(32, kTY);
   if (grid_ctas) *grid_ctas = gx * gy * nzc;
   const bool pair = sizeof(T) == 4 ? a.xlo != nullptr : a.xf_hi != nullptr;

@@ -48,20 +48,22 @@ __device__ __forceinline__ float2 shup2(float2 v) {
   return make_float2(__shfl_up_sync(FULL, v.x, 1), __shfl_up_sync(FULL, v.y, 1));
 }
 
+// One CTA of the product: tile (bx, by) of gx tiles along x, z-chunk bz; blin / nblk are the
+// CTA's linear index and the CTA count of this grid's launch (for the fused dot).
 template <int MODE, bool DOT>
-__global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
-    k_march2(const __grid_constant__ March2Args A, const __grid_constant__ March2Const K) {
+__device__ __forceinline__ void march2_body(const March2Args& A, const March2Const& K, int bx,
+                                            int by, int bz, int gx, unsigned blin,
+                                            unsigned nblk) {
   constexpr bool CHEBY = MODE == M_CHEB;
   PDL_ENTER();
   if (A.skip != nullptr && *A.skip) return;
   const Geom g = A.g;
   const int l = threadIdx.x, t = threadIdx.y;
-  const int i = (int)blockIdx.x * 30 - 1 + l;
-  const int j0 = (int)blockIdx.y * (2 * TYP - 2) - 1 + 2 * t;
+  const int i = bx * 30 - 1 + l;
+  const int j0 = by * (2 * TYP - 2) - 1 + 2 * t;
   const int j1 = j0 + 1;
-  const bool tile_fixed =
-      A.tile_fixed == nullptr || A.tile_fixed[blockIdx.x + gridDim.x * blockIdx.y] != 0;
-  const int kb = (int)blockIdx.z * A.kz;
+  const bool tile_fixed = A.tile_fixed == nullptr || A.tile_fixed[bx + gx * by] != 0;
+  const int kb = bz * A.kz;
   const int ke = min(kb + A.kz, g.nzn);
   const int nn = g.nn, plane = g.nxn * g.nyn, eplane = g.nx * g.ny;
   const bool col_i = i >= 0 && i < g.nxn;
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
     double v[1] = {((double)dhi.x + (double)dlo.x) + ((double)dhi.y + (double)dlo.y)};
     CgScalars* sc = A.sc;
     const int kind = A.dot_kind;
-    grid_reduce<1>(v, A.partials, A.counter, [sc, kind](const double* tot) {
+    grid_reduce_at<1>(v, A.partials, A.counter, [sc, kind](const double* tot) {
       if (kind == 1) {
         sc->pq = tot[0];
         if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
@@ -379,8 +381,30 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
         sc->beta = sc->rz != 0.0 ? tot[0] / sc->rz : 0.0;
         sc->rz = tot[0];
       }
-    });
+    }, blin, nblk);
   }
+}
+
+template <int MODE, bool DOT>
+__global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
+    k_march2(const __grid_constant__ March2Args A, const __grid_constant__ March2Const K) {
+  march2_body<MODE, DOT>(A, K, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x,
+                         blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                         gridDim.x * gridDim.y * gridDim.z);
+}
+
+// The same operation for several grids in one launch: block b belongs to grid q with
+// cta0[q] <= b < cta0[q+1] and is that grid's block b - cta0[q] in the order of k_march2's
+// (x, y, z) grid, so each grid sees exactly the blocks (and the dot partials) of its own
+// launch.
+template <int MODE, bool DOT>
+__global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
+    k_march2_batch(const __grid_constant__ March2Batch B, const __grid_constant__ March2Const K) {
+  const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
+  const int loc = (int)blockIdx.x - B.cta0[q];
+  const int gx = B.gx[q], gy = B.gy[q];
+  march2_body<MODE, DOT>(B.a[q], K, loc % gx, (loc / gx) % gy, loc / (gx * gy), gx,
+                         (unsigned)loc, (unsigned)(B.cta0[q + 1] - B.cta0[q]));
 }
 
 }  // namespace
@@ -403,25 +427,32 @@ std::vector<uint8_t> march2_tile_flags(const Geom& g, const std::vector<uint8_t>
   return f;
 }
 
-cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const March2Const& c,
-                          int num_sms) {
-  const Geom& g = a.g;
-  March2Args args = a;
-  const int gx = (g.nxn + 29) / 30;
-  const int gy = (g.nyn + 2 * TYP - 3) / (2 * TYP - 2);
-  const int tiles = gx * gy;
-  // one wave of resident CTAs (occupancy of the instance that will run)
+namespace {
+
+struct March2Shape {
+  int gx, gy, kz, nzc;
+};
+
+// Tiles and z-chunks of one grid's launch (the same for a single and a batched launch, so
+// that a grid's arithmetic does not depend on how it was launched).
+March2Shape march2_shape(int mode, bool dot, const Geom& g, int num_sms) {
+  March2Shape m;
+  m.gx = (g.nxn + 29) / 30;
+  m.gy = (g.nyn + 2 * TYP - 3) / (2 * TYP - 2);
+  const int tiles = m.gx * m.gy;
+  // one wave of resident CTAs (occupancy of the single-grid instance)
   int per_sm = 0;
   cudaError_t oe;
   if (mode == M_APPLY)
     oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, a.dot_kind ? k_march2<M_APPLY, true> : k_march2<M_APPLY, false>, 32 * TYP, 0);
+        &per_sm, dot ? k_march2<M_APPLY, true> : k_march2<M_APPLY, false>, 32 * TYP, 0);
   else if (mode == M_RESID)
     oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march2<M_RESID, false>,
                                                        32 * TYP, 0);
   else
     oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, a.dot_kind ? k_march2<M_CHEB, true> : k_march2<M_CHEB, false>, 32 * TYP, 0);
+        &per_sm, dot ? k_march2<M_CHEB, true> : k_march2<M_CHEB, false>, 32 * TYP, 0);
+  if (oe != cudaSuccess) cudaGetLastError();
   if (oe != cudaSuccess || per_sm < 1) per_sm = 2;
   const int target = per_sm * (num_sms > 0 ? num_sms : 152);
   // Each CTA marches kz + 1 element layers one after another, so a launch takes at least
@@ -430,8 +461,61 @@ cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const 
   int kz = (int)(((long long)g.nzn * tiles + target - 1) / target);
   if (kz < 1) kz = 1;
   if (kz > g.nzn) kz = g.nzn;
-  const int nzc = (g.nzn + kz - 1) / kz;
-  args.kz = kz;
+  m.kz = kz;
+  m.nzc = (g.nzn + kz - 1) / kz;
+  return m;
+}
+
+}  // namespace
+
+cudaError_t launch_march2_batch(cudaStream_t st, int mode, const March2Args* a, int n,
+                                const March2Const& c, int num_sms) {
+  if (n <= 0) return cudaSuccess;
+  const bool dot = a[0].dot_kind != 0;
+  for (int q = 0; q < n; ++q)
+    if ((a[q].dot_kind != 0) != dot) return cudaErrorInvalidValue;
+  for (int q0 = 0; q0 < n; q0 += kBatchMax) {
+    March2Batch B{};
+    B.n = std::min(kBatchMax, n - q0);
+    int ctas = 0;
+    for (int q = 0; q < B.n; ++q) {
+      March2Shape m = march2_shape(mode, dot, a[q0 + q].g, num_sms);
+      if (a[q0 + q].kz > 0) {  // z-chunk length chosen by the caller for the whole batch
+        m.kz = std::min(a[q0 + q].kz, a[q0 + q].g.nzn);
+        m.nzc = (a[q0 + q].g.nzn + m.kz - 1) / m.kz;
+      }
+      B.a[q] = a[q0 + q];
+      B.a[q].kz = m.kz;
+      B.gx[q] = m.gx;
+      B.gy[q] = m.gy;
+      B.cta0[q] = ctas;
+      ctas += m.gx * m.gy * m.nzc;
+    }
+    B.cta0[B.n] = ctas;
+    dim3 grid(ctas), block(32, TYP);
+    if (mode == M_APPLY) {
+      if (dot) pdl_launch(k_march2_batch<M_APPLY, true>, grid, block, 0, st, B, c);
+      else pdl_launch(k_march2_batch<M_APPLY, false>, grid, block, 0, st, B, c);
+    } else if (mode == M_RESID) {
+      if (dot) return cudaErrorInvalidValue;
+      pdl_launch(k_march2_batch<M_RESID, false>, grid, block, 0, st, B, c);
+    } else {
+      if (dot) pdl_launch(k_march2_batch<M_CHEB, true>, grid, block, 0, st, B, c);
+      else pdl_launch(k_march2_batch<M_CHEB, false>, grid, block, 0, st, B, c);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const March2Const& c,
+                          int num_sms) {
+  const Geom& g = a.g;
+  March2Args args = a;
+  const March2Shape m = march2_shape(mode, a.dot_kind != 0, g, num_sms);
+  const int gx = m.gx, gy = m.gy, nzc = m.nzc;
+  args.kz = m.kz;
   dim3 grid(gx, gy, nzc), block(32, TYP);
   const bool dot = a.dot_kind != 0;
   if (mode == M_APPLY) {

@@ -1,6 +1,8 @@
 // Multigrid transfers, coarse operators, the coarsest dense solve, CG recurrences and
 // reductions.  The solve of the state equation of Eq. 4 (Section III-D) is preconditioned
 // CG, the standard solver the paper names (PCG; multigrid is the stated alternative).
+#include <algorithm>
+
 #include "common.cuh"
 #include "host.h"
 
@@ -16,16 +18,20 @@ __device__ __forceinline__ bool skipped(const int* skip) { return skip != nullpt
 // over the elements around the node) is the diagonal of K (all three components equal).
 // Optional dot b.x1 for the Jacobi-preconditioned CG (dot_kind 2).
 // ---------------------------------------------------------------------------------------
+// (vb, vnb): the block's index and the block count of this grid's launch (grid-stride loop
+// and dot partials); batched launches pass a block's place within its grid.
 template <typename T, bool DOT>
-__global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restrict__ mask,
-                         const T* __restrict__ b, T c2, T k0diag, T* __restrict__ x1,
-                         T* __restrict__ x0, double* partials, unsigned* counter, CgScalars* sc,
-                         const int* skip) {
+__device__ __forceinline__ void jacobi_body(int vb, int vnb, Geom g, const T* __restrict__ s,
+                                            const uint8_t* __restrict__ mask,
+                                            const T* __restrict__ b, T c2, T k0diag,
+                                            T* __restrict__ x1, T* __restrict__ x0,
+                                            double* partials, unsigned* counter,
+                                            CgScalars* sc, const int* skip) {
   PDL_ENTER();
   if (skipped(skip)) return;
   double dot = 0.0;       // FP64 grids
   FloatPairSum dotf;      // FP32 grids
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nn; n += gridDim.x * blockDim.x) {
+  for (int n = vb * blockDim.x + threadIdx.x; n < g.nn; n += vnb * blockDim.x) {
     const int i = n % g.nxn, j = (n / g.nxn) % g.nyn, k = n / (g.nxn * g.nyn);
     // the (up to) eight elements around the node: indices clamped, absent ones weighted 0
     const int xa = max(i - 1, 0), xb = min(i, g.nx - 1);
@@ -55,13 +61,22 @@ __global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restr
   if (DOT) {
     if constexpr (sizeof(T) == 4) dot = dotf.value();
     double v[1] = {dot};
-    grid_reduce<1>(v, partials, counter, [sc](const double* tot) {
+    grid_reduce_at<1>(v, partials, counter, [sc](const double* tot) {
       sc->rz_new = tot[0];
       if (!isfinite(tot[0])) { sc->status |= DEV_NAN; sc->done = 1; }
       sc->beta = sc->rz != 0.0 ? tot[0] / sc->rz : 0.0;
       sc->rz = tot[0];
-    });
+    }, vb, vnb);
   }
+}
+
+template <typename T, bool DOT>
+__global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restrict__ mask,
+                         const T* __restrict__ b, T c2, T k0diag, T* __restrict__ x1,
+                         T* __restrict__ x0, double* partials, unsigned* counter, CgScalars* sc,
+                         const int* skip) {
+  jacobi_body<T, DOT>(blockIdx.x, gridDim.x, g, s, mask, b, c2, k0diag, x1, x0, partials,
+                      counter, sc, skip);
 }
 
 template <typename T>
@@ -88,12 +103,14 @@ cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* ma
 // Optionally fused with the first (zero-start) Chebyshev step on the coarse level:
 // x1 = c2 D^-1 r_c, D from the coarse moduli sc.
 template <typename T>
-__global__ void k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ rc,
-                           const uint8_t* __restrict__ mask_c, const int* skip,
-                           T* __restrict__ x1, const T* __restrict__ sc, T c2, T k0diag) {
+__device__ __forceinline__ void restrict_body(int vb, int vnb, Geom gf, Geom gc,
+                                              const T* __restrict__ rf, T* __restrict__ rc,
+                                              const uint8_t* __restrict__ mask_c,
+                                              const int* skip, T* __restrict__ x1,
+                                              const T* __restrict__ sc, T c2, T k0diag) {
   PDL_ENTER();
   if (skipped(skip)) return;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gc.nn; n += gridDim.x * blockDim.x) {
+  for (int n = vb * blockDim.x + threadIdx.x; n < gc.nn; n += vnb * blockDim.x) {
     const int I = n % gc.nxn, J = (n / gc.nxn) % gc.nyn, K = n / (gc.nxn * gc.nyn);
     // fine indices 2I-1, 2I, 2I+1 per axis with weights 1/2, 1, 1/2; indices outside the
     // fine grid are clamped and weighted 0 (same code path for every node)
@@ -147,6 +164,13 @@ __global__ void k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __rest
 }
 
 template <typename T>
+__global__ void k_restrict(Geom gf, Geom gc, const T* __restrict__ rf, T* __restrict__ rc,
+                           const uint8_t* __restrict__ mask_c, const int* skip,
+                           T* __restrict__ x1, const T* __restrict__ sc, T c2, T k0diag) {
+  restrict_body<T>(blockIdx.x, gridDim.x, gf, gc, rf, rc, mask_c, skip, x1, sc, c2, k0diag);
+}
+
+template <typename T>
 cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* rc,
                             const uint8_t* mask_c, const int* skip, T* x1, const T* sc, T c2,
                             T k0diag) {
@@ -160,11 +184,13 @@ cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* r
 // the same 2x2x2 form (an even index uses one coarse node with weights 1 and 0), so the
 // warp does not diverge on index parity.
 template <typename T>
-__global__ void k_prolong_add(Geom gf, Geom gc, const T* __restrict__ xc, T* __restrict__ xf,
-                              const uint8_t* __restrict__ mask_f, const int* skip) {
+__device__ __forceinline__ void prolong_body(int vb, int vnb, Geom gf, Geom gc,
+                                             const T* __restrict__ xc, T* __restrict__ xf,
+                                             const uint8_t* __restrict__ mask_f,
+                                             const int* skip) {
   PDL_ENTER();
   if (skipped(skip)) return;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gf.nn; n += gridDim.x * blockDim.x) {
+  for (int n = vb * blockDim.x + threadIdx.x; n < gf.nn; n += vnb * blockDim.x) {
     const int i = n % gf.nxn, j = (n / gf.nxn) % gf.nyn, k = n / (gf.nxn * gf.nyn);
     const int i0 = i >> 1, i1 = (i + 1) >> 1;
     const int j0 = j >> 1, j1 = (j + 1) >> 1;
@@ -188,6 +214,12 @@ __global__ void k_prolong_add(Geom gf, Geom gc, const T* __restrict__ xc, T* __r
       if (!((mk >> c) & 1u)) xf[idx] += acc;
     }
   }
+}
+
+template <typename T>
+__global__ void k_prolong_add(Geom gf, Geom gc, const T* __restrict__ xc, T* __restrict__ xf,
+                              const uint8_t* __restrict__ mask_f, const int* skip) {
+  prolong_body<T>(blockIdx.x, gridDim.x, gf, gc, xc, xf, mask_f, skip);
 }
 
 template <typename T>
@@ -358,10 +390,10 @@ cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint
 // z = D^-1/2 Ainv D^-1/2 r.  Ainv is symmetric, so thread `row` walks column `row`
 // (Ainv[c * n + row], consecutive threads read consecutive addresses); accumulated in T.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_apply(int n, const T* __restrict__ Ainv,
-                                                       const T* __restrict__ dsc,
-                                                       const T* __restrict__ r, T* __restrict__ z,
-                                                       const int* skip) {
+__device__ __forceinline__ void coarse_apply_body(int n, const T* __restrict__ Ainv,
+                                                  const T* __restrict__ dsc,
+                                                  const T* __restrict__ r, T* __restrict__ z,
+                                                  const int* skip) {
   PDL_ENTER();
   if (skipped(skip)) return;
   extern __shared__ unsigned char smem_raw[];
@@ -380,6 +412,14 @@ __global__ void __launch_bounds__(1024) k_coarse_apply(int n, const T* __restric
     for (; c < n; ++c) a0 += __ldg(Ainv + (size_t)c * n + row) * rs[c];
     z[row] = dsc[row] * ((a0 + a1) + (a2 + a3));
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_apply(int n, const T* __restrict__ Ainv,
+                                                       const T* __restrict__ dsc,
+                                                       const T* __restrict__ r, T* __restrict__ z,
+                                                       const int* skip) {
+  coarse_apply_body<T>(n, Ainv, dsc, r, z, skip);
 }
 
 template <typename T>
@@ -410,16 +450,18 @@ __device__ __forceinline__ void pair_axpy(float alpha, float pv, float& hi, floa
 }
 
 template <typename T, bool PAIRX>
-__global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __restrict__ r,
-                        const T* __restrict__ p, const T* __restrict__ q, double* partials,
-                        unsigned* counter, CgScalars* sc) {
+__device__ __forceinline__ void cg_xr_body(int vb, int vnb, int n, T* __restrict__ xhi,
+                                           T* __restrict__ xlo, T* __restrict__ r,
+                                           const T* __restrict__ p, const T* __restrict__ q,
+                                           double* partials, unsigned* counter,
+                                           CgScalars* sc) {
   PDL_ENTER();
   if (sc->done) return;
   const double alpha_d = sc->alpha;
   const T alpha = (T)alpha_d;
   double acc = 0.0;      // FP64 grids
   FloatPairSum accf;     // FP32 grids
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  const int tid = vb * blockDim.x + threadIdx.x, nt = vnb * blockDim.x;
   int i0 = 0;
   if constexpr (sizeof(T) == 4) {
     // float4 body: 16-byte accesses keep enough bytes in flight to stream at HBM rate
@@ -472,27 +514,44 @@ __global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __re
   }
   if constexpr (sizeof(T) == 4) acc = accf.value();
   double v[1] = {acc};
-  grid_reduce<1>(v, partials, counter, [sc](const double* tot) {
+  grid_reduce_at<1>(v, partials, counter, [sc](const double* tot) {
     sc->rr = tot[0];
     sc->it += 1;
     if (!isfinite(tot[0])) { sc->status |= DEV_NAN; sc->done = 1; }
     else if (tot[0] <= sc->tol2 || sc->it >= sc->maxit) sc->done = 1;
-  });
+  }, vb, vnb);
+}
+
+template <typename T, bool PAIRX>
+__global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __restrict__ r,
+                        const T* __restrict__ p, const T* __restrict__ q, double* partials,
+                        unsigned* counter, CgScalars* sc) {
+  cg_xr_body<T, PAIRX>(blockIdx.x, gridDim.x, n, xhi, xlo, r, p, q, partials, counter, sc);
+}
+
+// Blocks of the x/r update of an n-vector: enough for 16-byte accesses at HBM rate on large
+// grids (two waves of 304), fewer on small ones (one float4 per thread and pass); the same
+// count whether the grid is launched alone or in a batch, so that the reduction order and
+// the result do not depend on it.
+int cg_xr_blocks(int n) {
+  const int b = ((n >> 2) + kRedThreads - 1) / kRedThreads;
+  return b < 1 ? 1 : (b > 2 * kRedBlocks ? 2 * kRedBlocks : b);
 }
 
 template <typename T>
 cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* p, const T* q,
                          double* partials, unsigned* counter, CgScalars* sc) {
+  const int blocks = cg_xr_blocks(n);
   if (xlo) {
     if constexpr (sizeof(T) == 4) {
-      pdl_launch(k_cg_xr<T, true>, kRedBlocks * 2, kRedThreads, 0, st, n, xhi, xlo, r, p, q, partials,
-                                                               counter, sc);
+      pdl_launch(k_cg_xr<T, true>, blocks, kRedThreads, 0, st, n, xhi, xlo, r, p, q, partials,
+                 counter, sc);
       return cudaGetLastError();
     }
     return cudaErrorInvalidValue;
   }
-  pdl_launch(k_cg_xr<T, false>, kRedBlocks * 2, kRedThreads, 0, st, n, xhi, nullptr, r, p, q, partials,
-                                                            counter, sc);
+  pdl_launch(k_cg_xr<T, false>, blocks, kRedThreads, 0, st, n, xhi, nullptr, r, p, q, partials,
+             counter, sc);
   return cudaGetLastError();
 }
 
@@ -513,11 +572,12 @@ cudaError_t launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, CgSc
 
 // p = z + beta p
 template <typename T>
-__global__ void k_cg_p(int n, T* __restrict__ p, const T* __restrict__ z, CgScalars* sc) {
+__device__ __forceinline__ void cg_p_body(int vb, int vnb, int n, T* __restrict__ p,
+                                          const T* __restrict__ z, CgScalars* sc) {
   PDL_ENTER();
   if (sc->done) return;
   const T beta = (T)sc->beta;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  const int tid = vb * blockDim.x + threadIdx.x, nt = vnb * blockDim.x;
   int i0 = 0;
   if constexpr (sizeof(T) == 4) {
     const int n4 = n >> 2;
@@ -536,10 +596,160 @@ __global__ void k_cg_p(int n, T* __restrict__ p, const T* __restrict__ z, CgScal
 }
 
 template <typename T>
+__global__ void k_cg_p(int n, T* __restrict__ p, const T* __restrict__ z, CgScalars* sc) {
+  cg_p_body<T>(blockIdx.x, gridDim.x, n, p, z, sc);
+}
+
+template <typename T>
 cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc) {
   int blocks = (n + 255) / 256;
   if (blocks > 8 * 152) blocks = 8 * 152;
   pdl_launch(k_cg_p<T>, blocks, 256, 0, st, n, p, z, sc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched launches (FP32): block b belongs to grid q with cta0[q] <= b < cta0[q+1] and acts
+// as block b - cta0[q] of cta0[q+1] - cta0[q]; each grid gets the block count its own launch
+// would use, so its results do not depend on the batch.
+// ---------------------------------------------------------------------------------------
+__global__ void k_jacobi_batch(const __grid_constant__ FlatBatch<JacobiItem> B) {
+  const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
+  const JacobiItem& a = B.a[q];
+  jacobi_body<float, false>((int)blockIdx.x - B.cta0[q], B.cta0[q + 1] - B.cta0[q], a.g, a.s,
+                            a.mask, a.b, a.c2, a.k0diag, a.x1, nullptr, nullptr, nullptr,
+                            nullptr, a.skip);
+}
+
+__global__ void k_restrict_batch(const __grid_constant__ FlatBatch<RestrictItem> B) {
+  const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
+  const RestrictItem& a = B.a[q];
+  restrict_body<float>((int)blockIdx.x - B.cta0[q], B.cta0[q + 1] - B.cta0[q], a.gf, a.gc,
+                       a.rf, a.rc, a.mask_c, a.skip, a.x1, a.sc, a.c2, a.k0diag);
+}
+
+__global__ void k_prolong_batch(const __grid_constant__ FlatBatch<ProlongItem> B) {
+  const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
+  const ProlongItem& a = B.a[q];
+  prolong_body<float>((int)blockIdx.x - B.cta0[q], B.cta0[q + 1] - B.cta0[q], a.gf, a.gc,
+                      a.xc, a.xf, a.mask_f, a.skip);
+}
+
+// one block per grid
+__global__ void __launch_bounds__(1024)
+    k_coarse_apply_batch(const __grid_constant__ FlatBatch<CoarseItem> B) {
+  const CoarseItem& a = B.a[blockIdx.x];
+  coarse_apply_body<float>(a.n, a.Ainv, a.dsc, a.r, a.z, a.skip);
+}
+
+__global__ void k_cg_xr_batch(const __grid_constant__ FlatBatch<CgXrItem> B) {
+  const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
+  const CgXrItem& a = B.a[q];
+  cg_xr_body<float, true>((int)blockIdx.x - B.cta0[q], B.cta0[q + 1] - B.cta0[q], a.n, a.xhi,
+                          a.xlo, a.r, a.p, a.q, a.partials, a.counter, a.sc);
+}
+
+__global__ void k_cg_p_batch(const __grid_constant__ FlatBatch<CgPItem> B) {
+  const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
+  const CgPItem& a = B.a[q];
+  cg_p_body<float>((int)blockIdx.x - B.cta0[q], B.cta0[q + 1] - B.cta0[q], a.n, a.p, a.z, a.sc);
+}
+
+__global__ void k_loop_cond_batch(cudaGraphConditionalHandle h, CgScalars* const* scs, int n) {
+  PDL_ENTER();
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    CgScalars* sc = scs[q];
+    if (sc->done) continue;
+    sc->loops += 1;
+    if (sc->loops < sc->maxit + 8) atomicOr(&any, 1);
+    else sc->done = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+namespace {
+
+// Fill tables of up to kBatchMax entries with blocks(item) blocks each and launch them.
+template <class Item, class Blocks, class Launch>
+cudaError_t flat_batches(const Item* a, int n, Blocks blocks, Launch launch) {
+  for (int q0 = 0; q0 < n; q0 += kBatchMax) {
+    FlatBatch<Item> B{};
+    B.n = std::min(kBatchMax, n - q0);
+    int ctas = 0;
+    for (int q = 0; q < B.n; ++q) {
+      B.a[q] = a[q0 + q];
+      B.cta0[q] = ctas;
+      ctas += blocks(B.a[q]);
+    }
+    B.cta0[B.n] = ctas;
+    if (ctas > 0) {
+      launch(B, ctas);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+int clamp_blocks(int n, int cap) {
+  const int b = (n + 255) / 256;
+  return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+}  // namespace
+
+cudaError_t launch_jacobi_batch(cudaStream_t st, const JacobiItem* a, int n) {
+  return flat_batches(a, n, [](const JacobiItem& it) { return clamp_blocks(it.g.nn, 4096); },
+                      [st](const FlatBatch<JacobiItem>& B, int ctas) {
+                        pdl_launch(k_jacobi_batch, ctas, 256, 0, st, B);
+                      });
+}
+
+cudaError_t launch_restrict_batch(cudaStream_t st, const RestrictItem* a, int n) {
+  return flat_batches(a, n, [](const RestrictItem& it) { return clamp_blocks(it.gc.nn, 8192); },
+                      [st](const FlatBatch<RestrictItem>& B, int ctas) {
+                        pdl_launch(k_restrict_batch, ctas, 256, 0, st, B);
+                      });
+}
+
+cudaError_t launch_prolong_batch(cudaStream_t st, const ProlongItem* a, int n) {
+  return flat_batches(a, n, [](const ProlongItem& it) { return clamp_blocks(it.gf.nn, 16384); },
+                      [st](const FlatBatch<ProlongItem>& B, int ctas) {
+                        pdl_launch(k_prolong_batch, ctas, 256, 0, st, B);
+                      });
+}
+
+cudaError_t launch_coarse_apply_batch(cudaStream_t st, const CoarseItem* a, int n) {
+  int nmax = 0;
+  for (int q = 0; q < n; ++q) nmax = std::max(nmax, a[q].n);
+  const size_t smem = sizeof(float) * (size_t)nmax;
+  return flat_batches(a, n, [](const CoarseItem&) { return 1; },
+                      [st, smem](const FlatBatch<CoarseItem>& B, int ctas) {
+                        pdl_launch(k_coarse_apply_batch, ctas, 1024, smem, st, B);
+                      });
+}
+
+cudaError_t launch_cg_xr_batch(cudaStream_t st, const CgXrItem* a, int n) {
+  return flat_batches(a, n, [](const CgXrItem& it) { return cg_xr_blocks(it.n); },
+                      [st](const FlatBatch<CgXrItem>& B, int ctas) {
+                        pdl_launch(k_cg_xr_batch, ctas, kRedThreads, 0, st, B);
+                      });
+}
+
+cudaError_t launch_cg_p_batch(cudaStream_t st, const CgPItem* a, int n) {
+  return flat_batches(a, n, [](const CgPItem& it) { return clamp_blocks(it.n, 8 * 152); },
+                      [st](const FlatBatch<CgPItem>& B, int ctas) {
+                        pdl_launch(k_cg_p_batch, ctas, 256, 0, st, B);
+                      });
+}
+
+cudaError_t launch_loop_cond_batch(cudaStream_t st, cudaGraphConditionalHandle h,
+                                   CgScalars* const* scs, int n) {
+  pdl_launch(k_loop_cond_batch, 1, 256, 0, st, h, scs, n);
   return cudaGetLastError();
 }
 

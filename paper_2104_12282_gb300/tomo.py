@@ -90,6 +90,8 @@ def _load():
         "tomo_batch_create": (st, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
         "tomo_batch_append": (st, [P, G]),
         "tomo_batch_size": (st, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "tomo_batch_set_lockstep": (st, [P, ctypes.c_int32]),
+        "tomo_batch_lockstep_runs": (st, [P, ctypes.POINTER(ctypes.c_int64)]),
         "tomo_batch_gradient": (st, [P, P, ctypes.POINTER(ctypes.c_double), P, P,
                                      ctypes.POINTER(SolveInfo)]),
         "tomo_batch_destroy": (st, [P]),
@@ -162,6 +164,7 @@ def exported_symbols():
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
             "tomo_server_last_error", "tomo_grid_device_bytes", "tomo_estimate_device_bytes",
             "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
+            "tomo_batch_set_lockstep", "tomo_batch_lockstep_runs",
             "tomo_batch_gradient", "tomo_batch_destroy", "tomo_batch_last_error",
             "tomo_filter", "tomo_filter_d", "tomo_coarse_grain", "tomo_coarse_grain_d",
             "tomo_adjoint_gradient", "tomo_adjoint_gradient_d",
@@ -445,16 +448,26 @@ class Grid:
 
 
 class Batch:
-    """A set of FP32 grids evaluated concurrently (``tomo_batch_*``): ``workers`` host
-    threads, one CUDA stream each.  The batch does not own its grids."""
+    """A set of FP32 grids evaluated together (``tomo_batch_*``): ``workers`` host threads,
+    one CUDA stream each, for the per-grid steps; with ``lockstep`` (the default) one CG
+    loop for all grids, each phase one launch for every grid.  The batch does not own its
+    grids."""
 
-    def __init__(self, workers=8):
+    def __init__(self, workers=8, lockstep=True):
         h = ctypes.c_void_p()
         st = lib().tomo_batch_create(int(workers), ctypes.byref(h))
         if st != 0:
             raise TomoError(st, lib().tomo_batch_last_error(None).decode())
         self._h = h
         self.grids = []
+        lib().tomo_batch_set_lockstep(self._h, int(bool(lockstep)))
+
+    @property
+    def lockstep_runs(self):
+        """Number of gradient calls that ran in lockstep."""
+        n = ctypes.c_int64()
+        lib().tomo_batch_lockstep_runs(self._h, ctypes.byref(n))
+        return n.value
 
     def append(self, grid):
         st = lib().tomo_batch_append(self._h, grid._h)
