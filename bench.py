@@ -319,7 +319,7 @@ def extras(args, dev, stream):
         zs = [torch.tensor(P.random_field(q.dims, args.seed + i, 0.05, 1.0), dtype=torch.float32,
                            device=dev) for i, q in enumerate(ps)]
         dcs = [torch.empty_like(t) for t in zs]
-        with tomo.Batch(workers=16) as b:
+        with tomo.Batch(workers=8) as b:
             for gg in grids:
                 b.append(gg)
             b.gradient(zs, dcs)
@@ -338,7 +338,7 @@ def extras(args, dev, stream):
         seq_s = time.perf_counter() - t0
         out["batch_64_uneven"] = {
             "grad_evals_per_s": 64 / batch_s, "sequential_grad_evals_per_s": 64 / seq_s,
-            "workers": 16, "mode": mode, "elements": sum(q.n_el for q in ps),
+            "workers": 8, "mode": mode, "elements": sum(q.n_el for q in ps),
             "cg_iters_mean": statistics.mean(i.iters for i in infos)}
     finally:
         for gg in grids:

@@ -680,7 +680,7 @@ tomo_status volume_gradient(tomo_grid* G, T* out) {
   const int ne = G->g.nel;
   if (!G->dvdz_ready) {
     std::vector<T> v(ne, (T)(G->d.h * G->d.h * G->d.h));
-    CK(cudaMemcpy(G->dvdz, v.data(), sizeof(T) * ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(G->dvdz, v.data(), sizeof(T) * ne, cudaMemcpyHostToDevice, G->stream));
     G->dvdz_ready = true;  // G->dvdz holds the constant element volumes
   }
   CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
@@ -959,8 +959,11 @@ tomo_status gradient_begin(tomo_grid* G, const T* z, T* dcdz, T* dvdz, GradIO* i
 }
 
 // S6-S7 of a gradient after the solve: compliance, dc/drho, dc/dz = P^T dc/drho, dV/dz.
+// defer_scalar: a host `compliance` is left in G->h_scal (copied asynchronously; the caller
+// synchronises the stream and reads it) instead of synchronising here.
 template <typename T>
-tomo_status gradient_end(tomo_grid* G, const GradIO& io, double* compliance, T* dcdz, T* dvdz) {
+tomo_status gradient_end(tomo_grid* G, const GradIO& io, double* compliance, T* dcdz, T* dvdz,
+                         bool defer_scalar = false) {
   const size_t be = sizeof(T) * (size_t)G->g.nel;
   T* rho = (T*)G->rho;
   void* ddc = io.ddc;
@@ -980,7 +983,10 @@ tomo_status gradient_end(tomo_grid* G, const GradIO& io, double* compliance, T* 
   TRY(pcollect(G, 0, 5));
   TRY(copy_back(G, dcdz, ddc, be, io.h2));
   if (dvdz) TRY(copy_back(G, dvdz, ddv, be, io.h3));
-  TRY(write_scalar(G, compliance, G->dscal));
+  if (defer_scalar && compliance && !is_device_ptr(compliance))
+    CK(cudaMemcpyAsync(G->h_scal, G->dscal, sizeof(double), cudaMemcpyDeviceToHost, G->stream));
+  else
+    TRY(write_scalar(G, compliance, G->dscal));
   if (io.h1 || io.h2 || io.h3) TRY(sync(G));
   return TOMO_OK;
 }
@@ -1264,7 +1270,7 @@ tomo_status create_impl(tomo_grid* G) {
     const size_t lnv = sizeof(T) * 3 * (size_t)Lv.g.nn;
     TRY(dalloc(G, &Lv.s, sizeof(T) * (size_t)Lv.g.nel));
     TRY(dalloc(G, (void**)&Lv.mask, Lv.g.nn));
-    CK(cudaMemcpy(Lv.mask, Lv.hmask.data(), Lv.g.nn, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(Lv.mask, Lv.hmask.data(), Lv.g.nn, cudaMemcpyHostToDevice, G->stream));
     if (l > 0) TRY(dalloc(G, &Lv.b, lnv));
     TRY(dalloc(G, &Lv.x, lnv));
     TRY(dalloc(G, &Lv.xp, lnv));
@@ -1272,7 +1278,8 @@ tomo_status create_impl(tomo_grid* G) {
     if (sizeof(T) == 4) {
       const std::vector<uint8_t> fl = march2_tile_flags(Lv.g, Lv.hmask);
       TRY(dalloc(G, (void**)&Lv.tile_fixed, fl.size()));
-      CK(cudaMemcpy(Lv.tile_fixed, fl.data(), fl.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpyAsync(Lv.tile_fixed, fl.data(), fl.size(), cudaMemcpyHostToDevice,
+                         G->stream));
     }
   }
   if (G->coarse_n > 0) {
@@ -1301,8 +1308,9 @@ tomo_status create_impl(tomo_grid* G) {
     G->ff = 0.0;
     for (double v : fm) G->ff += v * v;
     std::vector<T> ft(fm.begin(), fm.end());
-    CK(cudaMemcpy(G->f_T, ft.data(), nv, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(G->f64, fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(G->f_T, ft.data(), nv, cudaMemcpyHostToDevice, G->stream));
+    CK(cudaMemcpyAsync(G->f64, fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice,
+                       G->stream));
   }
   G->rhs_T = G->f_T;
   G->rhs64 = G->f64;
@@ -1312,9 +1320,9 @@ tomo_status create_impl(tomo_grid* G) {
   G->partials_n = std::max(1 << 16, oc_partials_needed(g.nel));
   TRY(dalloc(G, (void**)&G->partials, sizeof(double) * (size_t)G->partials_n));
   TRY(dalloc(G, (void**)&G->counter, sizeof(unsigned) * 4));
-  CK(cudaMemset(G->counter, 0, sizeof(unsigned) * 4));
+  CK(cudaMemsetAsync(G->counter, 0, sizeof(unsigned) * 4, G->stream));
   TRY(dalloc(G, (void**)&G->sc, sizeof(CgScalars)));
-  CK(cudaMemset(G->sc, 0, sizeof(CgScalars)));
+  CK(cudaMemsetAsync(G->sc, 0, sizeof(CgScalars), G->stream));
   TRY(dalloc(G, (void**)&G->dscal, sizeof(double) * 8));
   CK(cudaMallocHost((void**)&G->h_sc, sizeof(CgScalars)));
   CK(cudaMallocHost((void**)&G->h_scal, sizeof(double) * 8));
@@ -1334,10 +1342,12 @@ tomo_status create_impl(tomo_grid* G) {
     }
     TRY(dalloc(G, (void**)&G->d_taps, sizeof(int4) * std::max(1, G->ntaps)));
     TRY(dalloc(G, &G->d_tapw, sizeof(T) * std::max(1, G->ntaps)));
-    CK(cudaMemcpy(G->d_taps, t4.data(), sizeof(int4) * G->ntaps, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(G->d_tapw, tw.data(), sizeof(T) * G->ntaps, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(G->d_taps, t4.data(), sizeof(int4) * G->ntaps, cudaMemcpyHostToDevice,
+                       G->stream));
+    CK(cudaMemcpyAsync(G->d_tapw, tw.data(), sizeof(T) * G->ntaps, cudaMemcpyHostToDevice,
+                       G->stream));
     std::vector<T> ones(g.nel, T(1));
-    CK(cudaMemcpy(G->dcp, ones.data(), ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(G->dcp, ones.data(), ne, cudaMemcpyHostToDevice, G->stream));
     CK(launch_filter<T>(G->stream, g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
                         G->filter_radius,
                         (const T*)G->dcp, nullptr, (T*)G->Hs, 2, 0, T(0), T(0), T(0), T(0),
@@ -1664,8 +1674,9 @@ tomo_status tomo_profile_read(tomo_grid* G, int64_t* launches, double* total_ms,
 // blocks of its own single-grid launches; only the z-chunks of the products are chosen for
 // the batch (one wave for all grids together), which changes the order in which the fused
 // dots (p.q, r.z) add their block partials, so a grid's result agrees with its result alone
-// to rounding (and is reproducible for the same batch).  Grids that cannot share a loop (FP64, Jacobi preconditioner, profiling,
-// different smoother settings or Poisson ratios) run one per worker stream instead.
+// to rounding (and is reproducible for the same batch).  Grids that cannot share a loop
+// (FP64, Jacobi preconditioner, profiling, different smoother settings or Poisson ratios)
+// run one per worker stream instead, bitwise as alone.
 // ---------------------------------------------------------------------------------------
 struct tomo_batch {
   std::vector<tomo_grid*> grids;
@@ -1998,7 +2009,8 @@ tomo_status batch_build_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs) {
   }
   std::vector<CgScalars*> h(n);
   for (int q = 0; q < n; ++q) h[q] = Gs[q]->sc;
-  BK(cudaMemcpy(B->d_scs, h.data(), sizeof(CgScalars*) * (size_t)n, cudaMemcpyHostToDevice));
+  BK(cudaMemcpyAsync(B->d_scs, h.data(), sizeof(CgScalars*) * (size_t)n, cudaMemcpyHostToDevice,
+                     B->bst));
   if (!B->cap) BK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
   cudaGraph_t graph;
   BK(cudaGraphCreate(&graph, 0));
@@ -2156,12 +2168,19 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
       }
       if (!trivial[i]) st[i] = pcg_result(G, info ? info + i : nullptr);
       if (st[i] == TOMO_OK)
-        st[i] = gradient_end<float>(G, io[i], compliance + i, dcdz[i], dvdz ? dvdz[i] : nullptr);
-      if (st[i] == TOMO_OK && cudaStreamSynchronize(G->stream) != cudaSuccess) {
-        cudaGetLastError();
-        st[i] = TOMO_ECUDA;
-      }
+        st[i] = gradient_end<float>(G, io[i], compliance + i, dcdz[i],
+                                    dvdz ? dvdz[i] : nullptr, true);
     });
+    // one synchronisation per worker stream, then the compliances
+    for (int w = 0; w < W; ++w)
+      if (cudaStreamSynchronize(B->streams[w]) != cudaSuccess) {
+        cudaGetLastError();
+        for (int i = 0; i < n; ++i)
+          if (st[i] == TOMO_OK) st[i] = fail(B->grids[i], TOMO_ECUDA, "batch stream failed");
+        break;
+      }
+    for (int i = 0; i < n; ++i)
+      if (st[i] == TOMO_OK && !is_device_ptr(compliance + i)) compliance[i] = *B->grids[i]->h_scal;
   }
   // the worker streams must not run ahead of anything still queued on the batch stream
   cudaStreamSynchronize(B->bst);
