@@ -288,12 +288,18 @@ def extras(args, dev, stream):
         g.set_warm_start(False)
         g.gradient(z, dc, dv)
         ms, (c, info) = timed(lambda: g.gradient(z, dc, dv), 3)
+        best, _ = g.autotune(z)    # smoother autotuner on the evolved design
+        g.gradient(z, dc, dv)
+        ms_t, (c_t, info_t) = timed(lambda: g.gradient(z, dc, dv), 3)
+        g.set_smoother(2, 2)
         out["evolved_field"] = {
             "recipe": "50 OC iterations from the uniform start (volfrac 0.12), warm-started "
                       "solves; then cold-start gradients on that design",
             "cold_ms_per_grad": ms, "cold_cg_iters": info.iters,
             "oc_loop_s_50_iters": loop_s, "warm_cg_iters_last": warm_its[-1],
-            "warm_cg_iters_mean": statistics.mean(warm_its)}
+            "warm_cg_iters_mean": statistics.mean(warm_its),
+            "autotuned": {"fine_degree": best[0], "coarse_degree": best[1],
+                          "cold_ms_per_grad": ms_t, "cold_cg_iters": info_t.iters}}
         # two-scale step of Algorithm 1 at N_B = 4 on the bumpy field
         nb = 4
         q = P.coarse_problem(p, nb)

@@ -228,6 +228,42 @@ tomo_status tomo_adjoint_gradient_d(tomo_grid* grid, const double* z, const doub
  * default) restores the zero start. */
 tomo_status tomo_set_warm_start(tomo_grid* grid, int32_t on);
 
+/* Smoother of the multigrid preconditioner (Section III-D names multigrid as the
+ * alternative to Jacobi-PCG; the smoother is this library's choice): Chebyshev-Jacobi of
+ * degree fine_degree on the finest level and coarse_degree on the coarser ones (1..16), on
+ * [lam / ratio, lam] of D^-1 K with lam the element bound (ratio > 1).  Any setting gives
+ * the same solve to the same tolerance; the number of CG iterations and the time per
+ * iteration change.  tomo_set_smoother waits for the grid's stream and drops the captured
+ * CG loops (rebuilt at the next solve); EINVAL for degrees or ratio out of range.
+ * tomo_get_smoother: any pointer may be NULL. */
+tomo_status tomo_set_smoother(tomo_grid* grid, int32_t fine_degree, int32_t coarse_degree,
+                              double ratio);
+tomo_status tomo_get_smoother(const tomo_grid* grid, int32_t* fine_degree,
+                              int32_t* coarse_degree, double* ratio);
+
+/* Smoother autotuner.  On the design z (N_el, host or device; filtered and turned into the
+ * material as tomo_gradient does) it times the state solve from a zero start for each
+ * candidate (pairs[2k], pairs[2k+1]) = (fine_degree, coarse_degree), k < n (1..64), at the
+ * grid's current ratio: one untimed solve, then reps (1..16) solves timed with CUDA events
+ * on the grid's stream, the median kept.  pairs == NULL: the built-in list (2,2) (2,3) (2,4)
+ * (1,3) (1,4) (1,6) (n ignored).  The fastest candidate that converges becomes the grid's
+ * smoother; results[k] (may be NULL) holds each candidate's median milliseconds (-1 when it
+ * failed), iterations and status; *best (may be NULL) its index.  If no candidate converges
+ * the grid keeps its previous smoother and ENOCONV is returned.  The grid's displacement is
+ * left as the last trial's. */
+typedef struct {
+  int32_t fine_degree, coarse_degree;
+  int32_t iters;
+  int32_t status;
+  double ms;
+} tomo_tune_result;
+tomo_status tomo_autotune_smoother(tomo_grid* grid, const float* z, const int32_t* pairs,
+                                   int32_t n, int32_t reps, tomo_tune_result* results,
+                                   int32_t* best);
+tomo_status tomo_autotune_smoother_d(tomo_grid* grid, const double* z, const int32_t* pairs,
+                                     int32_t n, int32_t reps, tomo_tune_result* results,
+                                     int32_t* best);
+
 /* Copy the displacement of the last tomo_gradient / tomo_solve on this grid to u
  * (3*N_n, host or device). */
 tomo_status tomo_get_displacement(tomo_grid* grid, float* u);

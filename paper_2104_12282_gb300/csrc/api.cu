@@ -1358,6 +1358,123 @@ tomo_status create_impl(tomo_grid* G) {
   return TOMO_OK;
 }
 
+// Chebyshev degrees (finest level, coarser levels) and interval ratio of a grid; the
+// captured CG loops, which bake them in, are dropped and rebuilt at the next solve.
+tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio) {
+  if (fine < 1 || fine > 16 || coarse < 1 || coarse > 16 || !(ratio > 1.0) || !std::isfinite(ratio))
+    return fail(G, TOMO_EINVAL, "smoother: degrees in 1..16 and ratio > 1 (got %d, %d, %g)",
+                fine, coarse, ratio);
+  if (fine == G->d.smoother_degree && coarse == G->d.coarse_degree && ratio == G->cheb_ratio)
+    return TOMO_OK;
+  TRY(sync(G));  // no captured loop of this grid is still running
+  G->d.smoother_degree = fine;
+  G->d.coarse_degree = coarse;
+  G->d.cheb_ratio = ratio;
+  G->cheb_ratio = ratio;
+  if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
+  if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
+  G->loop_exec = nullptr;
+  G->loop_exec_adj = nullptr;
+  G->gen += 1;
+  return TOMO_OK;
+}
+
+// The smoother autotuner: the state solve K(P z) u = f (cold start) timed with CUDA events
+// on the grid's stream for each candidate (fine, coarse) degree pair, reps times after one
+// untimed solve (which also captures that candidate's loop); the fastest candidate that
+// converges is kept.
+template <typename T>
+tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, int reps,
+                        tomo_tune_result* res, int32_t* best) {
+  // (fine, coarse) degrees: (2, 2) is fastest on random fields, (1, 4) on OC-evolved
+  // designs (near 0/1 densities), measured on the 192x96x76 MBB-type block
+  static const int32_t kDefault[] = {2, 2, 2, 3, 2, 4, 1, 3, 1, 4, 1, 6};
+  if (!z) return fail(G, TOMO_EINVAL, "null array");
+  if (!pairs) {
+    pairs = kDefault;
+    n = (int)(sizeof(kDefault) / sizeof(kDefault[0]) / 2);
+  }
+  if (n < 1 || n > 64 || reps < 1 || reps > 16)
+    return fail(G, TOMO_EINVAL, "autotune: 1..64 candidates and 1..16 repetitions");
+  if (G->d.precond != TOMO_PRECOND_MG)
+    return fail(G, TOMO_EINVAL, "autotune: the grid has no multigrid smoother");
+  for (int k = 0; k < n; ++k)
+    if (pairs[2 * k] < 1 || pairs[2 * k] > 16 || pairs[2 * k + 1] < 1 || pairs[2 * k + 1] > 16)
+      return fail(G, TOMO_EINVAL, "autotune: candidate %d has a degree outside 1..16", k);
+  const int fine0 = G->d.smoother_degree, coarse0 = G->d.coarse_degree;
+  const double ratio = G->cheb_ratio;
+  const size_t be = sizeof(T) * (size_t)G->g.nel;
+  const void* dz;
+  bool h1;
+  TRY(stage_in(G, z, be, 0, &dz, &h1));
+  const tomo_grid_desc& d = G->d;
+  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                      G->filter_radius, (const T*)dz, (const T*)G->Hs, (T*)G->rho, 0, 1,
+                      (T)d.E0, (T)d.Emin, (T)d.penal, (T)d.h, (T*)G->L[0].s));
+  G->launches += 1;
+  TRY(setup_levels<T>(G));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    CK(cudaGetLastError());
+  }
+  int bi = -1;
+  double bms = 0.0;
+  tomo_status st = TOMO_OK;
+  for (int k = 0; k < n && st == TOMO_OK; ++k) {
+    st = set_smoother(G, pairs[2 * k], pairs[2 * k + 1], ratio);
+    if (st != TOMO_OK) break;
+    tomo_solve_info info{};
+    tomo_status sk = pcg<T>(G, false, &info);  // untimed: captures this candidate's loop
+    std::vector<double> ms;
+    for (int r = 0; r < reps && sk == TOMO_OK; ++r) {
+      float t = 0.0f;
+      if (cudaEventRecord(e0, G->stream) != cudaSuccess) sk = TOMO_ECUDA;
+      if (sk == TOMO_OK) sk = pcg<T>(G, false, &info);
+      if (sk == TOMO_OK && (cudaEventRecord(e1, G->stream) != cudaSuccess ||
+                            cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        sk = TOMO_ECUDA;
+      ms.push_back(t);
+    }
+    if (sk == TOMO_ECUDA) {
+      cudaGetLastError();
+      st = fail(G, TOMO_ECUDA, "autotune: CUDA error while timing candidate %d", k);
+      break;
+    }
+    double med = 0.0;
+    if (sk == TOMO_OK) {
+      std::sort(ms.begin(), ms.end());
+      med = ms[ms.size() / 2];
+      if (bi < 0 || med < bms) {
+        bi = k;
+        bms = med;
+      }
+    }
+    if (res) {
+      res[k].fine_degree = pairs[2 * k];
+      res[k].coarse_degree = pairs[2 * k + 1];
+      res[k].iters = info.iters;
+      res[k].status = sk;
+      res[k].ms = sk == TOMO_OK ? med : -1.0;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == TOMO_OK && bi < 0)
+    st = fail(G, TOMO_ENOCONV, "autotune: no candidate converged");
+  if (st != TOMO_OK) {
+    std::string why = G->err;
+    set_smoother(G, fine0, coarse0, ratio);
+    G->err = why;
+    return st;
+  }
+  TRY(set_smoother(G, pairs[2 * bi], pairs[2 * bi + 1], ratio));
+  if (best) *best = bi;
+  return TOMO_OK;
+}
+
 }  // namespace
 
 // =======================================================================================
@@ -1478,6 +1595,40 @@ tomo_status tomo_set_warm_start(tomo_grid* G, int32_t on) {
   if (!G) return TOMO_EINVAL;
   G->warm_gradient = on != 0;
   return TOMO_OK;
+}
+
+tomo_status tomo_set_smoother(tomo_grid* G, int32_t fine_degree, int32_t coarse_degree,
+                              double ratio) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  return set_smoother(G, fine_degree, coarse_degree, ratio);
+}
+
+tomo_status tomo_get_smoother(const tomo_grid* G, int32_t* fine_degree, int32_t* coarse_degree,
+                              double* ratio) {
+  if (!G) return TOMO_EINVAL;
+  if (fine_degree) *fine_degree = G->d.smoother_degree;
+  if (coarse_degree) *coarse_degree = G->d.coarse_degree;
+  if (ratio) *ratio = G->cheb_ratio;
+  return TOMO_OK;
+}
+
+tomo_status tomo_autotune_smoother(tomo_grid* G, const float* z, const int32_t* pairs,
+                                   int32_t n, int32_t reps, tomo_tune_result* results,
+                                   int32_t* best) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  TRY(check_prec(G, false));
+  return do_autotune<float>(G, z, pairs, n, reps, results, best);
+}
+
+tomo_status tomo_autotune_smoother_d(tomo_grid* G, const double* z, const int32_t* pairs,
+                                     int32_t n, int32_t reps, tomo_tune_result* results,
+                                     int32_t* best) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  TRY(check_prec(G, true));
+  return do_autotune<double>(G, z, pairs, n, reps, results, best);
 }
 
 tomo_status tomo_set_stream(tomo_grid* G, void* stream) {
@@ -1684,8 +1835,9 @@ struct tomo_batch {
   std::string err;
   bool lockstep = true;
   int64_t lockstep_runs = 0;
-  // captured lockstep loop of the active grid set `plan`
+  // captured lockstep loop of the active grid set `plan` (with the grids' setting generations)
   std::vector<tomo_grid*> plan;
+  std::vector<int64_t> plan_gen;
   cudaStream_t bst = nullptr;  // stream of the batched launches
   cudaStream_t cap = nullptr;  // capture stream
   cudaGraphExec_t loop = nullptr;
@@ -2057,6 +2209,8 @@ tomo_status batch_build_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs) {
   cudaGraphDestroy(graph);
   BK(e);
   B->plan = Gs;
+  B->plan_gen.clear();
+  for (auto* G : Gs) B->plan_gen.push_back(G->gen);
   B->iter_launches = launches;
   return TOMO_OK;
 }
@@ -2137,7 +2291,9 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
     std::vector<float*> zz;
     bs = batch_vcycle(B, B->bst, act, r, true, &zz, &launches);
     if (bs == TOMO_OK) bs = batch_cg_p(B, B->bst, act, zz, &launches);
-    if (bs == TOMO_OK && (!B->loop || B->plan != act)) bs = batch_build_loop(B, act);
+    bool stale = !B->loop || B->plan != act;
+    for (size_t q = 0; !stale && q < act.size(); ++q) stale = B->plan_gen[q] != act[q]->gen;
+    if (bs == TOMO_OK && stale) bs = batch_build_loop(B, act);
     if (bs == TOMO_OK) {
       cudaError_t e = cudaGraphLaunch(B->loop, B->bst);
       for (size_t q = 0; q < act.size() && e == cudaSuccess; ++q)

@@ -352,6 +352,7 @@ struct tomo_grid {
   void* adj_hi = nullptr;      // adjoint state lambda (pair on FP32 grids)
   void* adj_lo = nullptr;
   bool use_graph = true;
+  int64_t gen = 0;  // bumped when settings baked into captured loops change (smoother)
   // phase timing (events at phase boundaries; the CG loop stays a graph)
   bool phase_prof = false;
   cudaEvent_t phase_ev[8] = {};

@@ -34,10 +34,14 @@ def paper_cantilever(mesh: int, volfrac: float = 0.12, radius: float = 0.08) -> 
 
 
 def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo.FP32,
-        rtol: float = 1e-6, warm: bool = True, maxit: int = 5000, z0=None, callback=None):
+        rtol: float = 1e-6, warm: bool = True, maxit: int = 5000, z0=None, callback=None,
+        autotune_every: int = 0):
     """Exact-gradient OC loop on the GPU.  Returns (z, history); history holds one dict per
     iteration: compliance, design change, CG iterations, wall time of the gradient and of
-    the coarse step (ms)."""
+    the coarse step (ms), and the smoother (fine, coarse degrees) the gradient used.
+    autotune_every > 0: the smoother autotuner runs on the current design at iterations
+    autotune_every, 2 autotune_every, ... (the design drifts from the smooth start towards
+    near 0/1 densities, which favour other smoother degrees); its time is not in `ms`."""
     import torch
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -65,6 +69,9 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
                     g.coarse_grain(z, block, zc)
                     ci = gc.solve(zc, uc)
                     coarse = ci.iters
+                tuned = None
+                if autotune_every > 0 and k > 0 and k % autotune_every == 0:
+                    tuned, _ = g.autotune(z)
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
                 c, info = g.gradient(z, dc, dv)
@@ -73,7 +80,8 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
                 t2 = time.perf_counter()
                 rec = dict(it=k, c=c, change=change, cg_iters=info.iters,
                            ms=(t2 - t1) * 1e3, coarse_ms=(t1 - t0) * 1e3,
-                           coarse_cg_iters=coarse)
+                           coarse_cg_iters=coarse, smoother=list(g.smoother()[:2]),
+                           tuned=tuned is not None)
                 hist.append(rec)
                 if callback:
                     callback(rec)
@@ -92,6 +100,8 @@ def main(argv=None):
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--cold", action="store_true", help="start every solve from zero")
     ap.add_argument("--quiet", action="store_true")
+    ap.add_argument("--autotune-every", type=int, default=0,
+                    help="run the smoother autotuner every N iterations (0: off)")
     a = ap.parse_args(argv)
     p = paper_cantilever(a.mesh)
     prec = tomo.FP64 if a.fp64 else tomo.FP32
@@ -101,14 +111,16 @@ def main(argv=None):
             print(json.dumps(rec), flush=True)
 
     t = time.perf_counter()
-    _, hist = run(p, a.iters, block=a.block, precision=prec, warm=not a.cold, callback=show)
+    _, hist = run(p, a.iters, block=a.block, precision=prec, warm=not a.cold, callback=show,
+                  autotune_every=a.autotune_every)
     wall = time.perf_counter() - t
     d = p.dims
     print(json.dumps({"mesh": a.mesh, "dims": [d.nx, d.ny, d.nz], "h": p.h, "rmin": p.rmin,
                       "block": a.block, "iters": a.iters, "final_c": hist[-1]["c"],
                       "wall_s": wall, "cg_iters_total": sum(r["cg_iters"] for r in hist),
                       "precision": "fp64" if a.fp64 else "fp32-mixed",
-                      "warm_start": not a.cold}), flush=True)
+                      "warm_start": not a.cold, "autotune_every": a.autotune_every,
+                      "gradient_s": sum(r["ms"] for r in hist) / 1e3}), flush=True)
 
 
 if __name__ == "__main__":

@@ -43,6 +43,11 @@ class GridDesc(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("fine_degree", ctypes.c_int32), ("coarse_degree", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
                 ("status", ctypes.c_int32), ("mg_levels", ctypes.c_int32)]
@@ -76,6 +81,14 @@ def _load():
         "tomo_destroy_grid": (st, [G]),
         "tomo_set_stream": (st, [G, P]),
         "tomo_set_warm_start": (st, [G, ctypes.c_int32]),
+        "tomo_set_smoother": (st, [G, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
+        "tomo_get_smoother": (st, [G, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_double)]),
+        "tomo_autotune_smoother": (st, [G, P, P, ctypes.c_int32, ctypes.c_int32, P,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+        "tomo_autotune_smoother_d": (st, [G, P, P, ctypes.c_int32, ctypes.c_int32, P,
+                                          ctypes.POINTER(ctypes.c_int32)]),
         "tomo_server_create": (st, [ctypes.c_int32, ctypes.c_uint64,
                                     ctypes.POINTER(ctypes.c_void_p)]),
         "tomo_server_submit": (st, [P, ctypes.POINTER(GridDesc), ctypes.c_int64, P, P, P,
@@ -160,7 +173,9 @@ def lib():
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["tomo_default_desc", "tomo_create_grid", "tomo_destroy_grid", "tomo_set_stream",
-            "tomo_set_warm_start", "tomo_server_create", "tomo_server_submit",
+            "tomo_set_warm_start", "tomo_set_smoother", "tomo_get_smoother",
+            "tomo_autotune_smoother", "tomo_autotune_smoother_d",
+            "tomo_server_create", "tomo_server_submit",
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
             "tomo_server_last_error", "tomo_grid_device_bytes", "tomo_estimate_device_bytes",
             "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
@@ -307,6 +322,44 @@ class Grid:
         st = lib().tomo_set_warm_start(self._h, int(bool(on)))
         if st != 0:
             raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def set_smoother(self, fine_degree, coarse_degree, ratio=None):
+        """Chebyshev degrees of the finest and the coarser levels (tomo_set_smoother); the
+        interval ratio stays unless given."""
+        if ratio is None:
+            ratio = self.smoother()[2]
+        st = lib().tomo_set_smoother(self._h, int(fine_degree), int(coarse_degree),
+                                     float(ratio))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def smoother(self):
+        """(fine_degree, coarse_degree, ratio) of the multigrid smoother."""
+        f, c, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        lib().tomo_get_smoother(self._h, ctypes.byref(f), ctypes.byref(c), ctypes.byref(r))
+        return f.value, c.value, r.value
+
+    def autotune(self, z, candidates=None, reps=2):
+        """Time the state solve on design z for each (fine, coarse) degree pair (the built-in
+        list when None), keep the fastest (tomo_autotune_smoother); returns (best pair,
+        list of dicts with fine, coarse, ms, iters, status per candidate)."""
+        if candidates is None:
+            pairs, n = None, 6
+        else:
+            flat = [int(v) for pq in candidates for v in pq]
+            pairs = (ctypes.c_int32 * len(flat))(*flat)
+            n = len(candidates)
+        res = (TuneResult * n)()
+        best = ctypes.c_int32(-1)
+        st = getattr(lib(), "tomo_autotune_smoother" + self._sfx)(
+            self._h, self._e(z, "z"), ctypes.cast(pairs, ctypes.c_void_p) if pairs else None,
+            n, int(reps), ctypes.cast(res, ctypes.c_void_p), ctypes.byref(best))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+        rows = [dict(fine=r.fine_degree, coarse=r.coarse_degree, ms=r.ms, iters=r.iters,
+                     status=r.status) for r in res]
+        b = rows[best.value]
+        return (b["fine"], b["coarse"]), rows
 
     def filter(self, x, out, transpose=False):
         self._call("tomo_filter", self._e(x, "in"), self._e(out, "out"), int(bool(transpose)))

@@ -1,0 +1,131 @@
+"""Smoother settings and the smoother autotuner (tomo_set_smoother, tomo_autotune_smoother):
+every setting solves the same system to the same tolerance (checked against the oracle's
+direct solve); the autotuner keeps the fastest converging candidate it timed; a lockstep
+batch follows a smoother change of its grids."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import topopt  # noqa: E402
+from paper_2104_12282_gb300 import problems as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2104_12282_gb300 import tomo  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _field(p, seed):
+    z = P.random_field(p.dims, seed, 0.05, 1.0).astype(np.float32)
+    return z, torch.tensor(z, device=DEV)
+
+
+@pytest.mark.parametrize("degs", [(2, 2), (1, 4), (3, 6), (1, 1)])
+def test_every_smoother_solves_to_tolerance(degs):
+    p = P.cantilever(24, 12, 12)
+    z, zt = _field(p, 31)
+    ref = topopt.Model(p).gradient(z.astype(np.float64), "direct")
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        g.set_smoother(*degs)
+        assert g.smoother()[:2] == degs
+        dc = torch.empty_like(zt)
+        c, info = g.gradient(zt, dc)
+    assert info.status == 0 and info.rel_res <= 1e-6
+    assert abs(c / ref["c"] - 1.0) <= 1e-5
+    d = dc.cpu().numpy().astype(np.float64)
+    assert np.abs(d - ref["dcdz"]).max() <= 1e-4 * np.abs(ref["dcdz"]).max()
+
+
+def test_smoother_settings_change_iterations():
+    p = P.mbb_block(48, 24, 19, volfrac=0.12, rmin=2.5)
+    _, zt = _field(p, 32)
+    its = {}
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        dc = torch.empty_like(zt)
+        for degs in ((1, 1), (2, 2), (2, 6)):
+            g.set_smoother(*degs)
+            _, info = g.gradient(zt, dc)
+            its[degs] = info.iters
+    assert its[(1, 1)] > its[(2, 2)] >= its[(2, 6)]
+
+
+def test_bad_smoother_values_are_rejected():
+    p = P.cantilever(8, 4, 4)
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        before = g.smoother()
+        for args in ((0, 2, 20.0), (2, 17, 20.0), (2, 2, 1.0), (2, 2, float("nan"))):
+            with pytest.raises(tomo.TomoError) as e:
+                g.set_smoother(*args)
+            assert e.value.status == 1
+        assert g.smoother() == before
+
+
+def test_autotune_keeps_the_fastest_converging_candidate():
+    p = P.mbb_block(48, 24, 19, volfrac=0.12, rmin=2.5)
+    z, zt = _field(p, 33)
+    cands = [(2, 2), (1, 4), (2, 4), (1, 1)]
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        best, rows = g.autotune(zt, cands, reps=2)
+        assert [(r["fine"], r["coarse"]) for r in rows] == cands
+        ok = [r for r in rows if r["status"] == 0]
+        assert ok and all(r["ms"] > 0 for r in ok)
+        fastest = min(ok, key=lambda r: r["ms"])
+        assert best == (fastest["fine"], fastest["coarse"])
+        assert g.smoother()[:2] == best
+        dc = torch.empty_like(zt)
+        c, info = g.gradient(zt, dc)
+        assert info.iters == fastest["iters"]
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g0:
+        dc0 = torch.empty_like(zt)
+        c0, _ = g0.gradient(zt, dc0)
+    assert abs(c / c0 - 1.0) <= 1e-5
+    # the built-in list
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        best, rows = g.autotune(zt)
+        assert len(rows) == 6 and best in [(r["fine"], r["coarse"]) for r in rows]
+
+
+def test_autotune_without_a_converging_candidate_keeps_the_smoother():
+    p = P.cantilever(24, 12, 12)
+    _, zt = _field(p, 34)
+    with tomo.Grid.from_problem(p, precision=tomo.FP32, maxit=1) as g:
+        g.set_smoother(2, 3)
+        with pytest.raises(tomo.TomoError) as e:
+            g.autotune(zt, [(1, 1), (2, 2)], reps=1)
+        assert e.value.status == 3
+        assert g.smoother()[:2] == (2, 3)
+
+
+def test_lockstep_batch_follows_a_smoother_change():
+    ps = P.uneven_cantilever_batch(21, 4)
+    zs = [torch.tensor(P.random_field(p.dims, 40 + i, 0.05, 1.0), dtype=torch.float32,
+                       device=DEV) for i, p in enumerate(ps)]
+    grids = [tomo.Grid.from_problem(p, precision=tomo.FP32) for p in ps]
+    try:
+        with tomo.Batch(workers=2) as b:
+            for g in grids:
+                b.append(g)
+            dcs = [torch.empty_like(z) for z in zs]
+            _, i0 = b.gradient(zs, dcs)
+            grids[0].set_smoother(1, 4)          # grids now differ: one per stream
+            b.gradient(zs, dcs)
+            assert b.lockstep_runs == 1
+            for g in grids[1:]:
+                g.set_smoother(1, 4)             # the same again: lockstep, new loop
+            cs, i1 = b.gradient(zs, dcs)
+            assert b.lockstep_runs == 2
+            torch.cuda.synchronize()
+        for p, z, c, dc, info in zip(ps, zs, cs, dcs, i1):
+            with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+                g.set_smoother(1, 4)
+                d0 = torch.empty_like(z)
+                c0, info0 = g.gradient(z, d0)
+            assert abs(c / c0 - 1.0) <= 1e-5 and abs(info.iters - info0.iters) <= 1
+    finally:
+        for g in grids:
+            g.close()
