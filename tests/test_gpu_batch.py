@@ -274,3 +274,29 @@ def test_batch_of_different_poisson_ratios_runs_per_stream():
     finally:
         for g in grids:
             g.close()
+
+
+def test_lockstep_with_host_arrays():
+    """Host (numpy) arrays go through the grids' staging buffers in lockstep too."""
+    ps = P.uneven_cantilever_batch(15, 3)
+    zh = [P.random_field(p.dims, 800 + i, 0.05, 1.0).astype(np.float32)
+          for i, p in enumerate(ps)]
+    grids = [tomo.Grid.from_problem(p, precision=tomo.FP32) for p in ps]
+    try:
+        with tomo.Batch(workers=2) as b:
+            for g in grids:
+                b.append(g)
+            dch = [np.zeros(p.n_el, np.float32) for p in ps]
+            dvh = [np.zeros(p.n_el, np.float32) for p in ps]
+            cs, infos = b.gradient(zh, dch, dvh)
+            assert b.lockstep_runs == 1
+            zd = [torch.tensor(z, device=DEV) for z in zh]
+            dcd = [torch.empty_like(z) for z in zd]
+            cs2, _ = b.gradient(zd, dcd)
+            torch.cuda.synchronize()
+        for c, c2, a, d in zip(cs, cs2, dch, dcd):
+            assert c == c2 and np.array_equal(a, d.cpu().numpy())
+        assert all(np.all(v > 0) for v in dvh)
+    finally:
+        for g in grids:
+            g.close()
