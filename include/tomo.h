@@ -233,8 +233,9 @@ tomo_status tomo_set_warm_start(tomo_grid* grid, int32_t on);
  * degree fine_degree on the finest level and coarse_degree on the coarser ones (1..16), on
  * [lam / ratio, lam] of D^-1 K with lam the element bound (ratio > 1).  Any setting gives
  * the same solve to the same tolerance; the number of CG iterations and the time per
- * iteration change.  tomo_set_smoother waits for the grid's stream and drops the captured
- * CG loops (rebuilt at the next solve); EINVAL for degrees or ratio out of range.
+ * iteration change.  tomo_set_smoother waits for the grid's stream and sets the captured
+ * CG loop aside (kept for up to 8 settings and reused when the setting returns; a new one
+ * is captured at the next solve); EINVAL for degrees or ratio out of range.
  * tomo_get_smoother: any pointer may be NULL. */
 tomo_status tomo_set_smoother(tomo_grid* grid, int32_t fine_degree, int32_t coarse_degree,
                               double ratio);
@@ -244,8 +245,9 @@ tomo_status tomo_get_smoother(const tomo_grid* grid, int32_t* fine_degree,
 /* Smoother autotuner.  On the design z (N_el, host or device; filtered and turned into the
  * material as tomo_gradient does) it times the state solve from a zero start for each
  * candidate (pairs[2k], pairs[2k+1]) = (fine_degree, coarse_degree), k < n (1..64), at the
- * grid's current ratio: one untimed solve, then reps (1..16) solves timed with CUDA events
- * on the grid's stream, the median kept.  pairs == NULL: the built-in list (2,2) (2,3) (2,4)
+ * grid's current ratio: one untimed solve (skipped when the grid kept that candidate's
+ * captured loop from an earlier use: a grid keeps the loops of up to 8 smoother settings),
+ * then reps (1..16) solves timed with CUDA events on the grid's stream, the median kept.  pairs == NULL: the built-in list (2,2) (2,3) (2,4)
  * (1,3) (1,4) (1,6) (n ignored).  The fastest candidate that converges becomes the grid's
  * smoother; results[k] (may be NULL) holds each candidate's median milliseconds (-1 when it
  * failed), iterations and status; *best (may be NULL) its index.  If no candidate converges

@@ -1177,6 +1177,8 @@ void free_grid(tomo_grid* G) {
   for (void* s : G->stage) F(s);
   if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
   if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
+  for (auto& e : G->loop_cache) cudaGraphExecDestroy(e.exec);
+  G->loop_cache.clear();
   F(G->adj_T);
   F(G->adj64);
   F(G->adj_hi);
@@ -1367,14 +1369,30 @@ tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio) {
   if (fine == G->d.smoother_degree && coarse == G->d.coarse_degree && ratio == G->cheb_ratio)
     return TOMO_OK;
   TRY(sync(G));  // no captured loop of this grid is still running
+  // keep the current load-slot loop for a later return to these settings (up to 8)
+  if (G->loop_exec) {
+    if (G->loop_cache.size() >= 8) {
+      cudaGraphExecDestroy(G->loop_cache.front().exec);
+      G->loop_cache.erase(G->loop_cache.begin());
+    }
+    G->loop_cache.push_back(tomo_grid::CachedLoop{G->d.smoother_degree, G->d.coarse_degree,
+                                                  G->cheb_ratio, G->loop_exec});
+  }
+  G->loop_exec = nullptr;
+  if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
+  G->loop_exec_adj = nullptr;
   G->d.smoother_degree = fine;
   G->d.coarse_degree = coarse;
   G->d.cheb_ratio = ratio;
   G->cheb_ratio = ratio;
-  if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
-  if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
-  G->loop_exec = nullptr;
-  G->loop_exec_adj = nullptr;
+  for (size_t k = 0; k < G->loop_cache.size(); ++k) {
+    const tomo_grid::CachedLoop& e = G->loop_cache[k];
+    if (e.fine == fine && e.coarse == coarse && e.ratio == ratio) {
+      G->loop_exec = e.exec;
+      G->loop_cache.erase(G->loop_cache.begin() + k);
+      break;
+    }
+  }
   G->gen += 1;
   return TOMO_OK;
 }
@@ -1426,7 +1444,9 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
     st = set_smoother(G, pairs[2 * k], pairs[2 * k + 1], ratio);
     if (st != TOMO_OK) break;
     tomo_solve_info info{};
-    tomo_status sk = pcg<T>(G, false, &info);  // untimed: captures this candidate's loop
+    // untimed solve, which captures this candidate's loop, unless the grid kept it
+    tomo_status sk = TOMO_OK;
+    if (!G->loop_exec || G->prof) sk = pcg<T>(G, false, &info);
     std::vector<double> ms;
     for (int r = 0; r < reps && sk == TOMO_OK; ++r) {
       float t = 0.0f;

@@ -353,6 +353,13 @@ struct tomo_grid {
   void* adj_lo = nullptr;
   bool use_graph = true;
   int64_t gen = 0;  // bumped when settings baked into captured loops change (smoother)
+  // captured loops (load slot) of smoother settings used before: (fine, coarse, ratio)
+  struct CachedLoop {
+    int fine, coarse;
+    double ratio;
+    cudaGraphExec_t exec;
+  };
+  std::vector<CachedLoop> loop_cache;
   // phase timing (events at phase boundaries; the CG loop stays a graph)
   bool phase_prof = false;
   cudaEvent_t phase_ev[8] = {};

@@ -35,13 +35,16 @@ def paper_cantilever(mesh: int, volfrac: float = 0.12, radius: float = 0.08) -> 
 
 def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo.FP32,
         rtol: float = 1e-6, warm: bool = True, maxit: int = 5000, z0=None, callback=None,
-        autotune_every: int = 0):
+        autotune_every: int = 0, tune: str = "online"):
     """Exact-gradient OC loop on the GPU.  Returns (z, history); history holds one dict per
     iteration: compliance, design change, CG iterations, wall time of the gradient and of
     the coarse step (ms), and the smoother (fine, coarse degrees) the gradient used.
-    autotune_every > 0: the smoother autotuner runs on the current design at iterations
-    autotune_every, 2 autotune_every, ... (the design drifts from the smooth start towards
-    near 0/1 densities, which favour other smoother degrees); its time is not in `ms`."""
+    autotune_every > 0: the smoother is re-chosen at iterations autotune_every,
+    2 autotune_every, ... (the design drifts from the smooth start towards near 0/1
+    densities, which favour other smoother degrees).  tune "offline": the library's
+    autotuner times extra solves of the current design (not counted in `ms`); "online": the
+    next gradients of the run itself try the candidates one each, then the fastest is kept
+    (no extra solves; the trial gradients are real iterations of the run)."""
     import torch
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -51,6 +54,8 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
     dc = torch.empty_like(z)
     dv = torch.empty_like(z)
     hist = []
+    cands = [(2, 2), (2, 3), (2, 4), (1, 3), (1, 4), (1, 6)]
+    trial = []      # online tuning: (candidate, ms) of the trial gradients so far
     with tomo.Grid.from_problem(problem, precision=precision, rtol=rtol, maxit=maxit) as g:
         g.set_warm_start(warm)
         gc = None
@@ -71,13 +76,24 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
                     coarse = ci.iters
                 tuned = None
                 if autotune_every > 0 and k > 0 and k % autotune_every == 0:
-                    tuned, _ = g.autotune(z)
+                    if tune == "offline":
+                        tuned, _ = g.autotune(z, reps=1)
+                    else:
+                        trial = [None] * len(cands)
+                if trial and None in trial:     # online: this gradient tries a candidate
+                    g.set_smoother(*cands[trial.index(None)])
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
                 c, info = g.gradient(z, dc, dv)
                 change = g.oc_step(z, dc, dv, problem.volfrac, problem.move, zn)
                 torch.cuda.synchronize()
                 t2 = time.perf_counter()
+                if trial and None in trial:
+                    trial[trial.index(None)] = (t2 - t1)
+                    if None not in trial:      # all tried: keep the fastest
+                        tuned = cands[int(np.argmin(trial))]
+                        g.set_smoother(*tuned)
+                        trial = []
                 rec = dict(it=k, c=c, change=change, cg_iters=info.iters,
                            ms=(t2 - t1) * 1e3, coarse_ms=(t1 - t0) * 1e3,
                            coarse_cg_iters=coarse, smoother=list(g.smoother()[:2]),
@@ -101,7 +117,10 @@ def main(argv=None):
     ap.add_argument("--cold", action="store_true", help="start every solve from zero")
     ap.add_argument("--quiet", action="store_true")
     ap.add_argument("--autotune-every", type=int, default=0,
-                    help="run the smoother autotuner every N iterations (0: off)")
+                    help="re-choose the smoother every N iterations (0: off)")
+    ap.add_argument("--tune", choices=("online", "offline"), default="online",
+                    help="online: try the candidates on the run's own gradients; offline: "
+                         "the library autotuner's extra solves")
     a = ap.parse_args(argv)
     p = paper_cantilever(a.mesh)
     prec = tomo.FP64 if a.fp64 else tomo.FP32
@@ -112,7 +131,7 @@ def main(argv=None):
 
     t = time.perf_counter()
     _, hist = run(p, a.iters, block=a.block, precision=prec, warm=not a.cold, callback=show,
-                  autotune_every=a.autotune_every)
+                  autotune_every=a.autotune_every, tune=a.tune)
     wall = time.perf_counter() - t
     d = p.dims
     print(json.dumps({"mesh": a.mesh, "dims": [d.nx, d.ny, d.nz], "h": p.h, "rmin": p.rmin,
@@ -120,6 +139,8 @@ def main(argv=None):
                       "wall_s": wall, "cg_iters_total": sum(r["cg_iters"] for r in hist),
                       "precision": "fp64" if a.fp64 else "fp32-mixed",
                       "warm_start": not a.cold, "autotune_every": a.autotune_every,
+                      "tune": a.tune if a.autotune_every else None,
+                      "smoother_final": hist[-1]["smoother"],
                       "gradient_s": sum(r["ms"] for r in hist) / 1e3}), flush=True)
 
 

@@ -2,7 +2,8 @@
 gradient requests on 2n x n x n domains of different sizes (seeded supports, loads and
 density fields), device-resident grids, admission under a device-memory budget; reports
 p50/p99 latency and throughput, next to serial FP64 GPU gradients on a sample of the same
-requests.
+requests.  --rate 0 submits every request at once (saturation: the throughput is then the
+request loop's capacity).
 
     python -m paper_2104_12282_gb300.serve --requests 1000 --rate 200 --budget-gb 150
 """
@@ -28,8 +29,11 @@ def percentile(xs, q):
 def run_stream(n_requests=1000, rate=200.0, seed=0, workers=16, budget_bytes=150 << 30,
                n_range=(12, 64), serial_sample=12):
     reqs = [P.served_request(seed, i, n_range) for i in range(n_requests)]
-    gaps = np.random.default_rng([seed, 1]).exponential(1.0 / rate, size=n_requests)
-    arrive = np.cumsum(gaps)
+    if rate > 0:
+        gaps = np.random.default_rng([seed, 1]).exponential(1.0 / rate, size=n_requests)
+        arrive = np.cumsum(gaps)
+    else:   # saturation
+        arrive = np.zeros(n_requests)
     lat, qms = [], []
     with tomo.Server(workers=workers, budget_bytes=budget_bytes) as srv:
         t0 = time.perf_counter()
@@ -60,7 +64,8 @@ def run_stream(n_requests=1000, rate=200.0, seed=0, workers=16, budget_bytes=150
             torch.cuda.synchronize()
             ser.append((time.perf_counter() - t) * 1e3)
     return {
-        "requests": n_requests, "rate_per_s": rate, "workers": workers,
+        "requests": n_requests, "rate_per_s": rate if rate > 0 else "all at once",
+        "workers": workers,
         "budget_gb": budget_bytes / 2 ** 30, "sizes": f"2n x n x n, n ~ U{{{n_range[0]}..{n_range[1]}}}",
         "throughput_per_s": n_requests / wall, "p50_ms": percentile(lat, 0.5),
         "p99_ms": percentile(lat, 0.99), "queue_p99_ms": percentile(qms, 0.99),

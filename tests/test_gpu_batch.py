@@ -300,3 +300,28 @@ def test_lockstep_with_host_arrays():
     finally:
         for g in grids:
             g.close()
+
+
+def test_lockstep_with_very_different_hierarchies():
+    """Grids of 2 to 6 multigrid levels and both problem types in one lockstep loop: each
+    grid's coarsest solve comes after the batch's down-sweep."""
+    ps = [P.cantilever(4, 2, 2), P.mbb_block(96, 48, 40, volfrac=0.12, rmin=2.5),
+          P.cantilever(9, 5, 3), P.mbb_block(33, 17, 9, rmin=1.5), P.cantilever(64, 32, 32)]
+    zs = _fields(ps, 900)
+    grids = [tomo.Grid.from_problem(p, precision=tomo.FP32) for p in ps]
+    try:
+        levels = [g.counts()[2] for g in grids]
+        assert min(levels) == 2 and max(levels) >= 6
+        alone = []
+        for g, z in zip(grids, zs):
+            dc = torch.empty_like(z)
+            c, info = g.gradient(z, dc)
+            torch.cuda.synchronize()
+            alone.append((c, info.iters, dc.cpu().numpy()))
+        cs, infos, dcs, _, runs = _run_batch(grids, zs, lockstep=True, workers=3)
+        assert runs == 1
+        for (c, it, dc), c2, i2, d2 in zip(alone, cs, infos, dcs):
+            assert i2.status == 0 and close(c2, d2, c, dc) and abs(it - i2.iters) <= 1
+    finally:
+        for g in grids:
+            g.close()
