@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -75,12 +76,71 @@ DenseK0<T> dense_k0(const tomo_grid* G) {
   return d;
 }
 
+// Device buffers come from the device's stream-ordered memory pool (cudaMallocAsync on the
+// grid's stream): a grid makes ~30 allocations, and plain cudaMalloc/cudaFree serialise
+// across host threads, which bounded the request loop (every request creates a grid).  The
+// pool keeps freed memory for reuse within this process (release threshold raised once);
+// grid creation ends with a stream synchronisation, so its buffers are ready for any stream.
+void pool_init_once() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
+}
+
 tomo_status dalloc(tomo_grid* G, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  CK(cudaMalloc(p, bytes));
-  if (G) G->dev_bytes += bytes;
+  pool_init_once();
+  CK(cudaMallocAsync(p, bytes, G->stream));
+  G->dev_bytes += bytes;
   return TOMO_OK;
+}
+
+// Small pinned host blocks (the CG scalars and result scalars read back per solve) from
+// 64 KiB page-locked slabs kept for the process: cudaMallocHost costs far more than a grid's
+// other host work.
+constexpr size_t kPinnedBlock = 256;
+struct PinnedSlabs {
+  std::mutex m;
+  std::vector<void*> free_blocks;
+};
+PinnedSlabs& pinned_slabs() {
+  static PinnedSlabs* s = new PinnedSlabs();  // never destroyed: blocks outlive static dtors
+  return *s;
+}
+
+void* pinned_get(size_t bytes) {
+  if (bytes > kPinnedBlock) return nullptr;
+  PinnedSlabs& P = pinned_slabs();
+  std::lock_guard<std::mutex> lk(P.m);
+  if (P.free_blocks.empty()) {
+    void* slab = nullptr;
+    if (cudaMallocHost(&slab, 64 * 1024) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (size_t o = 0; o < 64 * 1024; o += kPinnedBlock)
+      P.free_blocks.push_back(static_cast<char*>(slab) + o);
+  }
+  void* b = P.free_blocks.back();
+  P.free_blocks.pop_back();
+  std::memset(b, 0, kPinnedBlock);
+  return b;
+}
+
+void pinned_put(void* b) {
+  if (!b) return;
+  PinnedSlabs& P = pinned_slabs();
+  std::lock_guard<std::mutex> lk(P.m);
+  P.free_blocks.push_back(b);
 }
 
 bool is_device_ptr(const void* p) {
@@ -106,7 +166,7 @@ tomo_status stage_in(tomo_grid* G, const void* p, size_t bytes, int slot, const 
     G->stage_size.resize(slot + 1, 0);
   }
   if (G->stage_size[slot] < bytes) {
-    if (G->stage[slot]) cudaFree(G->stage[slot]);
+    if (G->stage[slot]) cudaFreeAsync(G->stage[slot], G->stream);
     G->dev_bytes -= G->stage_size[slot];
     G->stage[slot] = nullptr;
     G->stage_size[slot] = 0;
@@ -130,7 +190,7 @@ tomo_status stage_out(tomo_grid* G, void* p, size_t bytes, int slot, void** out,
     G->stage_size.resize(slot + 1, 0);
   }
   if (G->stage_size[slot] < bytes) {
-    if (G->stage[slot]) cudaFree(G->stage[slot]);
+    if (G->stage[slot]) cudaFreeAsync(G->stage[slot], G->stream);
     G->dev_bytes -= G->stage_size[slot];
     G->stage[slot] = nullptr;
     G->stage_size[slot] = 0;
@@ -1140,8 +1200,17 @@ std::vector<uint8_t> coarse_mask(const Geom& gf, const std::vector<uint8_t>& mf,
 
 void free_grid(tomo_grid* G) {
   if (!G) return;
-  auto F = [](void* p) {
-    if (p) cudaFree(p);
+  // nothing of the grid may still run; its buffers go back to the pool in stream order
+  cudaStream_t st = G->stream;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    st = nullptr;
+  }
+  auto F = [st](void* p) {
+    if (p && cudaFreeAsync(p, st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(p);
+    }
   };
   for (auto& Lv : G->L) {
     F(Lv.s);
@@ -1172,8 +1241,8 @@ void free_grid(tomo_grid* G) {
   F(G->counter);
   F(G->sc);
   F(G->dscal);
-  if (G->h_sc) cudaFreeHost(G->h_sc);
-  if (G->h_scal) cudaFreeHost(G->h_scal);
+  pinned_put(G->h_sc);
+  pinned_put(G->h_scal);
   for (void* s : G->stage) F(s);
   if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
   if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
@@ -1326,8 +1395,9 @@ tomo_status create_impl(tomo_grid* G) {
   TRY(dalloc(G, (void**)&G->sc, sizeof(CgScalars)));
   CK(cudaMemsetAsync(G->sc, 0, sizeof(CgScalars), G->stream));
   TRY(dalloc(G, (void**)&G->dscal, sizeof(double) * 8));
-  CK(cudaMallocHost((void**)&G->h_sc, sizeof(CgScalars)));
-  CK(cudaMallocHost((void**)&G->h_scal, sizeof(double) * 8));
+  G->h_sc = static_cast<CgScalars*>(pinned_get(sizeof(CgScalars)));
+  G->h_scal = static_cast<double*>(pinned_get(sizeof(double) * 8));
+  if (!G->h_sc || !G->h_scal) return fail(G, TOMO_ENOMEM, "pinned host memory");
   // filter taps and weight sums
   G->taps = filter_taps(G->d.rmin);
   G->ntaps = (int)G->taps.size();
