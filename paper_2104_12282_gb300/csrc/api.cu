@@ -1373,15 +1373,34 @@ tomo_status create_impl(tomo_grid* G) {
   TRY(dalloc(G, &G->Hs, ne));
   TRY(dalloc(G, &G->dvdz, ne));
   {
-    std::vector<double> fm(G->f);
-    for (size_t k = 0; k < fm.size(); ++k)
-      if (G->fixed[k]) fm[k] = 0.0;
+    // the load is sparse (point, line or face loads): zero both copies on the device and
+    // scatter the nonzero free entries
+    std::vector<int64_t> idx;
+    std::vector<double> val;
     G->ff = 0.0;
-    for (double v : fm) G->ff += v * v;
-    std::vector<T> ft(fm.begin(), fm.end());
-    CK(cudaMemcpyAsync(G->f_T, ft.data(), nv, cudaMemcpyHostToDevice, G->stream));
-    CK(cudaMemcpyAsync(G->f64, fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice,
-                       G->stream));
+    for (size_t k = 0; k < G->f.size(); ++k)
+      if (!G->fixed[k] && G->f[k] != 0.0) {
+        idx.push_back((int64_t)k);
+        val.push_back(G->f[k]);
+        G->ff += G->f[k] * G->f[k];
+      }
+    CK(cudaMemsetAsync(G->f_T, 0, nv, G->stream));
+    CK(cudaMemsetAsync(G->f64, 0, sizeof(double) * 3 * (size_t)g.nn, G->stream));
+    if (!idx.empty()) {
+      void* tmp = nullptr;
+      const size_t bi = sizeof(int64_t) * idx.size(), bv = sizeof(double) * val.size();
+      CK(cudaMallocAsync(&tmp, bi + bv, G->stream));
+      char* t = static_cast<char*>(tmp);
+      cudaError_t e = cudaMemcpyAsync(t, idx.data(), bi, cudaMemcpyHostToDevice, G->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t + bi, val.data(), bv, cudaMemcpyHostToDevice, G->stream);
+      if (e == cudaSuccess)
+        e = launch_scatter_load<T>(G->stream, (int)idx.size(), (const int64_t*)t,
+                                   (const double*)(t + bi), (T*)G->f_T, G->f64);
+      cudaFreeAsync(tmp, G->stream);
+      CK(e);
+      G->launches += 1;
+    }
   }
   G->rhs_T = G->f_T;
   G->rhs64 = G->f64;
@@ -1418,8 +1437,7 @@ tomo_status create_impl(tomo_grid* G) {
                        G->stream));
     CK(cudaMemcpyAsync(G->d_tapw, tw.data(), sizeof(T) * G->ntaps, cudaMemcpyHostToDevice,
                        G->stream));
-    std::vector<T> ones(g.nel, T(1));
-    CK(cudaMemcpyAsync(G->dcp, ones.data(), ne, cudaMemcpyHostToDevice, G->stream));
+    CK(launch_fill<T>(G->stream, g.nel, (T*)G->dcp, T(1)));
     CK(launch_filter<T>(G->stream, g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
                         G->filter_radius,
                         (const T*)G->dcp, nullptr, (T*)G->Hs, 2, 0, T(0), T(0), T(0), T(0),

@@ -76,6 +76,13 @@ struct MarchRrBatch {
 cudaError_t launch_march_rr_batch(cudaStream_t st, const MarchArgs<double>* a, int n,
                                   const ElemConst<double>& c, int num_sms);
 
+// p[0..n) = v; fT[idx[k]] = f64[idx[k]] = val[k] for k < nnz (vec.cu)
+template <typename T>
+cudaError_t launch_fill(cudaStream_t st, int64_t n, T* p, T v);
+template <typename T>
+cudaError_t launch_scatter_load(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
+                                T* fT, double* f64);
+
 // Batched pointwise/vector kernels (vec.cu) for FP32 grids: one entry per grid, the grid
 // owning the launch's blocks [cta0[q], cta0[q+1]).
 struct JacobiItem {  // zero-start first Chebyshev step x1 = c2 D^-1 b

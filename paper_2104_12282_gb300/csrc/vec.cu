@@ -608,6 +608,54 @@ cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc)
   return cudaGetLastError();
 }
 
+// p[0..n) = v
+template <typename T>
+__global__ void k_fill(int64_t n, T* __restrict__ p, T v) {
+  PDL_ENTER();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+template <typename T>
+cudaError_t launch_fill(cudaStream_t st, int64_t n, T* p, T v) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  pdl_launch(k_fill<T>, (int)blocks, 256, 0, st, n, p, v);
+  return cudaGetLastError();
+}
+
+// the load from its nonzero entries: fT[idx[k]] = val[k], f64[idx[k]] = val[k] (the vectors
+// are zeroed before)
+template <typename T>
+__global__ void k_scatter_load(int nnz, const int64_t* __restrict__ idx,
+                               const double* __restrict__ val, T* __restrict__ fT,
+                               double* __restrict__ f64) {
+  PDL_ENTER();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+    fT[idx[k]] = (T)val[k];
+    f64[idx[k]] = val[k];
+  }
+}
+
+template <typename T>
+cudaError_t launch_scatter_load(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
+                                T* fT, double* f64) {
+  if (nnz <= 0) return cudaSuccess;
+  int blocks = (nnz + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  pdl_launch(k_scatter_load<T>, blocks, 256, 0, st, nnz, idx, val, fT, f64);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fill<float>(cudaStream_t, int64_t, float*, float);
+template cudaError_t launch_fill<double>(cudaStream_t, int64_t, double*, double);
+template cudaError_t launch_scatter_load<float>(cudaStream_t, int, const int64_t*,
+                                                const double*, float*, double*);
+template cudaError_t launch_scatter_load<double>(cudaStream_t, int, const int64_t*,
+                                                 const double*, double*, double*);
+
 // ---------------------------------------------------------------------------------------
 // Batched launches (FP32): block b belongs to grid q with cta0[q] <= b < cta0[q+1] and acts
 // as block b - cta0[q] of cta0[q+1] - cta0[q]; each grid gets the block count its own launch
