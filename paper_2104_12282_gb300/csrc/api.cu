@@ -355,6 +355,9 @@ tomo_status setup_levels(tomo_grid* G) {
     G->launches += 1;
   }
   if (G->L.size() > 1) {
+    // (a non-positive pivot is replaced by 1, which keeps the coarsest solve SPD; the
+    // breakdown bit it sets is cleared when pcg_start resets the CG scalars: whether the
+    // preconditioned CG converges is what the solve reports)
     auto& C = G->L.back();
     CK(launch_coarse_factor<T>(G->stream, C.g, (const T*)C.s, C.mask, dense_k0<T>(G),
                                (T*)G->coarseA, (T*)G->coarseD, &G->sc->status));
