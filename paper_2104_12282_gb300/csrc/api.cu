@@ -208,7 +208,16 @@ tomo_status copy_back(tomo_grid* G, void* host, const void* dev, size_t bytes, b
   return TOMO_OK;
 }
 
+// The grid's stream waits for a coarsest factorisation still running on the side stream.
+tomo_status join_factor(tomo_grid* G) {
+  if (!G->factor_pending) return TOMO_OK;
+  G->factor_pending = false;
+  CK(cudaStreamWaitEvent(G->stream, G->ev_factor, 0));
+  return TOMO_OK;
+}
+
 tomo_status sync(tomo_grid* G) {
+  TRY(join_factor(G));
   CK(cudaStreamSynchronize(G->stream));
   return TOMO_OK;
 }
@@ -359,9 +368,22 @@ tomo_status setup_levels(tomo_grid* G) {
     // breakdown bit it sets is cleared when pcg_start resets the CG scalars: whether the
     // preconditioned CG converges is what the solve reports)
     auto& C = G->L.back();
-    CK(launch_coarse_factor<T>(G->stream, C.g, (const T*)C.s, C.mask, dense_k0<T>(G),
+    // one CTA for ~100+ us: overlapped with the first V-cycle's down-sweep, which needs it
+    // only at the coarsest level (profiling keeps everything on one stream)
+    TRY(join_factor(G));
+    cudaStream_t fst = G->stream;
+    if (!G->prof && G->side) {
+      CK(cudaEventRecord(G->ev_fork, G->stream));
+      CK(cudaStreamWaitEvent(G->side, G->ev_fork, 0));
+      fst = G->side;
+    }
+    CK(launch_coarse_factor<T>(fst, C.g, (const T*)C.s, C.mask, dense_k0<T>(G),
                                (T*)G->coarseA, (T*)G->coarseD, &G->sc->status));
     G->launches += 1;
+    if (fst != G->stream) {
+      CK(cudaEventRecord(G->ev_factor, G->side));
+      G->factor_pending = true;
+    }
   }
   return TOMO_OK;
 }
@@ -441,6 +463,7 @@ tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int
   auto& Lv = G->L[l];
   const int nl = (int)G->L.size();
   if (l == nl - 1) {
+    TRY(join_factor(G));
     LevelTimer lt(G, l);
     CK(launch_coarse_apply<T>(G->stream, G->coarse_n, (const T*)G->coarseA,
                               (const T*)G->coarseD, b, (T*)Lv.x, skip));
@@ -552,6 +575,7 @@ tomo_status enqueue_iteration(tomo_grid* G) {
 // with a kernel that clears the condition once CG has stopped.
 template <typename T>
 tomo_status build_loop_graph(tomo_grid* G, cudaGraphExec_t* out) {
+  TRY(join_factor(G));  // (nothing outside the capture may be waited on inside it)
   if (!G->cap_stream) CK(cudaStreamCreateWithFlags(&G->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t graph;
   CK(cudaGraphCreate(&graph, 0));
@@ -1205,6 +1229,7 @@ void free_grid(tomo_grid* G) {
   if (!G) return;
   // nothing of the grid may still run; its buffers go back to the pool in stream order
   cudaStream_t st = G->stream;
+  if (G->side) cudaStreamSynchronize(G->side);
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     st = nullptr;
@@ -1256,6 +1281,9 @@ void free_grid(tomo_grid* G) {
   F(G->adj_hi);
   F(G->adj_lo);
   if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
+  if (G->side) cudaStreamDestroy(G->side);
+  if (G->ev_fork) cudaEventDestroy(G->ev_fork);
+  if (G->ev_factor) cudaEventDestroy(G->ev_factor);
   for (auto e : G->ev) cudaEventDestroy(e);
   for (auto e : G->phase_ev)
     if (e) cudaEventDestroy(e);
@@ -1359,6 +1387,11 @@ tomo_status create_impl(tomo_grid* G) {
   if (G->coarse_n > 0) {
     TRY(dalloc(G, &G->coarseA, sizeof(T) * (size_t)G->coarse_n * G->coarse_n));
     TRY(dalloc(G, &G->coarseD, sizeof(T) * (size_t)G->coarse_n));
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&G->side, cudaStreamNonBlocking, greatest));
+    CK(cudaEventCreateWithFlags(&G->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&G->ev_factor, cudaEventDisableTiming));
   }
   // fine vectors
   TRY(dalloc(G, &G->f_T, nv));
@@ -2384,6 +2417,7 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
     if (st[i] == TOMO_OK)
       st[i] = pcg_start<float>(G, G->warm_gradient && G->have_solution,
                                info ? info + i : nullptr, &tv);
+    if (st[i] == TOMO_OK) st[i] = join_factor(G);  // the batch stream waits for this stream
     trivial[i] = tv ? 1 : 0;
   });
   for (int w = 0; w < W; ++w) {

@@ -346,6 +346,11 @@ struct tomo_grid {
   int partials_n = 0;
   double ff = 0.0;                  // ||f||^2 over free DOFs
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  // the coarsest factorisation runs on `side` (high priority) while the first V-cycle's
+  // down-sweep runs on `stream`; joined before the first coarsest solve (join_factor)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_factor = nullptr;
+  bool factor_pending = false;
   cudaGraphExec_t loop_exec = nullptr;  // device-side PCG loop (conditional while)
   // right-hand side of the next pcg: the load f (rhs_id 0) or an adjoint load (rhs_id 1);
   // each has its own captured loop, since the FP64 residual replacement reads it
