@@ -690,7 +690,12 @@ tomo_status pcg_start(tomo_grid* G, bool warm, tomo_solve_info* info, bool* triv
   } else {
     CK(cudaMemsetAsync(xhi, 0, sizeof(T) * n, G->stream));
     if (xlo) CK(cudaMemsetAsync(xlo, 0, sizeof(T) * n, G->stream));
-    CK(launch_mask_copy<T>(G->stream, g, (const T*)G->rhs_T, G->L[0].mask, r));
+    if (G->rhs_id == 0) {  // r = f (free entries): zero, then the load's nonzero entries
+      CK(cudaMemsetAsync(r, 0, sizeof(T) * n, G->stream));
+      CK(launch_scatter_vec<T>(G->stream, G->load_nnz, G->load_idx, G->load_val, r));
+    } else {
+      CK(launch_mask_copy<T>(G->stream, g, (const T*)G->rhs_T, G->L[0].mask, r));
+    }
     G->launches += 1;
   }
   CK(cudaMemsetAsync(p, 0, sizeof(T) * n, G->stream));
@@ -765,16 +770,18 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
 template <typename T>
 tomo_status volume_gradient(tomo_grid* G, T* out) {
   const int ne = G->g.nel;
-  if (!G->dvdz_ready) {
-    std::vector<T> v(ne, (T)(G->d.h * G->d.h * G->d.h));
-    CK(cudaMemcpyAsync(G->dvdz, v.data(), sizeof(T) * ne, cudaMemcpyHostToDevice, G->stream));
-    G->dvdz_ready = true;  // G->dvdz holds the constant element volumes
+  if (G->dvdz_ready) {  // design independent: computed on the first call, copied after
+    CK(cudaMemcpyAsync(out, G->dvdz, sizeof(T) * ne, cudaMemcpyDeviceToDevice, G->stream));
+    return TOMO_OK;
   }
+  CK(launch_fill<T>(G->stream, ne, (T*)G->dvdz, (T)(G->d.h * G->d.h * G->d.h)));
   CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
                       G->filter_radius,
                       (const T*)G->dvdz, (const T*)G->Hs, out, 1, 0, T(0), T(0), T(0), T(0),
                       nullptr));
-  G->launches += 1;
+  CK(cudaMemcpyAsync(G->dvdz, out, sizeof(T) * ne, cudaMemcpyDeviceToDevice, G->stream));
+  G->launches += 2;
+  G->dvdz_ready = true;
   return TOMO_OK;
 }
 
@@ -935,8 +942,14 @@ tomo_status compliance_and_sens(tomo_grid* G, const T* drho, const T* du, const 
                                 double* compliance, T* ddc) {
   const tomo_grid_desc& d = G->d;
   if (compliance) {
-    CK(launch_dot<double, T>(G->stream, 3 * G->g.nn, G->f64, du, dulo, G->partials, G->counter,
-                             G->dscal));
+    // f^T u: the load is sparse (point, line, face loads), so only its nonzero entries
+    if (G->load_nnz <= (1 << 18)) {
+      CK(launch_sparse_dot<T>(G->stream, G->load_nnz, G->load_idx, G->load_val, du, dulo,
+                              G->dscal));
+    } else {
+      CK(launch_dot<double, T>(G->stream, 3 * G->g.nn, G->f64, du, dulo, G->partials,
+                               G->counter, G->dscal));
+    }
     G->launches += 1;
   }
   if (ddc) {
@@ -1276,6 +1289,8 @@ void free_grid(tomo_grid* G) {
   if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
   for (auto& e : G->loop_cache) cudaGraphExecDestroy(e.exec);
   G->loop_cache.clear();
+  F(G->load_idx);
+  F(G->load_val);
   F(G->adj_T);
   F(G->adj64);
   F(G->adj_hi);
@@ -1422,19 +1437,16 @@ tomo_status create_impl(tomo_grid* G) {
       }
     CK(cudaMemsetAsync(G->f_T, 0, nv, G->stream));
     CK(cudaMemsetAsync(G->f64, 0, sizeof(double) * 3 * (size_t)g.nn, G->stream));
-    if (!idx.empty()) {
-      void* tmp = nullptr;
-      const size_t bi = sizeof(int64_t) * idx.size(), bv = sizeof(double) * val.size();
-      CK(cudaMallocAsync(&tmp, bi + bv, G->stream));
-      char* t = static_cast<char*>(tmp);
-      cudaError_t e = cudaMemcpyAsync(t, idx.data(), bi, cudaMemcpyHostToDevice, G->stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(t + bi, val.data(), bv, cudaMemcpyHostToDevice, G->stream);
-      if (e == cudaSuccess)
-        e = launch_scatter_load<T>(G->stream, (int)idx.size(), (const int64_t*)t,
-                                   (const double*)(t + bi), (T*)G->f_T, G->f64);
-      cudaFreeAsync(tmp, G->stream);
-      CK(e);
+    if (!idx.empty()) {  // kept: the compliance f^T u and the CG start use the entries
+      G->load_nnz = (int)idx.size();
+      TRY(dalloc(G, (void**)&G->load_idx, sizeof(int64_t) * idx.size()));
+      TRY(dalloc(G, (void**)&G->load_val, sizeof(double) * val.size()));
+      CK(cudaMemcpyAsync(G->load_idx, idx.data(), sizeof(int64_t) * idx.size(),
+                         cudaMemcpyHostToDevice, G->stream));
+      CK(cudaMemcpyAsync(G->load_val, val.data(), sizeof(double) * val.size(),
+                         cudaMemcpyHostToDevice, G->stream));
+      CK(launch_scatter_load<T>(G->stream, G->load_nnz, G->load_idx, G->load_val, (T*)G->f_T,
+                                G->f64));
       G->launches += 1;
     }
   }

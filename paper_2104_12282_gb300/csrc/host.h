@@ -82,6 +82,13 @@ cudaError_t launch_fill(cudaStream_t st, int64_t n, T* p, T v);
 template <typename T>
 cudaError_t launch_scatter_load(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
                                 T* fT, double* f64);
+// f^T (u + ulo) over the nonzero load entries (FP64, one block); r = scatter of the entries
+template <typename T>
+cudaError_t launch_sparse_dot(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
+                              const T* u, const T* ulo, double* out);
+template <typename T>
+cudaError_t launch_scatter_vec(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
+                               T* r);
 
 // Batched pointwise/vector kernels (vec.cu) for FP32 grids: one entry per grid, the grid
 // owning the launch's blocks [cta0[q], cta0[q+1]).
@@ -305,7 +312,11 @@ struct tomo_grid {
   int ntaps = 0;
   void* Hs = nullptr;          // T[nel]
   void* dvdz = nullptr;        // T[nel] P^T v (cached)
-  bool dvdz_ready = false;
+  bool dvdz_ready = false;     // dvdz holds P^T v (design independent, computed once)
+  // the load's nonzero free entries (indices into the 3*nn DOF vector, values)
+  int64_t* load_idx = nullptr;
+  double* load_val = nullptr;
+  int load_nnz = 0;
   std::vector<tomo_level> L;
   int coarse_n = 0;            // coarsest DOFs (dense)
   int filter_radius = 0;       // largest |offset| component of the filter taps

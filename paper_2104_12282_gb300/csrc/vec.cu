@@ -649,6 +649,67 @@ cudaError_t launch_scatter_load(cudaStream_t st, int nnz, const int64_t* idx, co
   return cudaGetLastError();
 }
 
+// out = sum_k val[k] (u + ulo)[idx[k]] in FP64 (one block, fixed order): f^T u for a sparse
+// load f given by its nonzero entries.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_sparse_dot(int nnz, const int64_t* __restrict__ idx,
+                                                     const double* __restrict__ val,
+                                                     const T* __restrict__ u,
+                                                     const T* __restrict__ ulo, double* out) {
+  PDL_ENTER();
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nnz; k += blockDim.x) {
+    const int64_t i = idx[k];
+    double uv = (double)u[i];
+    if (ulo) uv += (double)ulo[i];
+    acc += val[k] * uv;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+template <typename T>
+cudaError_t launch_sparse_dot(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
+                              const T* u, const T* ulo, double* out) {
+  pdl_launch(k_sparse_dot<T>, 1, 1024, 0, st, nnz, idx, val, u, ulo, out);
+  return cudaGetLastError();
+}
+
+// r = 0 on every DOF, then r[idx[k]] = val[k]: the CG start residual f (masked) from the load's
+// nonzero entries
+template <typename T>
+__global__ void k_scatter_vec(int nnz, const int64_t* __restrict__ idx,
+                              const double* __restrict__ val, T* __restrict__ r) {
+  PDL_ENTER();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x)
+    r[idx[k]] = (T)val[k];
+}
+
+template <typename T>
+cudaError_t launch_scatter_vec(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
+                               T* r) {
+  if (nnz <= 0) return cudaSuccess;
+  int blocks = (nnz + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  pdl_launch(k_scatter_vec<T>, blocks, 256, 0, st, nnz, idx, val, r);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sparse_dot<float>(cudaStream_t, int, const int64_t*, const double*,
+                                              const float*, const float*, double*);
+template cudaError_t launch_sparse_dot<double>(cudaStream_t, int, const int64_t*, const double*,
+                                               const double*, const double*, double*);
+template cudaError_t launch_scatter_vec<float>(cudaStream_t, int, const int64_t*, const double*,
+                                               float*);
+template cudaError_t launch_scatter_vec<double>(cudaStream_t, int, const int64_t*,
+                                                const double*, double*);
 template cudaError_t launch_fill<float>(cudaStream_t, int64_t, float*, float);
 template cudaError_t launch_fill<double>(cudaStream_t, int64_t, double*, double);
 template cudaError_t launch_scatter_load<float>(cudaStream_t, int, const int64_t*,
