@@ -327,6 +327,12 @@ tomo_status tomo_batch_append(tomo_batch* batch, tomo_grid* grid);
 tomo_status tomo_batch_size(const tomo_batch* batch, int32_t* count);
 tomo_status tomo_batch_set_lockstep(tomo_batch* batch, int32_t on);
 tomo_status tomo_batch_lockstep_runs(const tomo_batch* batch, int64_t* runs);
+/* Phases of the last lockstep call, milliseconds: ms[0] host time to issue the per-grid
+ * steps before the loop (filter, material, level setup, CG start), ms[1] device time from
+ * their end to the end of the first V-cycle and search direction, ms[2] the CG loop,
+ * ms[3] the read-back of the grids' CG scalars, ms[4] host time of the per-grid steps after
+ * the loop (results, sensitivities, filter adjoints, up to the last stream's completion). */
+tomo_status tomo_batch_phase_times(const tomo_batch* batch, double* ms);
 tomo_status tomo_batch_gradient(tomo_batch* batch, const float* const* z, double* compliance,
                                 float* const* dcdz, float* const* dvdz, tomo_solve_info* info);
 tomo_status tomo_batch_destroy(tomo_batch* batch);

@@ -2,6 +2,7 @@
 // the exact-gradient evaluation (Algorithm 1, exact branch; Eq. 4-5, Section III-D).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -2002,6 +2003,11 @@ struct tomo_batch {
   int64_t iter_launches = 0;  // batched launches per loop iteration
   std::vector<cudaEvent_t> wev;
   cudaEvent_t bev = nullptr;
+  // phase timing of the last lockstep call: host ms of phase A (enqueue) and phase C
+  // (results), device ms from the end of phase A to the end of the first V-cycle, of the CG
+  // loop, and of the scalar read-back (events on the batch stream)
+  cudaEvent_t tev[4] = {};
+  double phase_ms[5] = {};
 };
 
 namespace {
@@ -2418,6 +2424,9 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
   std::vector<char> trivial(n, 0);
   std::vector<cudaStream_t> own(n);
   for (int i = 0; i < n; ++i) own[i] = B->grids[i]->stream;
+  for (auto& e : B->tev)
+    if (!e) BK(cudaEventCreate(&e));
+  const auto h0 = std::chrono::steady_clock::now();
   // phase A: S1-S2 and the CG start of every grid, on the worker streams
   for_grids_lpt(B, W, [&](int w, int i) {
     tomo_grid* G = B->grids[i];
@@ -2429,13 +2438,23 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
     if (st[i] == TOMO_OK)
       st[i] = pcg_start<float>(G, G->warm_gradient && G->have_solution,
                                info ? info + i : nullptr, &tv);
-    if (st[i] == TOMO_OK) st[i] = join_factor(G);  // the batch stream waits for this stream
     trivial[i] = tv ? 1 : 0;
   });
   for (int w = 0; w < W; ++w) {
     BK(cudaEventRecord(B->wev[w], B->streams[w]));
     BK(cudaStreamWaitEvent(B->bst, B->wev[w], 0));
   }
+  // the coarsest factorisations run concurrently on the grids' side streams; the batch
+  // stream (first coarsest solve) waits for each of them, not the worker streams
+  for (int i = 0; i < n; ++i) {
+    tomo_grid* G = B->grids[i];
+    if (G->factor_pending) {
+      G->factor_pending = false;
+      BK(cudaStreamWaitEvent(B->bst, G->ev_factor, 0));
+    }
+  }
+  const auto h1 = std::chrono::steady_clock::now();
+  BK(cudaEventRecord(B->tev[0], B->bst));
   // phase B: one CG loop for the grids that have a system to solve
   std::vector<tomo_grid*> act;
   for (int i = 0; i < n; ++i)
@@ -2448,23 +2467,37 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
     std::vector<float*> zz;
     bs = batch_vcycle(B, B->bst, act, r, true, &zz, &launches);
     if (bs == TOMO_OK) bs = batch_cg_p(B, B->bst, act, zz, &launches);
+    if (bs == TOMO_OK && cudaEventRecord(B->tev[1], B->bst) != cudaSuccess) bs = TOMO_ECUDA;
     bool stale = !B->loop || B->plan != act;
     for (size_t q = 0; !stale && q < act.size(); ++q) stale = B->plan_gen[q] != act[q]->gen;
     if (bs == TOMO_OK && stale) bs = batch_build_loop(B, act);
     if (bs == TOMO_OK) {
       cudaError_t e = cudaGraphLaunch(B->loop, B->bst);
+      if (e == cudaSuccess) e = cudaEventRecord(B->tev[2], B->bst);
       for (size_t q = 0; q < act.size() && e == cudaSuccess; ++q)
         e = cudaMemcpyAsync(act[q]->h_sc, act[q]->sc, sizeof(CgScalars),
                             cudaMemcpyDeviceToHost, B->bst);
+      if (e == cudaSuccess) e = cudaEventRecord(B->tev[3], B->bst);
       if (e == cudaSuccess) e = cudaStreamSynchronize(B->bst);
       if (e != cudaSuccess) {
         B->err = std::string("lockstep CG loop: ") + cudaGetErrorString(e);
         bs = TOMO_ECUDA;
       }
+      float t01 = 0.f, t12 = 0.f, t23 = 0.f;
+      if (bs == TOMO_OK) {
+        cudaEventElapsedTime(&t01, B->tev[0], B->tev[1]);
+        cudaEventElapsedTime(&t12, B->tev[1], B->tev[2]);
+        cudaEventElapsedTime(&t23, B->tev[2], B->tev[3]);
+        cudaGetLastError();
+      }
+      B->phase_ms[1] = t01;
+      B->phase_ms[2] = t12;
+      B->phase_ms[3] = t23;
     }
     if (bs == TOMO_OK)
       for (auto* G : act) G->launches += launches + (int64_t)G->h_sc->loops * B->iter_launches;
   }
+  const auto h2 = std::chrono::steady_clock::now();
   if (bs == TOMO_OK) {
     BK(cudaEventRecord(B->bev, B->bst));
     // phase C: results, S6-S7 on the worker streams
@@ -2495,6 +2528,9 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
     for (int i = 0; i < n; ++i)
       if (st[i] == TOMO_OK && !is_device_ptr(compliance + i)) compliance[i] = *B->grids[i]->h_scal;
   }
+  const auto h3 = std::chrono::steady_clock::now();
+  B->phase_ms[0] = std::chrono::duration<double, std::milli>(h1 - h0).count();
+  B->phase_ms[4] = std::chrono::duration<double, std::milli>(h3 - h2).count();
   // the worker streams must not run ahead of anything still queued on the batch stream
   cudaStreamSynchronize(B->bst);
   for (int i = 0; i < n; ++i) B->grids[i]->stream = own[i];
@@ -2544,6 +2580,12 @@ tomo_status tomo_batch_append(tomo_batch* B, tomo_grid* G) {
 tomo_status tomo_batch_set_lockstep(tomo_batch* B, int32_t on) {
   if (!B) return TOMO_EINVAL;
   B->lockstep = on != 0;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_phase_times(const tomo_batch* B, double* ms) {
+  if (!B || !ms) return TOMO_EINVAL;
+  for (int k = 0; k < 5; ++k) ms[k] = B->phase_ms[k];
   return TOMO_OK;
 }
 
@@ -2610,6 +2652,8 @@ tomo_status tomo_batch_destroy(tomo_batch* B) {
   if (B->d_scs) cudaFree(B->d_scs);
   for (auto e : B->wev) cudaEventDestroy(e);
   if (B->bev) cudaEventDestroy(B->bev);
+  for (auto e : B->tev)
+    if (e) cudaEventDestroy(e);
   delete B;
   return TOMO_OK;
 }

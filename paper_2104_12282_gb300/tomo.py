@@ -105,6 +105,7 @@ def _load():
         "tomo_batch_size": (st, [P, ctypes.POINTER(ctypes.c_int32)]),
         "tomo_batch_set_lockstep": (st, [P, ctypes.c_int32]),
         "tomo_batch_lockstep_runs": (st, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "tomo_batch_phase_times": (st, [P, P]),
         "tomo_batch_gradient": (st, [P, P, ctypes.POINTER(ctypes.c_double), P, P,
                                      ctypes.POINTER(SolveInfo)]),
         "tomo_batch_destroy": (st, [P]),
@@ -179,7 +180,7 @@ def exported_symbols():
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
             "tomo_server_last_error", "tomo_grid_device_bytes", "tomo_estimate_device_bytes",
             "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
-            "tomo_batch_set_lockstep", "tomo_batch_lockstep_runs",
+            "tomo_batch_set_lockstep", "tomo_batch_lockstep_runs", "tomo_batch_phase_times",
             "tomo_batch_gradient", "tomo_batch_destroy", "tomo_batch_last_error",
             "tomo_filter", "tomo_filter_d", "tomo_coarse_grain", "tomo_coarse_grain_d",
             "tomo_adjoint_gradient", "tomo_adjoint_gradient_d",
@@ -514,6 +515,14 @@ class Batch:
         self._h = h
         self.grids = []
         lib().tomo_batch_set_lockstep(self._h, int(bool(lockstep)))
+
+    def phase_times(self):
+        """Phases of the last lockstep call in ms (tomo_batch_phase_times): issue of the
+        per-grid steps before the loop, first V-cycle, CG loop, scalar read-back, per-grid
+        steps after the loop."""
+        ms = (ctypes.c_double * 5)()
+        lib().tomo_batch_phase_times(self._h, ctypes.cast(ms, ctypes.c_void_p))
+        return dict(zip(("issue_before", "first_vcycle", "loop", "readback", "after"), ms))
 
     @property
     def lockstep_runs(self):
