@@ -652,10 +652,9 @@ tomo_status pcg_start(tomo_grid* G, bool warm, tomo_solve_info* info, bool* triv
   h.maxit = G->d.maxit;
   h.rr_every = G->d.rr_every > 0 ? G->d.rr_every : 0;
   *G->h_sc = h;
-  CK(cudaMemcpyAsync(G->sc, G->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, G->stream));
   if (ff == 0.0) {
-    CK(cudaMemsetAsync(xhi, 0, sizeof(T) * n, G->stream));
-    if (xlo) CK(cudaMemsetAsync(xlo, 0, sizeof(T) * n, G->stream));
+    CK(launch_cg_start<T>(G->stream, n, xhi, xlo, nullptr, nullptr, G->sc, h));
+    G->launches += 1;
     TRY(sync(G));
     if (info) {
       info->iters = 0;
@@ -668,6 +667,8 @@ tomo_status pcg_start(tomo_grid* G, bool warm, tomo_solve_info* info, bool* triv
     return TOMO_OK;
   }
   if (warm) {
+    CK(launch_cg_start<T>(G->stream, n, nullptr, nullptr, nullptr, p, G->sc, h));
+    G->launches += 1;
     bool done = false;
     if constexpr (sizeof(T) == 4) {
       if (G->s64) {  // r = f - K x evaluated in FP64 from the float pair, rounded once
@@ -688,18 +689,15 @@ tomo_status pcg_start(tomo_grid* G, bool warm, tomo_solve_info* info, bool* triv
       a.y = r;
       TRY(march<T>(G, 0, M_RESID, a));
     }
+  } else if (G->rhs_id == 0) {  // x = 0, p = 0, r = f: zeros, then the load's nonzero entries
+    CK(launch_cg_start<T>(G->stream, n, xhi, xlo, r, p, G->sc, h));
+    CK(launch_scatter_vec<T>(G->stream, G->load_nnz, G->load_idx, G->load_val, r));
+    G->launches += 2;
   } else {
-    CK(cudaMemsetAsync(xhi, 0, sizeof(T) * n, G->stream));
-    if (xlo) CK(cudaMemsetAsync(xlo, 0, sizeof(T) * n, G->stream));
-    if (G->rhs_id == 0) {  // r = f (free entries): zero, then the load's nonzero entries
-      CK(cudaMemsetAsync(r, 0, sizeof(T) * n, G->stream));
-      CK(launch_scatter_vec<T>(G->stream, G->load_nnz, G->load_idx, G->load_val, r));
-    } else {
-      CK(launch_mask_copy<T>(G->stream, g, (const T*)G->rhs_T, G->L[0].mask, r));
-    }
-    G->launches += 1;
+    CK(launch_cg_start<T>(G->stream, n, xhi, xlo, nullptr, p, G->sc, h));
+    CK(launch_mask_copy<T>(G->stream, g, (const T*)G->rhs_T, G->L[0].mask, r));
+    G->launches += 2;
   }
-  CK(cudaMemsetAsync(p, 0, sizeof(T) * n, G->stream));
   return TOMO_OK;
 }
 

@@ -89,6 +89,10 @@ cudaError_t launch_sparse_dot(cudaStream_t st, int nnz, const int64_t* idx, cons
 template <typename T>
 cudaError_t launch_scatter_vec(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
                                T* r);
+// one launch: zero the non-null vectors among xhi, xlo, r, p (n each) and set *sc = h
+template <typename T>
+cudaError_t launch_cg_start(cudaStream_t st, int n, T* xhi, T* xlo, T* r, T* p,
+                            tomo::CgScalars* sc, const tomo::CgScalars& h);
 
 // Batched pointwise/vector kernels (vec.cu) for FP32 grids: one entry per grid, the grid
 // owning the launch's blocks [cta0[q], cta0[q+1]).

@@ -374,10 +374,10 @@ cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint
   const size_t extra = sizeof(T) * (size_t)g.nel + (size_t)g.nn + 16;
   const size_t full = sizeof(T) * ((size_t)n * n + 4 * n) + extra;
   if (full <= 200 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_factor<T, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024 + 1024);
-    if (e != cudaSuccess) return e;
+    static cudaError_t attr = cudaFuncSetAttribute(
+        k_coarse_factor<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        200 * 1024 + 1024);  // once per process (and per type)
+    if (attr != cudaSuccess) return attr;
     pdl_launch(k_coarse_factor<T, true>, 1, 1024, full, st, g, s, mask, K0, A, dscale, status);
   } else {
     pdl_launch(k_coarse_factor<T, false>, 1, 1024, sizeof(T) * 4 * (size_t)n + extra, st, g, s,
@@ -710,6 +710,44 @@ template cudaError_t launch_scatter_vec<float>(cudaStream_t, int, const int64_t*
                                                float*);
 template cudaError_t launch_scatter_vec<double>(cudaStream_t, int, const int64_t*,
                                                 const double*, double*);
+// Start of a CG solve in one launch: the non-null vectors among x_hi, x_lo, r, p (n each) are
+// zeroed and *sc = h (the solve's scalars, passed by value).
+template <typename T>
+__global__ void k_cg_start(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __restrict__ r,
+                           T* __restrict__ p, CgScalars* sc, CgScalars h) {
+  PDL_ENTER();
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sc = h;
+  T* v[4] = {xhi, xlo, r, p};
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    T* x = v[a];
+    if (!x) continue;
+    int i0 = 0;
+    if constexpr (sizeof(T) == 4) {
+      const int n4 = n >> 2;
+      for (int i = tid; i < n4; i += nt)
+        reinterpret_cast<float4*>(x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      i0 = n4 << 2;
+    }
+    for (int i = i0 + tid; i < n; i += nt) x[i] = T(0);
+  }
+}
+
+template <typename T>
+cudaError_t launch_cg_start(cudaStream_t st, int n, T* xhi, T* xlo, T* r, T* p, CgScalars* sc,
+                            const CgScalars& h) {
+  int blocks = ((n >> 2) + 255) / 256;
+  if (blocks > 8 * 152) blocks = 8 * 152;
+  if (blocks < 1) blocks = 1;
+  pdl_launch(k_cg_start<T>, blocks, 256, 0, st, n, xhi, xlo, r, p, sc, h);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_cg_start<float>(cudaStream_t, int, float*, float*, float*, float*,
+                                            CgScalars*, const CgScalars&);
+template cudaError_t launch_cg_start<double>(cudaStream_t, int, double*, double*, double*,
+                                             double*, CgScalars*, const CgScalars&);
 template cudaError_t launch_fill<float>(cudaStream_t, int64_t, float*, float);
 template cudaError_t launch_fill<double>(cudaStream_t, int64_t, double*, double);
 template cudaError_t launch_scatter_load<float>(cudaStream_t, int, const int64_t*,
