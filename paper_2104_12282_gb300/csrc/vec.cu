@@ -2,6 +2,7 @@
 // reductions.  The solve of the state equation of Eq. 4 (Section III-D) is preconditioned
 // CG, the standard solver the paper names (PCG; multigrid is the stated alternative).
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "host.h"
@@ -820,17 +821,31 @@ __global__ void k_loop_cond_batch(cudaGraphConditionalHandle h, CgScalars* const
 
 namespace {
 
-// Fill tables of up to kBatchMax entries with blocks(item) blocks each and launch them.
-template <class Item, class Blocks, class Launch>
-cudaError_t flat_batches(const Item* a, int n, Blocks blocks, Launch launch) {
+// Fill tables of up to kBatchMax entries and launch them.  blocks(item): the block count of
+// the item's own launch; work(item) > 0: the launch shares about kBatchBlocks blocks among
+// the items in proportion to their work (at most their own count, at least one), since a
+// batch of small grids at their own counts carries thousands of nearly empty blocks.  Only
+// for kernels whose results do not depend on the block count (grid-stride pointwise work),
+// or whose reduction order may follow the batch.
+constexpr int kBatchBlocks = 2 * 8 * 152;  // two waves of 256-thread blocks
+template <class Item, class Blocks, class Work, class Launch>
+cudaError_t flat_batches(const Item* a, int n, Blocks blocks, Work work, Launch launch) {
   for (int q0 = 0; q0 < n; q0 += kBatchMax) {
     FlatBatch<Item> B{};
     B.n = std::min(kBatchMax, n - q0);
+    double wsum = 0.0;
+    for (int q = 0; q < B.n; ++q) wsum += (double)work(a[q0 + q]);
     int ctas = 0;
     for (int q = 0; q < B.n; ++q) {
       B.a[q] = a[q0 + q];
       B.cta0[q] = ctas;
-      ctas += blocks(B.a[q]);
+      int b = blocks(B.a[q]);
+      const double w = (double)work(B.a[q]);
+      if (w > 0.0 && wsum > 0.0) {
+        const int share = (int)std::ceil(kBatchBlocks * w / wsum);
+        b = std::max(1, std::min(b, share));
+      }
+      ctas += b;
     }
     B.cta0[B.n] = ctas;
     if (ctas > 0) {
@@ -851,6 +866,7 @@ int clamp_blocks(int n, int cap) {
 
 cudaError_t launch_jacobi_batch(cudaStream_t st, const JacobiItem* a, int n) {
   return flat_batches(a, n, [](const JacobiItem& it) { return clamp_blocks(it.g.nn, 4096); },
+                      [](const JacobiItem& it) { return it.g.nn; },
                       [st](const FlatBatch<JacobiItem>& B, int ctas) {
                         pdl_launch(k_jacobi_batch, ctas, 256, 0, st, B);
                       });
@@ -858,6 +874,7 @@ cudaError_t launch_jacobi_batch(cudaStream_t st, const JacobiItem* a, int n) {
 
 cudaError_t launch_restrict_batch(cudaStream_t st, const RestrictItem* a, int n) {
   return flat_batches(a, n, [](const RestrictItem& it) { return clamp_blocks(it.gc.nn, 8192); },
+                      [](const RestrictItem& it) { return it.gc.nn; },
                       [st](const FlatBatch<RestrictItem>& B, int ctas) {
                         pdl_launch(k_restrict_batch, ctas, 256, 0, st, B);
                       });
@@ -865,6 +882,7 @@ cudaError_t launch_restrict_batch(cudaStream_t st, const RestrictItem* a, int n)
 
 cudaError_t launch_prolong_batch(cudaStream_t st, const ProlongItem* a, int n) {
   return flat_batches(a, n, [](const ProlongItem& it) { return clamp_blocks(it.gf.nn, 16384); },
+                      [](const ProlongItem& it) { return it.gf.nn; },
                       [st](const FlatBatch<ProlongItem>& B, int ctas) {
                         pdl_launch(k_prolong_batch, ctas, 256, 0, st, B);
                       });
@@ -875,6 +893,7 @@ cudaError_t launch_coarse_apply_batch(cudaStream_t st, const CoarseItem* a, int 
   for (int q = 0; q < n; ++q) nmax = std::max(nmax, a[q].n);
   const size_t smem = sizeof(float) * (size_t)nmax;
   return flat_batches(a, n, [](const CoarseItem&) { return 1; },
+                      [](const CoarseItem&) { return 0; },
                       [st, smem](const FlatBatch<CoarseItem>& B, int ctas) {
                         pdl_launch(k_coarse_apply_batch, ctas, 1024, smem, st, B);
                       });
@@ -882,6 +901,7 @@ cudaError_t launch_coarse_apply_batch(cudaStream_t st, const CoarseItem* a, int 
 
 cudaError_t launch_cg_xr_batch(cudaStream_t st, const CgXrItem* a, int n) {
   return flat_batches(a, n, [](const CgXrItem& it) { return cg_xr_blocks(it.n); },
+                      [](const CgXrItem& it) { return it.n; },
                       [st](const FlatBatch<CgXrItem>& B, int ctas) {
                         pdl_launch(k_cg_xr_batch, ctas, kRedThreads, 0, st, B);
                       });
@@ -889,6 +909,7 @@ cudaError_t launch_cg_xr_batch(cudaStream_t st, const CgXrItem* a, int n) {
 
 cudaError_t launch_cg_p_batch(cudaStream_t st, const CgPItem* a, int n) {
   return flat_batches(a, n, [](const CgPItem& it) { return clamp_blocks(it.n, 8 * 152); },
+                      [](const CgPItem& it) { return it.n; },
                       [st](const FlatBatch<CgPItem>& B, int ctas) {
                         pdl_launch(k_cg_p_batch, ctas, 256, 0, st, B);
                       });
