@@ -432,10 +432,12 @@ tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_star
     }
     const int dk = (dot && last) ? 2 : 0;
     if (s == 0 && zero_start) {
-      if (!first_done) {  // (else the restriction that produced b already wrote X)
+      if (!first_done) {  // (else the restriction or the CG update already wrote X)
         LevelTimer lt(G, l);
+        // on the finest level of a fused grid this also keeps D^-1 for the CG update
+        T* invd = (l == 0 && G->fuse_j0) ? (T*)G->invd : nullptr;
         CK(launch_jacobi<T>(G->stream, Lv.g, (const T*)Lv.s, Lv.mask, b, (T)c2, k0d, *X,
-                            nullptr, G->partials, G->counter, G->sc, dk, skip));
+                            nullptr, G->partials, G->counter, G->sc, dk, skip, invd));
         G->launches += 1;
       }
       // X = x1; x0 = 0 is implicit: the next step is told not to read Y
@@ -508,7 +510,7 @@ tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int
 
 // z = M r with rz/beta from the fused dot
 template <typename T>
-tomo_status precond(tomo_grid* G, const T* r, T** z) {
+tomo_status precond(tomo_grid* G, const T* r, T** z, bool first_done0 = false) {
   const int* skip = &G->sc->done;
   if (G->d.precond == TOMO_PRECOND_JACOBI) {
     auto& L0 = G->L[0];
@@ -518,7 +520,7 @@ tomo_status precond(tomo_grid* G, const T* r, T** z) {
     *z = (T*)L0.x;
     return TOMO_OK;
   }
-  return vcycle<T>(G, 0, r, z, true, skip);
+  return vcycle<T>(G, 0, r, z, true, skip, first_done0);
 }
 
 // One PCG iteration: q = A p (alpha), x/r update (convergence test), residual replacement
@@ -539,7 +541,11 @@ tomo_status enqueue_iteration(tomo_grid* G) {
   a.dot_kind = 1;
   a.skip = &G->sc->done;
   TRY(march<T>(G, 0, M_APPLY, a));
-  CK(launch_cg_xr<T>(G->stream, n, xhi, xlo, r, p, q, G->partials, G->counter, G->sc));
+  // fused grids: the update also writes the next V-cycle's first finest-level step
+  T* x1 = G->fuse_j0 ? (T*)G->L[0].x : nullptr;
+  const T c2 = (T)(1.0 / cheb(G).theta);
+  CK(launch_cg_xr<T>(G->stream, n, xhi, xlo, r, p, q, G->partials, G->counter, G->sc, x1,
+                     (const T*)G->invd, c2));
   G->launches += 1;
   if (G->d.rr_every > 0) {
     // residual replacement r = f - K x on iterations it % rr_every == 0 (device gate), in
@@ -562,11 +568,16 @@ tomo_status enqueue_iteration(tomo_grid* G) {
       rr.yf = r;
       rr.skip = &G->sc->done;
       rr.gate = G->sc;
+      if (G->fuse_j0) {  // the first step follows the replaced residual
+        rr.x1f = (float*)x1;
+        rr.invdf = (const float*)G->invd;
+        rr.c2f = (float)c2;
+      }
       TRY(march<double>(G, 0, M_RESID, rr, G->s64));
     }
   }
   T* z = nullptr;
-  TRY(precond<T>(G, r, &z));
+  TRY(precond<T>(G, r, &z, G->fuse_j0));
   CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
   G->launches += 1;
   return TOMO_OK;
@@ -1290,6 +1301,7 @@ void free_grid(tomo_grid* G) {
   G->loop_cache.clear();
   F(G->load_idx);
   F(G->load_val);
+  F(G->invd);
   F(G->adj_T);
   F(G->adj64);
   F(G->adj_hi);
@@ -1397,6 +1409,10 @@ tomo_status create_impl(tomo_grid* G) {
       CK(cudaMemcpyAsync(Lv.tile_fixed, fl.data(), fl.size(), cudaMemcpyHostToDevice,
                          G->stream));
     }
+  }
+  if (G->coarse_n > 0 && sizeof(T) == 4) {
+    TRY(dalloc(G, &G->invd, sizeof(T) * (size_t)g.nn));
+    G->fuse_j0 = true;
   }
   if (G->coarse_n > 0) {
     TRY(dalloc(G, &G->coarseA, sizeof(T) * (size_t)G->coarse_n * G->coarse_n));

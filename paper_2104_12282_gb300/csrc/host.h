@@ -62,6 +62,11 @@ struct MarchArgs {
   const float* xf_hi;
   const float* xf_lo;
   float* yf;
+  // JOIN RESID only, optional: also the zero-start Jacobi step from the new residual,
+  // x1f = c2f * yf * invdf[node] (the finest level's first smoothing step, see k_cg_xr)
+  float* x1f;
+  const float* invdf;
+  float c2f;
 };
 
 // Table of a batched FP64 residual launch (gated residual replacement of several FP32
@@ -215,7 +220,8 @@ cudaError_t launch_march(cudaStream_t st, int mode, const MarchArgs<T>& a, const
 template <typename T>
 cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* mask, const T* b,
                           T c2, T k0diag, T* x1, T* x0zero, double* partials,
-                          unsigned* counter, CgScalars* sc, int dot_kind, const int* skip);
+                          unsigned* counter, CgScalars* sc, int dot_kind, const int* skip,
+                          T* invd = nullptr);
 template <typename T>
 cudaError_t launch_restrict(cudaStream_t st, Geom gf, Geom gc, const T* rf, T* rc,
                             const uint8_t* mask_c, const int* skip, T* x1 = nullptr,
@@ -235,7 +241,8 @@ cudaError_t launch_coarse_apply(cudaStream_t st, int n, const T* Ainv, const T* 
 // CG recurrences.  xlo != nullptr selects the float-pair iterate (x = xhi + xlo).
 template <typename T>
 cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* p, const T* q,
-                         double* partials, unsigned* counter, CgScalars* sc);
+                         double* partials, unsigned* counter, CgScalars* sc, T* x1 = nullptr,
+                         const T* invd = nullptr, T c2 = T(0));
 template <typename T>
 cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc);
 cudaError_t launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, CgScalars* sc);
@@ -379,6 +386,11 @@ struct tomo_grid {
   void* adj_hi = nullptr;      // adjoint state lambda (pair on FP32 grids)
   void* adj_lo = nullptr;
   bool use_graph = true;
+  // FP32 multigrid grids: the CG x/r update also writes the finest level's zero-start
+  // Jacobi step x1 = c2 D^-1 r (D^-1 per node in invd, from the first V-cycle of the solve),
+  // so the V-cycles inside the loop skip that launch
+  bool fuse_j0 = false;
+  void* invd = nullptr;
   int64_t gen = 0;  // bumped when settings baked into captured loops change (smoother)
   // captured loops (load slot) of smoother settings used before: (fine, coarse, ratio)
   struct CachedLoop {

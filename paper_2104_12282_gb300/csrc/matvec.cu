@@ -282,8 +282,13 @@ __device__ __forceinline__ void march_body(const MarchArgs<T>& A, const ElemCons
           if (DOT) dot += (double)(A0[c] * yv);
         } else if (MODE == M_RESID) {
           const T rv = fx ? T(0) : (bv[c] - out[c]);
-          if constexpr (JOIN) A.yf[idx] = (float)rv;
-          else A.y[idx] = rv;
+          if constexpr (JOIN) {
+            const float rf = (float)rv;
+            A.yf[idx] = rf;
+            if (A.x1f) A.x1f[idx] = A.c2f * rf * A.invdf[n_out];
+          } else {
+            A.y[idx] = rv;
+          }
         } else {
           const T dg = C.k0diag * Stot;
           const T w = dg > T(0) ? (bv[c] - out[c]) / dg : T(0);

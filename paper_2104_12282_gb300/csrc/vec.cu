@@ -27,7 +27,8 @@ __device__ __forceinline__ void jacobi_body(int vb, int vnb, Geom g, const T* __
                                             const T* __restrict__ b, T c2, T k0diag,
                                             T* __restrict__ x1, T* __restrict__ x0,
                                             double* partials, unsigned* counter,
-                                            CgScalars* sc, const int* skip) {
+                                            CgScalars* sc, const int* skip,
+                                            T* __restrict__ invd = nullptr) {
   PDL_ENTER();
   if (skipped(skip)) return;
   double dot = 0.0;       // FP64 grids
@@ -45,6 +46,7 @@ __device__ __forceinline__ void jacobi_body(int vb, int vnb, Geom g, const T* __
     const T S = wza * (wya * row(za + ya) + wyb * row(za + yb)) +
                 wzb * (wya * row(zb + ya) + wyb * row(zb + yb));
     const T dg = k0diag * S;
+    if (invd) invd[n] = dg > T(0) ? T(1) / dg : T(0);  // kept for the fused later steps
     const unsigned mk = mask[n];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -75,24 +77,25 @@ template <typename T, bool DOT>
 __global__ void k_jacobi(Geom g, const T* __restrict__ s, const uint8_t* __restrict__ mask,
                          const T* __restrict__ b, T c2, T k0diag, T* __restrict__ x1,
                          T* __restrict__ x0, double* partials, unsigned* counter, CgScalars* sc,
-                         const int* skip) {
+                         const int* skip, T* __restrict__ invd) {
   jacobi_body<T, DOT>(blockIdx.x, gridDim.x, g, s, mask, b, c2, k0diag, x1, x0, partials,
-                      counter, sc, skip);
+                      counter, sc, skip, invd);
 }
 
 template <typename T>
 cudaError_t launch_jacobi(cudaStream_t st, Geom g, const T* s, const uint8_t* mask, const T* b,
                           T c2, T k0diag, T* x1, T* x0zero, double* partials,
-                          unsigned* counter, CgScalars* sc, int dot_kind, const int* skip) {
+                          unsigned* counter, CgScalars* sc, int dot_kind, const int* skip,
+                          T* invd) {
   int blocks = (g.nn + 255) / 256;
   if (dot_kind) {
     if (blocks > kRedBlocks) blocks = kRedBlocks;
-    pdl_launch(k_jacobi<T, true>, blocks, 256, 0, st, g, s, mask, b, c2, k0diag, x1, x0zero, partials,
-                                              counter, sc, skip);
+    pdl_launch(k_jacobi<T, true>, blocks, 256, 0, st, g, s, mask, b, c2, k0diag, x1, x0zero,
+               partials, counter, sc, skip, invd);
   } else {
     if (blocks > 4096) blocks = 4096;
-    pdl_launch(k_jacobi<T, false>, blocks, 256, 0, st, g, s, mask, b, c2, k0diag, x1, x0zero, nullptr,
-                                               nullptr, nullptr, skip);
+    pdl_launch(k_jacobi<T, false>, blocks, 256, 0, st, g, s, mask, b, c2, k0diag, x1, x0zero,
+               nullptr, nullptr, nullptr, skip, invd);
   }
   return cudaGetLastError();
 }
@@ -450,12 +453,16 @@ __device__ __forceinline__ void pair_axpy(float alpha, float pv, float& hi, floa
   hi = hi2;
 }
 
+// x1 != nullptr: also the finest level's zero-start Jacobi step from the new residual,
+// x1[c nn + m] = c2 r[c nn + m] invd[m] (the first smoothing step of the next V-cycle).
 template <typename T, bool PAIRX>
 __device__ __forceinline__ void cg_xr_body(int vb, int vnb, int n, T* __restrict__ xhi,
                                            T* __restrict__ xlo, T* __restrict__ r,
                                            const T* __restrict__ p, const T* __restrict__ q,
                                            double* partials, unsigned* counter,
-                                           CgScalars* sc) {
+                                           CgScalars* sc, T* __restrict__ x1 = nullptr,
+                                           const T* __restrict__ invd = nullptr, T c2 = T(0)) {
+  const int nn = n / 3;
   PDL_ENTER();
   if (sc->done) return;
   const double alpha_d = sc->alpha;
@@ -491,6 +498,19 @@ __device__ __forceinline__ void cg_xr_body(int vb, int vnb, int n, T* __restrict
       rv.z = rv.z - alpha * qv.z;
       rv.w = rv.w - alpha * qv.w;
       reinterpret_cast<float4*>(r)[v] = rv;
+      if (x1) {
+        const int i = v << 2;
+        int m = i - (i / nn) * nn;   // node of DOF i; the next three follow (wrapping at nn)
+        float4 xv;
+        xv.x = c2 * rv.x * invd[m];
+        m = (m + 1 == nn) ? 0 : m + 1;
+        xv.y = c2 * rv.y * invd[m];
+        m = (m + 1 == nn) ? 0 : m + 1;
+        xv.z = c2 * rv.z * invd[m];
+        m = (m + 1 == nn) ? 0 : m + 1;
+        xv.w = c2 * rv.w * invd[m];
+        reinterpret_cast<float4*>(x1)[v] = xv;
+      }
       accf.add(__fmul_rn(rv.x, rv.x));
       accf.add(__fmul_rn(rv.y, rv.y));
       accf.add(__fmul_rn(rv.z, rv.z));
@@ -510,6 +530,7 @@ __device__ __forceinline__ void cg_xr_body(int vb, int vnb, int n, T* __restrict
     }
     const T rv = r[i] - alpha * q[i];
     r[i] = rv;
+    if (x1) x1[i] = c2 * rv * invd[i - (i / nn) * nn];
     if constexpr (sizeof(T) == 4) accf.add(__fmul_rn(rv, rv));
     else acc += rv * rv;
   }
@@ -526,8 +547,10 @@ __device__ __forceinline__ void cg_xr_body(int vb, int vnb, int n, T* __restrict
 template <typename T, bool PAIRX>
 __global__ void k_cg_xr(int n, T* __restrict__ xhi, T* __restrict__ xlo, T* __restrict__ r,
                         const T* __restrict__ p, const T* __restrict__ q, double* partials,
-                        unsigned* counter, CgScalars* sc) {
-  cg_xr_body<T, PAIRX>(blockIdx.x, gridDim.x, n, xhi, xlo, r, p, q, partials, counter, sc);
+                        unsigned* counter, CgScalars* sc, T* __restrict__ x1,
+                        const T* __restrict__ invd, T c2) {
+  cg_xr_body<T, PAIRX>(blockIdx.x, gridDim.x, n, xhi, xlo, r, p, q, partials, counter, sc, x1,
+                       invd, c2);
 }
 
 // Blocks of the x/r update of an n-vector: enough for 16-byte accesses at HBM rate on large
@@ -541,18 +564,19 @@ int cg_xr_blocks(int n) {
 
 template <typename T>
 cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* p, const T* q,
-                         double* partials, unsigned* counter, CgScalars* sc) {
+                         double* partials, unsigned* counter, CgScalars* sc, T* x1,
+                         const T* invd, T c2) {
   const int blocks = cg_xr_blocks(n);
   if (xlo) {
     if constexpr (sizeof(T) == 4) {
       pdl_launch(k_cg_xr<T, true>, blocks, kRedThreads, 0, st, n, xhi, xlo, r, p, q, partials,
-                 counter, sc);
+                 counter, sc, x1, invd, c2);
       return cudaGetLastError();
     }
     return cudaErrorInvalidValue;
   }
   pdl_launch(k_cg_xr<T, false>, blocks, kRedThreads, 0, st, n, xhi, nullptr, r, p, q, partials,
-             counter, sc);
+             counter, sc, x1, invd, c2);
   return cudaGetLastError();
 }
 
@@ -987,7 +1011,7 @@ cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo,
 #define INST(T)                                                                               \
   template cudaError_t launch_jacobi<T>(cudaStream_t, Geom, const T*, const uint8_t*, const T*, \
                                         T, T, T*, T*, double*, unsigned*, CgScalars*, int,     \
-                                        const int*);                                         \
+                                        const int*, T*);                                     \
   template cudaError_t launch_restrict<T>(cudaStream_t, Geom, Geom, const T*, T*,             \
                                           const uint8_t*, const int*, T*, const T*, T, T);   \
   template cudaError_t launch_prolong_add<T>(cudaStream_t, Geom, Geom, const T*, T*,          \
@@ -998,7 +1022,7 @@ cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo,
   template cudaError_t launch_coarse_apply<T>(cudaStream_t, int, const T*, const T*, const T*, \
                                               T*, const int*);                               \
   template cudaError_t launch_cg_xr<T>(cudaStream_t, int, T*, T*, T*, const T*, const T*,     \
-                                       double*, unsigned*, CgScalars*);                      \
+                                       double*, unsigned*, CgScalars*, T*, const T*, T);     \
   template cudaError_t launch_cg_p<T>(cudaStream_t, int, T*, const T*, CgScalars*);           \
   template cudaError_t launch_mask_copy<T>(cudaStream_t, Geom, const T*, const uint8_t*, T*);
 INST(float)

@@ -425,3 +425,21 @@ def test_maxit_reports_no_convergence():
         with pytest.raises(tomo.TomoError) as e:
             g.gradient(z, dc)
     assert e.value.status == 3
+
+
+@pytest.mark.parametrize("rr", [1, 3])
+def test_multigrid_with_frequent_residual_replacement(rr):
+    """FP32 multigrid-PCG whose FP64 residual replacement runs every rr iterations (it then
+    also renews the finest level's first smoothing step): same solution as the oracle."""
+    p = P.cantilever(24, 12, 12)
+    rho = f32(P.random_field(p.dims, 19, 0.05, 1.0))
+    m = topopt.Model(p)
+    ref = m.gradient(rho, "direct")
+    with tomo.Grid.from_problem(p, precision=tomo.FP32, rr_every=rr) as g:
+        z = T(rho, tomo.FP32)
+        dc = torch.empty_like(z)
+        c, info = g.gradient(z, dc)
+        torch.cuda.synchronize()
+    assert info.status == 0 and info.iters > rr
+    assert abs(c / ref["c"] - 1.0) <= 1e-5
+    assert guarded_rel(H(dc), ref["dcdz"]) <= 1e-4
