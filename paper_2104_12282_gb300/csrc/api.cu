@@ -921,7 +921,7 @@ template <typename T>
 tomo_status do_solve(tomo_grid* G, const T* rho, T* u, tomo_solve_info* info) {
   if (!rho || !u) return fail(G, TOMO_EINVAL, "null array");
   const size_t be = sizeof(T) * (size_t)G->g.nel, bn = sizeof(T) * 3 * (size_t)G->g.nn;
-  const void *drho, *du;
+  const void *drho = nullptr, *du = nullptr;
   bool h1, h2;
   TRY(stage_in(G, rho, be, 0, &drho, &h1));
   TRY(stage_in(G, u, bn, 2, &du, &h2));
@@ -987,7 +987,7 @@ template <typename T>
 tomo_status do_sensitivity(tomo_grid* G, const T* rho, const T* u, double* compliance, T* dc) {
   if (!rho || !u) return fail(G, TOMO_EINVAL, "null array");
   const size_t be = sizeof(T) * (size_t)G->g.nel, bn = sizeof(T) * 3 * (size_t)G->g.nn;
-  const void *drho, *du;
+  const void *drho = nullptr, *du = nullptr;
   void* ddc = nullptr;
   bool h1, h2, h3 = false;
   TRY(stage_in(G, rho, be, 0, &drho, &h1));
