@@ -338,7 +338,8 @@ tomo_status tomo_batch_gradient(tomo_batch* batch, const float* const* z, double
 tomo_status tomo_batch_destroy(tomo_batch* batch);
 const char* tomo_batch_last_error(const tomo_batch* batch);
 
-/* Request loop (serving): gradient requests on design domains of different sizes, run
+/* Request loop (serving): gradient and optimisation requests on design domains of
+ * different sizes, run
  * by `workers` threads with one CUDA stream each, with grids kept resident on the device
  * per session and admission by device memory.  The paper has no counterpart (it optimises
  * one design at a time); the arithmetic of each request is tomo_gradient's.
@@ -349,6 +350,14 @@ const char* tomo_batch_last_error(const tomo_batch* batch);
  *   grid for this request only).  dcdz (N_el) and dvdz (N_el, may be NULL) are host
  *   arrays owned by the caller, written before tomo_server_wait returns the ticket.
  *   TOMO_ENOMEM if the request alone exceeds the budget.
+ * tomo_server_submit_optimize: an optimisation request, iters (>= 1) OC iterations from
+ *   the design z on the request's grid, each tomo_gradient (solves warm-started from the
+ *   previous one) then tomo_oc_step with volfrac and move; the design stays on the device
+ *   for the whole run and the final one is written to z_out (host, N_el, caller-owned, may
+ *   be the z array) before tomo_server_wait returns.  result.compliance and result.info
+ *   are those of the last gradient (the design before the last update).  Same sessions,
+ *   admission and errors as tomo_server_submit (the run's four N_el buffers are added to
+ *   the footprint).
  * tomo_server_wait: blocks until the ticket is done, fills *result, forgets the ticket.
  * Requests start in arrival order among those whose memory can be found (idle resident
  * grids of other sessions are evicted least recently used first); a request starts as
@@ -375,6 +384,10 @@ typedef struct {
 tomo_status tomo_server_create(int32_t workers, uint64_t budget_bytes, tomo_server** out);
 tomo_status tomo_server_submit(tomo_server* server, const tomo_grid_desc* desc, int64_t session,
                                const float* z, float* dcdz, float* dvdz, int64_t* ticket);
+tomo_status tomo_server_submit_optimize(tomo_server* server, const tomo_grid_desc* desc,
+                                        int64_t session, const float* z, int32_t iters,
+                                        double volfrac, double move, float* z_out,
+                                        int64_t* ticket);
 tomo_status tomo_server_wait(tomo_server* server, int64_t ticket, tomo_result* result);
 tomo_status tomo_server_get_stats(tomo_server* server, tomo_server_stats* stats);
 tomo_status tomo_server_destroy(tomo_server* server);

@@ -1,4 +1,4 @@
-// Request loop for gradient requests on design domains of different sizes.
+// Request loop for gradient and optimisation requests on design domains of different sizes.
 //
 // The paper optimises one design at a time; serving many designs at once needs a runtime
 // around the exact-gradient path.  This one is built on the public C ABI only:
@@ -46,6 +46,10 @@ struct Request {
   std::vector<float> z;
   float* dcdz = nullptr;  // caller-owned host outputs
   float* dvdz = nullptr;
+  // optimisation request (iters > 0): OC iterations from z, final design into z_out
+  int iters = 0;
+  double volfrac = 0.0, move = 0.0;
+  float* z_out = nullptr;
   size_t est_bytes = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
   tomo_result res{};
@@ -116,6 +120,40 @@ struct tomo_server {
     return slots.back().get();
   }
 
+  // An optimisation request on grid g (stream st): the design stays on the device for the
+  // whole run (gradient with warm-started solves, then the OC update, iters times); the
+  // compliance and solve info of the last gradient go to the result, the final design to
+  // r.z_out.  The grid's warm-start setting is restored (off) afterwards.
+  tomo_status optimise(tomo_grid* g, cudaStream_t st, Request& r) {
+    const size_t ne = r.z.size();
+    float* buf = nullptr;
+    if (cudaMallocAsync((void**)&buf, sizeof(float) * 4 * ne, st) != cudaSuccess) {
+      cudaGetLastError();
+      return TOMO_ENOMEM;
+    }
+    float *z = buf, *zn = buf + ne, *dc = buf + 2 * ne, *dv = buf + 3 * ne;
+    tomo_status s = TOMO_OK;
+    if (cudaMemcpyAsync(z, r.z.data(), sizeof(float) * ne, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      s = TOMO_ECUDA;
+    if (s == TOMO_OK) s = tomo_set_warm_start(g, 1);
+    for (int k = 0; k < r.iters && s == TOMO_OK; ++k) {
+      s = tomo_gradient(g, z, &r.res.compliance, dc, dv, &r.res.info);
+      double change = 0.0;
+      if (s == TOMO_OK) s = tomo_oc_step(g, z, dc, dv, r.volfrac, r.move, zn, &change);
+      std::swap(z, zn);
+    }
+    tomo_set_warm_start(g, 0);
+    if (s == TOMO_OK &&
+        cudaMemcpyAsync(r.z_out, z, sizeof(float) * ne, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+      s = TOMO_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess && s == TOMO_OK) s = TOMO_ECUDA;
+    cudaFreeAsync(buf, st);
+    cudaGetLastError();
+    return s;
+  }
+
   void work(int w) {
     cudaStream_t st = streams[w];
     for (;;) {
@@ -170,7 +208,10 @@ struct tomo_server {
       } else {
         tomo_set_stream(g, st);
       }
-      if (s == TOMO_OK) {
+      if (s == TOMO_OK && r->iters > 0) {
+        s = optimise(g, st, *r);
+        if (s != TOMO_OK) note(tomo_last_error(g));
+      } else if (s == TOMO_OK) {
         s = tomo_gradient(g, r->z.data(), &r->res.compliance, r->dcdz, r->dvdz, &r->res.info);
         if (s == TOMO_OK && cudaStreamSynchronize(st) != cudaSuccess) {
           cudaGetLastError();
@@ -208,6 +249,55 @@ struct tomo_server {
   }
 };
 
+namespace {
+
+tomo_status submit_request(tomo_server* S, const tomo_grid_desc* desc, int64_t session,
+                           const float* z, float* dcdz, float* dvdz, int iters, double volfrac,
+                           double move, float* z_out, int64_t* ticket) {
+  if (desc->precision != TOMO_FP32) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->err = "the request loop serves FP32 grids";
+    return TOMO_EINVAL;
+  }
+  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1) return TOMO_EINVAL;
+  auto r = std::make_unique<Request>();
+  r->session = session;
+  r->desc = *desc;
+  const size_t nn = (size_t)(desc->nx + 1) * (desc->ny + 1) * (desc->nz + 1);
+  const size_t ne = (size_t)desc->nx * desc->ny * desc->nz;
+  r->fixed.assign(desc->fixed_dof, desc->fixed_dof + 3 * nn);
+  r->f.assign(desc->f, desc->f + 3 * nn);
+  r->z.assign(z, z + ne);
+  r->desc.fixed_dof = nullptr;
+  r->desc.f = nullptr;
+  r->desc.stream = nullptr;
+  r->dcdz = dcdz;
+  r->dvdz = dvdz;
+  r->iters = iters;
+  r->volfrac = volfrac;
+  r->move = move;
+  r->z_out = z_out;
+  size_t est = 0;
+  tomo_estimate_device_bytes(desc, &est);
+  if (iters > 0) est += sizeof(float) * 4 * ne;  // the run's design and gradient buffers
+  r->est_bytes = est;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (est > S->budget) {
+    S->err = "request needs more device memory than the server's budget";
+    return TOMO_ENOMEM;
+  }
+  r->t_submit = Clock::now();
+  r->ticket = S->next_ticket++;
+  *ticket = r->ticket;
+  S->queue.push_back(r->ticket);
+  S->reqs[r->ticket] = std::move(r);
+  S->stats.submitted += 1;
+  S->cv_work.notify_one();
+  return TOMO_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 tomo_status tomo_server_create(int32_t workers, uint64_t budget_bytes, tomo_server** out) {
@@ -238,44 +328,22 @@ tomo_status tomo_server_create(int32_t workers, uint64_t budget_bytes, tomo_serv
   return TOMO_OK;
 }
 
+
 tomo_status tomo_server_submit(tomo_server* S, const tomo_grid_desc* desc, int64_t session,
                                const float* z, float* dcdz, float* dvdz, int64_t* ticket) {
   if (!S || !desc || !z || !dcdz || !ticket || !desc->fixed_dof || !desc->f) return TOMO_EINVAL;
-  if (desc->precision != TOMO_FP32) {
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->err = "the request loop serves FP32 grids";
+  return submit_request(S, desc, session, z, dcdz, dvdz, 0, 0.0, 0.0, nullptr, ticket);
+}
+
+tomo_status tomo_server_submit_optimize(tomo_server* S, const tomo_grid_desc* desc,
+                                        int64_t session, const float* z, int32_t iters,
+                                        double volfrac, double move, float* z_out,
+                                        int64_t* ticket) {
+  if (!S || !desc || !z || !z_out || !ticket || !desc->fixed_dof || !desc->f || iters < 1 ||
+      !(volfrac > 0.0 && volfrac <= 1.0) || !(move > 0.0))
     return TOMO_EINVAL;
-  }
-  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1) return TOMO_EINVAL;
-  auto r = std::make_unique<Request>();
-  r->session = session;
-  r->desc = *desc;
-  const size_t nn = (size_t)(desc->nx + 1) * (desc->ny + 1) * (desc->nz + 1);
-  const size_t ne = (size_t)desc->nx * desc->ny * desc->nz;
-  r->fixed.assign(desc->fixed_dof, desc->fixed_dof + 3 * nn);
-  r->f.assign(desc->f, desc->f + 3 * nn);
-  r->z.assign(z, z + ne);
-  r->desc.fixed_dof = nullptr;
-  r->desc.f = nullptr;
-  r->desc.stream = nullptr;
-  r->dcdz = dcdz;
-  r->dvdz = dvdz;
-  size_t est = 0;
-  tomo_estimate_device_bytes(desc, &est);
-  r->est_bytes = est;
-  std::lock_guard<std::mutex> lk(S->mu);
-  if (est > S->budget) {
-    S->err = "request needs more device memory than the server's budget";
-    return TOMO_ENOMEM;
-  }
-  r->t_submit = Clock::now();
-  r->ticket = S->next_ticket++;
-  *ticket = r->ticket;
-  S->queue.push_back(r->ticket);
-  S->reqs[r->ticket] = std::move(r);
-  S->stats.submitted += 1;
-  S->cv_work.notify_one();
-  return TOMO_OK;
+  return submit_request(S, desc, session, z, nullptr, nullptr, iters, volfrac, move, z_out,
+                        ticket);
 }
 
 tomo_status tomo_server_wait(tomo_server* S, int64_t ticket, tomo_result* result) {

@@ -93,6 +93,9 @@ def _load():
                                     ctypes.POINTER(ctypes.c_void_p)]),
         "tomo_server_submit": (st, [P, ctypes.POINTER(GridDesc), ctypes.c_int64, P, P, P,
                                     ctypes.POINTER(ctypes.c_int64)]),
+        "tomo_server_submit_optimize": (st, [P, ctypes.POINTER(GridDesc), ctypes.c_int64, P,
+                                             ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                             P, ctypes.POINTER(ctypes.c_int64)]),
         "tomo_server_wait": (st, [P, ctypes.c_int64, ctypes.POINTER(Result)]),
         "tomo_server_get_stats": (st, [P, ctypes.POINTER(ServerStats)]),
         "tomo_server_destroy": (st, [P]),
@@ -175,6 +178,7 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["tomo_default_desc", "tomo_create_grid", "tomo_destroy_grid", "tomo_set_stream",
             "tomo_set_warm_start", "tomo_set_smoother", "tomo_get_smoother",
+            "tomo_server_submit_optimize",
             "tomo_autotune_smoother", "tomo_autotune_smoother_d",
             "tomo_server_create", "tomo_server_submit",
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
@@ -636,8 +640,27 @@ class Server:
         self._pending[t.value] = (dc, dv, keep, zz)
         return t.value
 
+    def submit_optimize(self, p, iters, z=None, session=-1, volfrac=None, move=None):
+        """Queue an optimisation request: `iters` OC iterations of problem p from design z
+        (default p.z0) with p's volume fraction and move limit unless given; ``wait``
+        returns (Result, final design, None)."""
+        d, keep = _problem_desc(p, FP32)
+        zz = np.ascontiguousarray(np.asarray(p.z0 if z is None else z, np.float32))
+        zo = np.empty(p.n_el, np.float32)
+        t = ctypes.c_int64()
+        st = lib().tomo_server_submit_optimize(
+            self._h, ctypes.byref(d), int(session), zz.ctypes.data_as(ctypes.c_void_p),
+            int(iters), float(p.volfrac if volfrac is None else volfrac),
+            float(p.move if move is None else move), zo.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(t))
+        if st != 0:
+            raise TomoError(st, lib().tomo_server_last_error(self._h).decode())
+        self._pending[t.value] = (zo, None, keep, zz)
+        return t.value
+
     def wait(self, ticket):
-        """Returns (Result, dcdz, dvdz) for a ticket."""
+        """Returns (Result, dcdz, dvdz) for a gradient ticket, (Result, final design, None)
+        for an optimisation ticket."""
         r = Result()
         st = lib().tomo_server_wait(self._h, int(ticket), ctypes.byref(r))
         if st != 0:

@@ -90,3 +90,43 @@ def test_a_failing_request_does_not_disturb_the_others():
         assert r.status == 0
         c, dc0, _ = _alone(p)
         assert r.compliance == c and np.array_equal(dc, dc0)
+
+
+def test_optimisation_requests_equal_the_loop_alone():
+    """Optimisation requests (OC iterations with warm-started solves on the request's grid)
+    give bitwise the final design and last compliance of the same loop run alone; a gradient
+    request that follows on the same session grid still gives its cold result alone."""
+    ps = [P.served_request(11, i, (6, 12)) for i in range(4)]
+    iters = 6
+    alone = []
+    for p in ps:
+        with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+            g.set_warm_start(True)
+            z = torch.tensor(np.asarray(p.z0, np.float32), device="cuda")
+            dc, dv, zn = torch.empty_like(z), torch.empty_like(z), torch.empty_like(z)
+            for _ in range(iters):
+                c, info = g.gradient(z, dc, dv)
+                g.oc_step(z, dc, dv, p.volfrac, p.move, zn)
+                z, zn = zn, z
+            torch.cuda.synchronize()
+            alone.append((c, info.iters, z.cpu().numpy()))
+    with tomo.Server(workers=3, budget_bytes=1 << 30) as srv:
+        tickets = [srv.submit_optimize(p, iters, session=(i if i % 2 else -1))
+                   for i, p in enumerate(ps)]
+        tickets.append(srv.submit(ps[1], session=1))
+        res = [srv.wait(t) for t in tickets]
+    for (c, it, z), (r, zo, _) in zip(alone, res[:4]):
+        assert r.status == 0, r.message
+        assert r.compliance == c and r.info.iters == it
+        assert np.array_equal(zo, z)
+    r, dc, _ = res[4]
+    c0, dc0, _ = _alone(ps[1])
+    assert r.status == 0 and r.compliance == c0 and np.array_equal(dc, dc0)
+
+
+def test_bad_optimisation_requests_are_rejected():
+    p = P.served_request(12, 0, (6, 8))
+    with tomo.Server(workers=1, budget_bytes=1 << 30) as srv:
+        for kw in (dict(iters=0), dict(iters=3, volfrac=0.0), dict(iters=3, move=0.0)):
+            with pytest.raises(tomo.TomoError):
+                srv.submit_optimize(p, **kw)
