@@ -2,7 +2,7 @@
 gradient requests on 2n x n x n domains of different sizes (seeded supports, loads and
 density fields), device-resident grids, admission under a device-memory budget; reports
 p50/p99 latency and throughput, next to serial FP64 GPU gradients on a sample of the same
-requests.  --rate 0 submits every request at once (saturation: the throughput is then the
+requests.  --opt-frac mixes in optimisation requests (--opt-iters OC iterations each).  --rate 0 submits every request at once (saturation: the throughput is then the
 request loop's capacity).
 
     python -m paper_2104_12282_gb300.serve --requests 1000 --rate 200 --budget-gb 150
@@ -27,27 +27,29 @@ def percentile(xs, q):
 
 
 def run_stream(n_requests=1000, rate=200.0, seed=0, workers=16, budget_bytes=150 << 30,
-               n_range=(12, 64), serial_sample=12):
+               n_range=(12, 64), serial_sample=12, opt_frac=0.0, opt_iters=10):
     reqs = [P.served_request(seed, i, n_range) for i in range(n_requests)]
     if rate > 0:
         gaps = np.random.default_rng([seed, 1]).exponential(1.0 / rate, size=n_requests)
         arrive = np.cumsum(gaps)
     else:   # saturation
         arrive = np.zeros(n_requests)
-    lat, qms = [], []
+    # a seeded fraction of the requests are optimisation requests (opt_iters OC iterations)
+    is_opt = np.random.default_rng([seed, 2]).random(n_requests) < opt_frac
+    lat, qms, lat_opt = [], [], []
     with tomo.Server(workers=workers, budget_bytes=budget_bytes) as srv:
         t0 = time.perf_counter()
         tickets = []
-        for p, ta in zip(reqs, arrive):
+        for p, ta, o in zip(reqs, arrive, is_opt):
             dt = t0 + ta - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            tickets.append(srv.submit(p))
-        for t in tickets:
+            tickets.append(srv.submit_optimize(p, opt_iters) if o else srv.submit(p))
+        for t, o in zip(tickets, is_opt):
             r, _, _ = srv.wait(t)
             if r.status != 0:
                 raise RuntimeError(f"request {t} failed: {r.message.decode()}")
-            lat.append(r.queue_ms + r.run_ms)
+            (lat_opt if o else lat).append(r.queue_ms + r.run_ms)
             qms.append(r.queue_ms)
         wall = time.perf_counter() - t0
         st = srv.stats()
@@ -69,6 +71,9 @@ def run_stream(n_requests=1000, rate=200.0, seed=0, workers=16, budget_bytes=150
         "budget_gb": budget_bytes / 2 ** 30, "sizes": f"2n x n x n, n ~ U{{{n_range[0]}..{n_range[1]}}}",
         "throughput_per_s": n_requests / wall, "p50_ms": percentile(lat, 0.5),
         "p99_ms": percentile(lat, 0.99), "queue_p99_ms": percentile(qms, 0.99),
+        "optimisation_requests": int(is_opt.sum()), "opt_iters": opt_iters if opt_frac > 0 else 0,
+        "opt_p50_ms": percentile(lat_opt, 0.5) if lat_opt else None,
+        "opt_p99_ms": percentile(lat_opt, 0.99) if lat_opt else None,
         "serial_fp64_ms_mean": statistics.mean(ser), "serial_fp64_per_s": 1e3 / statistics.mean(ser),
         "grids_created": st["grids_created"], "evictions": st["evictions"],
         "peak_resident_gb": st["peak_bytes"] / 2 ** 30}
@@ -81,8 +86,13 @@ def main(argv=None):
     ap.add_argument("--workers", type=int, default=16)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--opt-frac", type=float, default=0.0,
+                    help="fraction of the requests that are optimisation requests")
+    ap.add_argument("--opt-iters", type=int, default=10,
+                    help="OC iterations of an optimisation request")
     a = ap.parse_args(argv)
-    out = run_stream(a.requests, a.rate, a.seed, a.workers, int(a.budget_gb * 2 ** 30))
+    out = run_stream(a.requests, a.rate, a.seed, a.workers, int(a.budget_gb * 2 ** 30),
+                     opt_frac=a.opt_frac, opt_iters=a.opt_iters)
     print(json.dumps(out), flush=True)
 
 
