@@ -353,7 +353,6 @@ def extras(args, dev, stream):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
 
     from paper_2104_12282_gb300 import problems as P

@@ -411,7 +411,6 @@ def test_wrong_precision_and_sizes_are_rejected():
                      torch.zeros(p.n_el, dtype=torch.float64, device=DEV))
         with pytest.raises(ValueError):
             g.filter(torch.zeros(p.n_el + 1, device=DEV), torch.zeros(p.n_el + 1, device=DEV))
-        import ctypes
         st = tomo.lib().tomo_filter_d(g._h, None, None, 0)
         assert st == 1
         assert b"precision" in tomo.lib().tomo_last_error(g._h)

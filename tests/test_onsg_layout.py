@@ -1,6 +1,5 @@
 """Block layout of the two-scale features (§III-C) used by the synthetic-gradient model:
 brute-force element loops on CPU tensors."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
