@@ -2075,7 +2075,7 @@ bool lockstep_compatible(const std::vector<tomo_grid*>& Gs) {
   const tomo_grid* A = Gs[0];
   for (const tomo_grid* G : Gs) {
     if (G->prec != TOMO_FP32 || G->d.precond != TOMO_PRECOND_MG || !G->use_graph || G->prof ||
-        G->phase_prof || G->rhs_id != 0 || G->L.size() < 2)
+        G->phase_prof || G->rhs_id != 0 || G->L.size() < 2 || !G->fuse_j0)
       return false;
     if (G->d.smoother_degree != A->d.smoother_degree ||
         G->d.coarse_degree != A->d.coarse_degree || G->d.rr_every != A->d.rr_every ||
@@ -2141,7 +2141,8 @@ std::vector<ChebCoef> cheb_steps(const tomo_grid* G, int K) {
 // on level 0 computes r.z (beta).  *launches counts the batched launches issued.
 tomo_status batch_vcycle(tomo_batch* B, cudaStream_t st, const std::vector<tomo_grid*>& Gs,
                          const std::vector<const float*>& rin, bool dot,
-                         std::vector<float*>* zout, int64_t* launches) {
+                         std::vector<float*>* zout, int64_t* launches,
+                         bool first_done0 = false) {
   const int n = (int)Gs.size();
   const tomo_grid* G0 = Gs[0];
   const March2Const kc = march2_const(G0);
@@ -2191,12 +2192,15 @@ tomo_status batch_vcycle(tomo_batch* B, cudaStream_t st, const std::vector<tomo_
     for (int q : P) cf[q] = cheb_steps(Gs[q], K);
     for (int s = 0; s < K; ++s) {
       if (s == 0) {
-        if (l == 0) {  // (levels >= 1: the restriction that produced b wrote x1)
+        // (levels >= 1: the restriction that produced b wrote x1; level 0 inside the loop:
+        // the CG update did)
+        if (l == 0 && !first_done0) {
           std::vector<JacobiItem> ja;
           for (int q : P) {
             const tomo_level& Lv = Gs[q]->L[0];
             ja.push_back(JacobiItem{Lv.g, (const float*)Lv.s, Lv.mask, rhs(q, 0), cf[q][0].c2,
-                                    (float)Gs[q]->k0diag, X[q][0], &Gs[q]->sc->done});
+                                    (float)Gs[q]->k0diag, X[q][0], &Gs[q]->sc->done,
+                                    Gs[q]->fuse_j0 ? (float*)Gs[q]->invd : nullptr});
           }
           BK(launch_jacobi_batch(st, ja.data(), (int)ja.size()));
           *launches += 1;
@@ -2291,11 +2295,13 @@ tomo_status batch_iteration(tomo_batch* B, cudaStream_t st, const std::vector<to
   }
   BK(launch_march2_batch(st, M_APPLY, ma.data(), n, march2_const(G0), G0->num_sms));
   *launches += 1;
+  // every lockstep grid is an FP32 multigrid grid, so all have the fused first step
   std::vector<CgXrItem> xa;
   for (auto* G : Gs)
     xa.push_back(CgXrItem{3 * G->g.nn, (float*)G->xhi, (float*)G->xlo, (float*)G->r,
                           (const float*)G->p, (const float*)G->q, G->partials, G->counter,
-                          G->sc});
+                          G->sc, (float*)G->L[0].x, (const float*)G->invd,
+                          (float)(1.0 / cheb(G).theta)});
   BK(launch_cg_xr_batch(st, xa.data(), n));
   *launches += 1;
   if (G0->d.rr_every > 0) {
@@ -2313,6 +2319,9 @@ tomo_status batch_iteration(tomo_batch* B, cudaStream_t st, const std::vector<to
       rr.yf = (float*)G->r;
       rr.skip = &G->sc->done;
       rr.gate = G->sc;
+      rr.x1f = (float*)G->L[0].x;
+      rr.invdf = (const float*)G->invd;
+      rr.c2f = (float)(1.0 / cheb(G).theta);
       ra.push_back(rr);
     }
     BK(launch_march_rr_batch(st, ra.data(), n, elem_const<double>(G0), G0->num_sms));
@@ -2321,7 +2330,7 @@ tomo_status batch_iteration(tomo_batch* B, cudaStream_t st, const std::vector<to
   std::vector<const float*> r(n);
   for (int q = 0; q < n; ++q) r[q] = (const float*)Gs[q]->r;
   std::vector<float*> z;
-  TRY(batch_vcycle(B, st, Gs, r, true, &z, launches));
+  TRY(batch_vcycle(B, st, Gs, r, true, &z, launches, true));
   return batch_cg_p(B, st, Gs, z, launches);
 }
 

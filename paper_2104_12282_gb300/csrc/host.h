@@ -109,6 +109,7 @@ struct JacobiItem {  // zero-start first Chebyshev step x1 = c2 D^-1 b
   float c2, k0diag;
   float* x1;
   const int* skip;
+  float* invd;  // optional: D^-1 per node kept for the fused later steps
 };
 struct RestrictItem {  // r_c = P^T r_f (+ fused zero-start step on the coarse level)
   Geom gf, gc;
@@ -145,6 +146,9 @@ struct CgXrItem {  // x += alpha p (float pair), r -= alpha q, r.r -> convergenc
   double* partials;
   unsigned* counter;
   CgScalars* sc;
+  float* x1;          // optional: the finest zero-start Jacobi step c2 D^-1 r (see k_cg_xr)
+  const float* invd;
+  float c2;
 };
 struct CgPItem {  // p = z + beta p
   int n;

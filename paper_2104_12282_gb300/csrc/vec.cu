@@ -790,7 +790,7 @@ __global__ void k_jacobi_batch(const __grid_constant__ FlatBatch<JacobiItem> B) 
   const JacobiItem& a = B.a[q];
   jacobi_body<float, false>((int)blockIdx.x - B.cta0[q], B.cta0[q + 1] - B.cta0[q], a.g, a.s,
                             a.mask, a.b, a.c2, a.k0diag, a.x1, nullptr, nullptr, nullptr,
-                            nullptr, a.skip);
+                            nullptr, a.skip, a.invd);
 }
 
 __global__ void k_restrict_batch(const __grid_constant__ FlatBatch<RestrictItem> B) {
@@ -818,7 +818,8 @@ __global__ void k_cg_xr_batch(const __grid_constant__ FlatBatch<CgXrItem> B) {
   const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
   const CgXrItem& a = B.a[q];
   cg_xr_body<float, true>((int)blockIdx.x - B.cta0[q], B.cta0[q + 1] - B.cta0[q], a.n, a.xhi,
-                          a.xlo, a.r, a.p, a.q, a.partials, a.counter, a.sc);
+                          a.xlo, a.r, a.p, a.q, a.partials, a.counter, a.sc, a.x1, a.invd,
+                          a.c2);
 }
 
 __global__ void k_cg_p_batch(const __grid_constant__ FlatBatch<CgPItem> B) {
