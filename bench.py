@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -175,41 +176,74 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 class ClockSampler:
+    """SM clocks and throttle reasons sampled by nvidia-smi while the timed steps run.
+
+    Entering starts the sampler and waits (at most ``wait_s``) for its first row, so that
+    nvidia-smi's own start-up does not eat into a short timed region; rows are then kept
+    until exit.  The interval is 50 ms, falling back to 200 ms if nvidia-smi exits without
+    a row at the shorter one."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVALS_MS = (50, 200)
 
-    def __init__(self, index):
+    def __init__(self, index, exe="nvidia-smi", wait_s=5.0):
         self.index = index
+        self.exe = exe
+        self.wait_s = wait_s
         self.proc = None
+        self.thread = None
+        self.rows = []
+        self.interval_ms = None
+
+    def _start(self, ms):
+        proc = subprocess.Popen(
+            [self.exe, "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+             "--format=csv,noheader,nounits", "-lms", str(ms)],
+            stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+        rows = []
+        seen = threading.Event()
+
+        def pump():
+            for line in proc.stdout:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+                    seen.set()
+            seen.set()
+
+        t = threading.Thread(target=pump, daemon=True)
+        t.start()
+        seen.wait(timeout=self.wait_s)
+        return proc, rows, t
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except (FileNotFoundError, OSError):
-            self.proc = None
+        for ms in self.INTERVALS_MS:
+            try:
+                proc, rows, t = self._start(ms)
+            except (FileNotFoundError, OSError):
+                return self
+            if rows or proc.poll() is None:
+                self.proc, self.rows, self.thread, self.interval_ms = proc, rows, t, ms
+                return self
+            proc.wait()
+            t.join(timeout=5)
         return self
 
     def __exit__(self, *a):
-        self.rows = []
         if self.proc is None:
             return
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        for line in out.splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
+            self.proc.wait()
+        self.thread.join(timeout=5)
+        self.rows = list(self.rows)
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
@@ -221,7 +255,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(self.rows)}
+                "samples": len(self.rows), "interval_ms": self.interval_ms}
 
 
 def peak_hbm():
