@@ -1313,6 +1313,7 @@ void free_grid(tomo_grid* G) {
   for (auto e : G->ev) cudaEventDestroy(e);
   for (auto e : G->phase_ev)
     if (e) cudaEventDestroy(e);
+  if (tomo::g_cur_err == &G->err) tomo::g_cur_err = nullptr;
   delete G;
 }
 
@@ -1720,15 +1721,18 @@ tomo_status tomo_create_grid(const tomo_grid_desc* desc, tomo_grid** out) {
       cudaDeviceGetAttribute(&G->num_sms, cudaDevAttrMultiProcessorCount, G->device) !=
           cudaSuccess) {
     cudaGetLastError();
+    tomo::g_cur_err = nullptr;
     delete G;
     return fail(nullptr, TOMO_ECUDA, "no usable CUDA device");
   }
   build_unit_stiffness(d.nu, G->K0);
   if (!build_hadamard_blocks(G->K0, G->blk, &G->k0diag)) {
+    tomo::g_cur_err = nullptr;
     delete G;
     return fail(nullptr, TOMO_EINVAL, "element stiffness is not cube-symmetric");
   }
   if (!block_kinds(G->blk, &G->kinds)) {
+    tomo::g_cur_err = nullptr;
     delete G;
     return fail(nullptr, TOMO_EINVAL, "element stiffness blocks are not of the isotropic kinds");
   }

@@ -28,10 +28,11 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tomo.h"
+#include "admission.h"
 
 namespace {
 
-using Clock = std::chrono::steady_clock;
+using tomo_serve::Clock;
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
@@ -56,28 +57,9 @@ struct Request {
   Clock::time_point t_submit, t_start, t_done;
 };
 
-struct Slot {
-  tomo_grid* grid = nullptr;
-  int64_t session = -1;
-  tomo_grid_desc desc{};  // dims and parameters the grid was created with
-  size_t bytes = 0;       // reserved (estimate) or held (measured) device bytes
-  bool busy = false;
-  Clock::time_point last_used;
-};
-
-bool same_problem(const tomo_grid_desc& a, const tomo_grid_desc& b) {
-  return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.h == b.h && a.E0 == b.E0 &&
-         a.Emin == b.Emin && a.nu == b.nu && a.penal == b.penal && a.rmin == b.rmin &&
-         a.precision == b.precision && a.precond == b.precond && a.rtol == b.rtol &&
-         a.maxit == b.maxit && a.mg_levels == b.mg_levels &&
-         a.smoother_degree == b.smoother_degree && a.coarse_degree == b.coarse_degree &&
-         a.cheb_ratio == b.cheb_ratio && a.cheb_lmax == b.cheb_lmax && a.rr_every == b.rr_every;
-}
-
 }  // namespace
 
 struct tomo_server {
-  size_t budget = 0;
   std::vector<std::thread> threads;
   std::vector<cudaStream_t> streams;
   std::mutex mu;
@@ -86,39 +68,9 @@ struct tomo_server {
   int64_t next_ticket = 1;
   std::deque<int64_t> queue;
   std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
-  std::vector<std::unique_ptr<Slot>> slots;
-  size_t resident = 0;
+  tomo_serve::Admission pool;  // resident grids, budget and eviction (under mu)
   tomo_server_stats stats{};
   std::string err;
-
-  // Under mu: a slot for request r (resident idle grid of its session, or room for a new
-  // one after evicting idle grids), or nullptr.  Evicted grids are handed back in `dead`.
-  Slot* admit(Request& r, std::vector<tomo_grid*>& dead) {
-    if (r.session >= 0)
-      for (auto& s : slots)
-        if (s->session == r.session && same_problem(s->desc, r.desc)) {
-          if (s->busy) return nullptr;  // the session's grid is in use (or being created)
-          return s.get();
-        }
-    while (resident + r.est_bytes > budget) {
-      Slot* lru = nullptr;
-      for (auto& s : slots)
-        if (!s->busy && (!lru || s->last_used < lru->last_used)) lru = s.get();
-      if (!lru) return nullptr;
-      resident -= lru->bytes;
-      if (lru->grid) dead.push_back(lru->grid);
-      stats.evictions += 1;
-      slots.erase(std::find_if(slots.begin(), slots.end(),
-                               [&](const std::unique_ptr<Slot>& p) { return p.get() == lru; }));
-    }
-    auto s = std::make_unique<Slot>();
-    s->session = r.session;
-    s->desc = r.desc;
-    s->bytes = r.est_bytes;
-    resident += s->bytes;
-    slots.push_back(std::move(s));
-    return slots.back().get();
-  }
 
   // An optimisation request on grid g (stream st): the design stays on the device for the
   // whole run (gradient with warm-started solves, then the OC update, iters times); the
@@ -158,7 +110,7 @@ struct tomo_server {
     cudaStream_t st = streams[w];
     for (;;) {
       Request* r = nullptr;
-      Slot* slot = nullptr;
+      tomo_serve::Slot* slot = nullptr;
       std::vector<tomo_grid*> dead;
       {
         std::unique_lock<std::mutex> lk(mu);
@@ -166,7 +118,7 @@ struct tomo_server {
           if (stop) return;
           for (auto it = queue.begin(); it != queue.end(); ++it) {
             Request& q = *reqs[*it];
-            slot = admit(q, dead);
+            slot = pool.admit(q.session, q.desc, q.est_bytes, dead);
             if (slot) {
               r = &q;
               queue.erase(it);
@@ -176,10 +128,10 @@ struct tomo_server {
           if (r) break;
           cv_work.wait(lk);
         }
-        slot->busy = true;
         r->state = 1;
         r->t_start = Clock::now();
-        stats.peak_bytes = std::max<uint64_t>(stats.peak_bytes, resident);
+        stats.evictions = pool.evictions;
+        stats.peak_bytes = std::max<uint64_t>(stats.peak_bytes, pool.resident);
       }
       for (tomo_grid* e : dead) {  // evicted idle grids: quiesce on this worker's stream
         tomo_set_stream(e, st);
@@ -227,16 +179,8 @@ struct tomo_server {
         r->res.run_ms = ms_between(r->t_start, r->t_done);
         r->state = 2;
         stats.completed += 1;
-        slot->busy = false;
-        slot->last_used = r->t_done;
-        if (s != TOMO_OK || r->session < 0) {  // no session (or a failure): free at once
-          if (slot->grid) dead.push_back(slot->grid);
-          resident -= slot->bytes;
-          slots.erase(std::find_if(slots.begin(), slots.end(),
-                                   [&](const std::unique_ptr<Slot>& p) {
-                                     return p.get() == slot;
-                                   }));
-        }
+        // no session (or a failure): the grid is freed at once
+        pool.release(slot, s == TOMO_OK && r->session >= 0, r->t_done, dead);
       }
       for (tomo_grid* e : dead) {
         tomo_set_stream(e, st);
@@ -282,7 +226,7 @@ tomo_status submit_request(tomo_server* S, const tomo_grid_desc* desc, int64_t s
   if (iters > 0) est += sizeof(float) * 4 * ne;  // the run's design and gradient buffers
   r->est_bytes = est;
   std::lock_guard<std::mutex> lk(S->mu);
-  if (est > S->budget) {
+  if (est > S->pool.budget) {
     S->err = "request needs more device memory than the server's budget";
     return TOMO_ENOMEM;
   }
@@ -307,7 +251,7 @@ tomo_status tomo_server_create(int32_t workers, uint64_t budget_bytes, tomo_serv
   if (workers > 64) workers = 64;
   std::unique_ptr<tomo_server> S(new (std::nothrow) tomo_server());
   if (!S) return TOMO_ENOMEM;
-  S->budget = (size_t)budget_bytes;
+  S->pool.budget = (size_t)budget_bytes;
   for (int w = 0; w < workers; ++w) {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -365,8 +309,9 @@ tomo_status tomo_server_get_stats(tomo_server* S, tomo_server_stats* st) {
   if (!S || !st) return TOMO_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
   *st = S->stats;
-  st->resident_bytes = S->resident;
-  st->resident_grids = (int32_t)S->slots.size();
+  st->evictions = S->pool.evictions;
+  st->resident_bytes = S->pool.resident;
+  st->resident_grids = (int32_t)S->pool.slots.size();
   st->queued = (int32_t)S->queue.size();
   return TOMO_OK;
 }
@@ -379,7 +324,7 @@ tomo_status tomo_server_destroy(tomo_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->threads) t.join();
-  for (auto& s : S->slots)
+  for (auto& s : S->pool.slots)
     if (s->grid) tomo_destroy_grid(s->grid);
   for (auto s : S->streams) cudaStreamDestroy(s);
   delete S;

@@ -47,7 +47,7 @@ def test_adjoint_gradient_matches_oracle(prec, kind):
         assert np.abs(got - ref["dJdz"]).max() <= 1e-9 * scale
         assert np.abs(u.cpu().numpy() - ref["u"]).max() <= 1e-9 * np.abs(ref["u"]).max()
     else:
-        # J = l^T u with a signed l: judge it against sum |l||u| (no cancellation credit)
+        # J = l^T u with a signed l: measure its error against sum |l||u| (no cancellation credit)
         assert abs(J - ref["J"]) <= 1e-5 * (np.abs(l) @ np.abs(ref["u"]))
         assert np.abs(got - ref["dJdz"]).max() <= 1e-4 * scale
 
