@@ -176,12 +176,14 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 class ClockSampler:
-    """SM clocks and throttle reasons sampled by nvidia-smi while the timed steps run.
+    """SM clocks and throttle reasons sampled by nvidia-smi every 50 ms (200 ms if nvidia-smi
+    exits without a row at the shorter interval).
 
     Entering starts the sampler and waits (at most ``wait_s``) for its first row, so that
-    nvidia-smi's own start-up does not eat into a short timed region; rows are then kept
-    until exit.  The interval is 50 ms, falling back to 200 ms if nvidia-smi exits without
-    a row at the shorter one."""
+    nvidia-smi's own start-up is over before the timed region; enter before the warm-up
+    steps.  ``mark()`` at the start of the timed region drops the rows taken before it (an
+    idle GPU there reads a low clock); at exit, if no row has arrived since the mark, the
+    sampler waits up to two intervals for one."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -193,7 +195,9 @@ class ClockSampler:
         self.wait_s = wait_s
         self.proc = None
         self.thread = None
+        self._rows = []
         self.rows = []
+        self.first = 0
         self.interval_ms = None
 
     def _start(self, ms):
@@ -224,15 +228,23 @@ class ClockSampler:
             except (FileNotFoundError, OSError):
                 return self
             if rows or proc.poll() is None:
-                self.proc, self.rows, self.thread, self.interval_ms = proc, rows, t, ms
+                self.proc, self._rows, self.thread, self.interval_ms = proc, rows, t, ms
                 return self
             proc.wait()
             t.join(timeout=5)
         return self
 
+    def mark(self):
+        """The timed region starts now."""
+        self.first = len(self._rows)
+
     def __exit__(self, *a):
         if self.proc is None:
             return
+        deadline = time.perf_counter() + 2 * self.interval_ms / 1000.0
+        while (len(self._rows) <= self.first and self.proc.poll() is None
+               and time.perf_counter() < deadline):
+            time.sleep(0.005)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -240,7 +252,7 @@ class ClockSampler:
             self.proc.kill()
             self.proc.wait()
         self.thread.join(timeout=5)
-        self.rows = list(self.rows)
+        self.rows = list(self._rows[self.first:])
 
     def summary(self):
         if not self.rows:
@@ -426,14 +438,15 @@ def run_ours(args):
         grid.oc_step(z, dc_, dv_, p.volfrac, p.move, zn_)
         return c, info
 
-    for w in range(args.warmup):
-        step(g, zs[w % 2], dc, dv, zn)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     iters, comps = [], []
-    barrier()
-    l0 = g.launch_count()
     with ClockSampler(dev.index) as clk:
+        for w in range(args.warmup):
+            step(g, zs[w % 2], dc, dv, zn)
+        barrier()
+        l0 = g.launch_count()
+        clk.mark()
         for s in range(args.steps):
             flush.fill_(float(s))
             ev[s][0].record(stream)
