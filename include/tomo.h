@@ -302,7 +302,8 @@ tomo_status tomo_profile_read(tomo_grid* grid, int64_t* launches, double* total_
 /* Batches of independent grids (uneven sizes allowed), evaluated together.  The paper
  * optimises one design at a time; a batch serves many small problems at once on one GPU.
  * tomo_batch_create: workers = number of concurrent host threads and CUDA streams (<= 0:
- * 8, at most 64).  tomo_batch_append: adds a grid (not owned; it must outlive its use in
+ * 8, at most 64), created on the device current at the call; every grid of the batch must
+ * live on that device.  tomo_batch_append: adds a grid (not owned; it must outlive its use in
  * the batch and must not be used elsewhere while a batch call runs).  tomo_batch_gradient:
  * tomo_gradient on every grid i with z[i], &compliance[i], dcdz[i], dvdz[i] (dvdz or any
  * dvdz[i] may be NULL), info[i] (info may be NULL); FP32 grids only.

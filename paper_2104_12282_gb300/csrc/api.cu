@@ -2007,6 +2007,7 @@ tomo_status tomo_profile_read(tomo_grid* G, int64_t* launches, double* total_ms,
 struct tomo_batch {
   std::vector<tomo_grid*> grids;
   std::vector<cudaStream_t> streams;
+  int device = 0;  // device of the worker streams (current at creation)
   std::string err;
   bool lockstep = true;
   int64_t lockstep_runs = 0;
@@ -2419,6 +2420,8 @@ void for_grids_lpt(tomo_batch* B, int W, Fn fn) {
   });
   std::atomic<int> next{0};
   auto work = [&](int w) {
+    // a new host thread starts on device 0: select the batch's device first
+    if (w > 0 && cudaSetDevice(B->device) != cudaSuccess) cudaGetLastError();
     for (int k = next++; k < n; k = next++) fn(w, order[k]);
   };
   std::vector<std::thread> pool;
@@ -2580,6 +2583,12 @@ tomo_status tomo_batch_create(int32_t workers, tomo_batch** out) {
   if (workers > 64) workers = 64;
   tomo_batch* B = new (std::nothrow) tomo_batch();
   if (!B) return TOMO_ENOMEM;
+  if (cudaGetDevice(&B->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete B;
+    g_create_err = "tomo_batch_create: no usable CUDA device";
+    return TOMO_ECUDA;
+  }
   for (int w = 0; w < workers; ++w) {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -2597,6 +2606,10 @@ tomo_status tomo_batch_create(int32_t workers, tomo_batch** out) {
 
 tomo_status tomo_batch_append(tomo_batch* B, tomo_grid* G) {
   if (!B || !G) return TOMO_EINVAL;
+  if (G->device != B->device) {
+    B->err = "the grid lives on another device than the batch's streams";
+    return TOMO_EINVAL;
+  }
   for (auto* q : B->grids)
     if (q == G) {
       B->err = "grid appended twice";
