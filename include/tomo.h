@@ -361,11 +361,13 @@ const char* tomo_batch_last_error(const tomo_batch* batch);
  *   the footprint).
  * tomo_server_wait: blocks until the ticket is done, fills *result, forgets the ticket.
  * Requests start in arrival order among those whose memory can be found (idle resident
- * grids of other sessions are evicted least recently used first); a request starts as
- * soon as a worker is free, while others run.  Each request runs in order on one stream
+ * grids of other sessions are evicted least recently used first, and only when that makes
+ * room for the request); a request starts as soon as a worker is free, while others run.  Each request runs in order on one stream
  * on its own grid, so its result is the one it gives alone.
  * tomo_server_destroy: stops the workers after their running requests; requests still
- * queued are dropped (wait for every ticket first). */
+ * queued are dropped (wait for every ticket first).
+ * tomo_server_last_error: the last submit/wait error of the server, copied for the calling
+ *   thread (valid until that thread's next call). */
 typedef struct tomo_server tomo_server;
 typedef struct {
   int64_t ticket;

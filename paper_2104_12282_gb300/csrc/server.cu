@@ -333,7 +333,11 @@ tomo_status tomo_server_destroy(tomo_server* S) {
 
 const char* tomo_server_last_error(const tomo_server* S) {
   if (!S) return "";
-  return S->err.c_str();
+  // a copy per calling thread: another thread's submit may replace the message meanwhile
+  static thread_local std::string copy;
+  std::lock_guard<std::mutex> lk(const_cast<tomo_server*>(S)->mu);
+  copy = S->err;
+  return copy.c_str();
 }
 
 }  // extern "C"
