@@ -55,3 +55,30 @@ def test_create_rejects_bad_descriptor_without_gpu(libpath):
     st = L.tomo_create_grid(ctypes.byref(d), ctypes.byref(h))
     assert st == 1 and not h.value
     assert b"dimensions" in L.tomo_last_error(None)
+
+
+def test_device_footprint_estimate_without_gpu(libpath):
+    """The footprint estimate used for admission is host arithmetic: it covers at least the
+    nodal vectors CG needs, grows linearly with the grid beyond a fixed reserve, costs more
+    in FP64, and rejects empty grids."""
+    from paper_2104_12282_gb300 import problems as P
+    from paper_2104_12282_gb300 import tomo
+    p = P.mbb_192x96x76(0)
+    ndof = 3 * p.dims.n_nodes
+    e32 = tomo.estimate_device_bytes(p, precision=tomo.FP32)
+    e64 = tomo.estimate_device_bytes(p, precision=tomo.FP64)
+    # x (hi, lo), r, p, q and the level-0 smoother vectors: at least six FP32 nodal vectors
+    assert 6 * 4 * ndof <= e32 <= 200 * ndof
+    assert e64 > e32
+    # beyond a fixed reserve, each added DOF costs at least the six FP32 vectors' 24 bytes
+    small = P.cantilever(96, 48, 48)
+    big = P.cantilever(192, 96, 96)
+    grow = tomo.estimate_device_bytes(big) - tomo.estimate_device_bytes(small)
+    per_dof = grow / (3 * (big.dims.n_nodes - small.dims.n_nodes))
+    assert 24.0 <= per_dof <= 200.0
+    L = tomo.lib()
+    d = tomo.GridDesc()
+    L.tomo_default_desc(ctypes.byref(d))
+    d.nx = 0
+    out = ctypes.c_size_t()
+    assert L.tomo_estimate_device_bytes(ctypes.byref(d), ctypes.byref(out)) == 1
