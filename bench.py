@@ -33,6 +33,8 @@ METRIC = ("grad evals/s @1.4M voxels, mixed vs FP64 GPU at ≤1e-5 compliance er
 UNIT = "grad evals/s"
 WORKLOAD = "mbb_block 192x96x76 (1,400,832 voxels, 4,324,551 DOFs), bumpy density field"
 SAMPLE_DIMS = (48, 24, 19)   # CPU oracle sample: same recipe on 1/64 of the voxels
+SMALL_SAMPLE_DIMS = (24, 12, 10)  # reference arm with many steps: ~1/8 of that
+REF_STEPS_FULL_SAMPLE = 40  # above this many warm-up + timed steps, the small sample
 
 
 def parse():
@@ -85,12 +87,13 @@ def whole_job_rate(world, steps_per_rank, slowest_ms):
 # ---------------------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------------------
-def oracle_sample(seed):
-    """One exact-gradient evaluation plus OC step by the FP64 oracle on the sample box
-    (Jacobi-PCG to 1e-6, the paper's standard solver form).  Returns (seconds, cores)."""
+def oracle_sample(seed, dims=SAMPLE_DIMS):
+    """One exact-gradient evaluation plus OC step by the FP64 oracle on a sample box of the
+    benchmark recipe (Jacobi-PCG to 1e-6, the paper's standard solver form).  Returns
+    (seconds, cores, voxels)."""
     from oracle import topopt
     from paper_2104_12282_gb300 import problems as P
-    p = P.mbb_block(*SAMPLE_DIMS, volfrac=0.12, rmin=2.5)
+    p = P.mbb_block(*dims, volfrac=0.12, rmin=2.5)
     p.z0 = P.bumpy_field(p.dims, seed)
     m = topopt.Model(p)
     t0 = time.perf_counter()
@@ -150,15 +153,18 @@ def run_reference(args):
     n_sample = None
     from paper_2104_12282_gb300 import problems as P
     full = P.GridDims(192, 96, 76).n_el
+    # each step is a bounded sample: the 1/64 box (~2-5 s of CPU work), or the ~1/490 box
+    # when that many steps would not end within a few minutes
+    dims = SAMPLE_DIMS if args.warmup + args.steps <= REF_STEPS_FULL_SAMPLE else SMALL_SAMPLE_DIMS
     for s in range(args.warmup + args.steps):
-        dt, c, n_sample = oracle_sample(args.seed + s)
+        dt, c, n_sample = oracle_sample(args.seed + s, dims)
         if s >= args.warmup:
             ts.append(dt)
             cores = max(cores, c)
     mean = statistics.mean(ts)
     value = (n_sample / full) / mean
     ms_full = mean * (full / n_sample) * 1e3
-    sample = (f"FP64 oracle gradient+OC at {SAMPLE_DIMS[0]}x{SAMPLE_DIMS[1]}x{SAMPLE_DIMS[2]} "
+    sample = (f"FP64 oracle gradient+OC at {dims[0]}x{dims[1]}x{dims[2]} "
               f"({n_sample} voxels) per step, scaled to 1,400,832 voxels by element count")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

@@ -21,3 +21,16 @@ def test_reference_arm_json_line():
         assert k in out, k
     assert out["impl"] == "reference" and out["value"] > 0
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
+    assert "48x24x19" in out["cpu_baseline"]["sample"]
+
+
+def test_reference_arm_keeps_many_steps_bounded():
+    """Past 40 warm-up + timed steps each step samples the ~1/490 box, so a long run still
+    ends within minutes; the line says which sample it timed."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "41", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    out = json.loads([l for l in r.stdout.splitlines() if l.strip()][-1])
+    assert out["steps"] == 41 and out["value"] > 0
+    assert "24x12x10" in out["config"]["sample"] and "24x12x10" in out["cpu_baseline"]["sample"]
