@@ -178,15 +178,18 @@ tomo_status tomo_oc_step_d(tomo_grid* grid, const double* z, const double* dcdz,
                            double* change);
 
 /* tomo_oc_step without any allocation, for callers that may not allocate device memory
- * (code running while a stream is captured into a CUDA graph, runtimes that own all device
- * memory through their own pool, loops that cannot afford an allocation's implicit
- * synchronisation).  The paper has no counterpart: this is a deployment variant of
- * tomo_oc_step for FP32 data, computing the same update with the same multiplier search.
+ * (runtimes that own all device memory through their own pool and forbid driver
+ * allocations, loops that cannot afford an allocation's implicit synchronisation).  The
+ * paper has no counterpart: this is a deployment variant of tomo_oc_step for FP32 data,
+ * computing the same update with the same multiplier search.
  *   n_el:   number of design variables, 1 <= n_el <= 4,194,304 (larger: TOMO_EINVAL);
  *   h:      element edge (V_max = volfrac * n_el * h^3);
- *   z, dcdz, dvdz, z_new: DEVICE float arrays of n_el entries (host pointers: TOMO_EINVAL);
- *   change: DEVICE double receiving max |z_new - z|, or NULL;
- *   stream: cudaStream_t the work is queued on (NULL = legacy default); nothing waits.
+ *   z, dcdz, dvdz, z_new: float arrays of n_el entries in device memory of the CURRENT
+ *           device (host pointers or another GPU's memory: TOMO_EINVAL);
+ *   change: double in device memory of the current device receiving max |z_new - z|, or
+ *           NULL;
+ *   stream: cudaStream_t of the current device the work is queued on (NULL = legacy
+ *           default; a stream of another device: TOMO_EINVAL); nothing waits.
  * Scratch: a static device array of about 0.5 MiB inside this library, held by every GPU
  * that loads it until the process exits.  The first call on a device resolves that array's
  * device address (cudaGetSymbolAddress) with the device current; make that first call

@@ -3,8 +3,9 @@
 // idle grids.  The caller serialises every call (the request loop holds its mutex).
 //
 // A request is admitted onto the idle resident grid of its session when that grid was made
-// for the same problem, or onto a new slot when its estimated bytes fit the budget after
-// evicting idle grids, oldest use first.  Nothing is evicted unless the request is
+// for the same problem (raising the slot's reservation when the request needs more than the
+// grid reserved), or onto a new slot, when the bytes it adds fit the budget after evicting
+// other idle grids, oldest use first.  Nothing is evicted unless the request is
 // admitted: when busy grids hold too much of the budget the request waits and every idle
 // grid stays resident.
 #pragma once
@@ -51,33 +52,43 @@ struct Admission {
   // (the caller destroys them outside its lock).
   Slot* admit(int64_t session, const tomo_grid_desc& desc, size_t est,
               std::vector<tomo_grid*>& dead) {
+    Slot* reuse = nullptr;
     if (session >= 0)
       for (auto& s : slots)
         if (s->session == session && same_problem(s->desc, desc)) {
           if (s->busy) return nullptr;  // the session's grid is in use (or being created)
-          s->busy = true;
-          return s.get();
+          reuse = s.get();
+          break;
         }
+    // bytes to reserve on top of what the slot holds: a resident grid may take a request
+    // that needs more than it was created for (an optimisation run's design buffers)
+    const size_t need = reuse ? (est > reuse->bytes ? est - reuse->bytes : 0) : est;
     size_t idle = 0;
     for (auto& s : slots)
-      if (!s->busy) idle += s->bytes;
-    if (resident + est > budget + idle) return nullptr;  // busy grids hold the rest
-    while (resident + est > budget) {
+      if (!s->busy && s.get() != reuse) idle += s->bytes;
+    if (resident + need > budget + idle) return nullptr;  // busy grids hold the rest
+    while (resident + need > budget) {
       Slot* lru = nullptr;
       for (auto& s : slots)
-        if (!s->busy && (!lru || s->last_used < lru->last_used)) lru = s.get();
+        if (!s->busy && s.get() != reuse && (!lru || s->last_used < lru->last_used))
+          lru = s.get();
       if (!lru) return nullptr;  // unreachable: the check above leaves enough idle bytes
       resident -= lru->bytes;
       if (lru->grid) dead.push_back(lru->grid);
       evictions += 1;
       erase(lru);
     }
+    resident += need;
+    if (reuse) {
+      reuse->bytes += need;
+      reuse->busy = true;
+      return reuse;
+    }
     auto s = std::make_unique<Slot>();
     s->session = session;
     s->desc = desc;
     s->bytes = est;
     s->busy = true;
-    resident += est;
     slots.push_back(std::move(s));
     return slots.back().get();
   }

@@ -410,12 +410,15 @@ constexpr int kOcPerThread = 8;
 template <typename T>
 __global__ void __launch_bounds__(kOcThreads)
     k_oc_pass(int n, const T* __restrict__ z, const T* __restrict__ dc, const T* __restrict__ w,
-              double vmax, T move, double* bracket, double* partials, unsigned* counter) {
+              double vmax, T move, double* bracket, double* partials, unsigned* counter,
+              int first) {
   PDL_ENTER();
   __shared__ T s_scale[kOcCand];
   __shared__ double s_w[kOcThreads / 32][kOcCand];
   __shared__ bool s_last;
-  const double a = bracket[0], b = bracket[1];
+  // the first pass starts from the full search range; later passes read the bracket the
+  // previous pass left
+  const double a = first ? -100.0 : bracket[0], b = first ? 100.0 : bracket[1];
   if (a >= b) return;  // converged (uniform across the grid)
   if (threadIdx.x < kOcCand) {
     const double e = a + (b - a) * (double)threadIdx.x / (double)(kOcCand - 1);
@@ -599,13 +602,10 @@ cudaError_t launch_oc(cudaStream_t st, int n, const T* z, const T* dc, const T* 
   const int per_block = kOcThreads * kOcPerThread;
   const int blocks = (n + per_block - 1) / per_block;
   if (blocks > max_blocks) return cudaErrorInvalidValue;
-  const double init[2] = {-100.0, 100.0};
-  cudaError_t e = cudaMemcpyAsync(bracket, init, sizeof(init), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
   // 31^9 > 200 / (1e-10 / ln 2): nine passes always reach the tolerance
   for (int pass = 0; pass < 9; ++pass)
-    pdl_launch(k_oc_pass<T>, blocks, kOcThreads, 0, st, n, z, dc, w, vmax, (T)move, bracket, partials,
-                                                counter);
+    pdl_launch(k_oc_pass<T>, blocks, kOcThreads, 0, st, n, z, dc, w, vmax, (T)move, bracket,
+               partials, counter, pass == 0 ? 1 : 0);
   int fb = (n + kOcThreads - 1) / kOcThreads;
   if (fb > 2 * 152 * 4) fb = 2 * 152 * 4;
   pdl_launch(k_oc_final<T>, fb, kOcThreads, 0, st, n, z, dc, w, (T)move, bracket, znew, partials,

@@ -1,13 +1,12 @@
 // tomo_oc_step_noalloc: the optimality-criteria update for callers that cannot allocate
 // device memory.
 //
-// Some callers are not allowed to call cudaMalloc at all: code that runs while a stream is
-// being captured into a CUDA graph (allocation breaks or invalidates the capture), runtimes
-// that hand out every byte of device memory through their own pool and forbid driver
-// allocations behind their back, and latency-critical loops where an allocation's implicit
-// device synchronisation is unacceptable.  This entry point needs no grid handle (creating
-// one allocates) and no staging buffers: its scratch lives in the file-scope array below,
-// which every GPU that loads this library keeps until the process exits.
+// Some callers are not allowed to call cudaMalloc at all: runtimes that hand out every byte
+// of device memory through their own pool and forbid driver allocations behind their back,
+// and latency-critical loops where an allocation's implicit device synchronisation is
+// unacceptable.  This entry point needs no grid handle (creating one allocates) and no
+// staging buffers: its scratch lives in the file-scope array below, which every GPU that
+// loads this library keeps until the process exits.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -39,13 +38,16 @@ tomo_status noalloc_fail(tomo_status st, const char* msg) {
   return st;
 }
 
-bool on_device(const void* p) {
+// p is device (or managed) memory of device dev: the kernels run on the current device and
+// read the arrays without peer access, so memory of another GPU is rejected here.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -63,18 +65,28 @@ extern "C" tomo_status tomo_oc_step_noalloc(int64_t n_el, double h, const float*
                                      "move > 0");
   if (!z || !dcdz || !dvdz || !z_new)
     return noalloc_fail(TOMO_EINVAL, "tomo_oc_step_noalloc: null array");
-  if (!on_device(z) || !on_device(dcdz) || !on_device(dvdz) || !on_device(z_new) ||
-      (change && !on_device(change)))
-    return noalloc_fail(TOMO_EINVAL,
-                        "tomo_oc_step_noalloc: all arrays (and change, if given) must be "
-                        "device pointers");
-  if (z_new == z || z_new == dcdz || z_new == dvdz)
-    return noalloc_fail(TOMO_EINVAL, "tomo_oc_step_noalloc: z_new overlaps an input");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return noalloc_fail(TOMO_ECUDA, "tomo_oc_step_noalloc: no usable CUDA device");
   }
+  if (!on_device(z, dev) || !on_device(dcdz, dev) || !on_device(dvdz, dev) ||
+      !on_device(z_new, dev) || (change && !on_device(change, dev)))
+    return noalloc_fail(TOMO_EINVAL,
+                        "tomo_oc_step_noalloc: all arrays (and change, if given) must be "
+                        "device memory of the current device");
+  if (stream) {
+    int sdev = -1;
+    if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return noalloc_fail(TOMO_EINVAL, "tomo_oc_step_noalloc: invalid stream");
+    }
+    if (sdev != dev)
+      return noalloc_fail(TOMO_EINVAL,
+                          "tomo_oc_step_noalloc: the stream belongs to another device");
+  }
+  if (z_new == z || z_new == dcdz || z_new == dvdz)
+    return noalloc_fail(TOMO_EINVAL, "tomo_oc_step_noalloc: z_new overlaps an input");
   double* scratch = nullptr;
   {
     // First call on a device: resolve the device address of the static scratch with that
@@ -97,7 +109,8 @@ extern "C" tomo_status tomo_oc_step_noalloc(int64_t n_el, double h, const float*
   unsigned* counter = reinterpret_cast<unsigned*>(scal);  // scal[0]
   double* change_dev = scal + 1;
   double* bracket = scal + 2;
-  // the grid-completion counter must start at zero; the rest is written before it is read
+  // the grid-completion counter must start at zero; the rest (bracket included: the first
+  // pass of the search starts from the full range) is written before it is read
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(double), st);
   const int n = (int)n_el;
   if (e == cudaSuccess && tomo::oc_max_blocks(n) * 32 > kNoAllocPartials) e = cudaErrorInvalidValue;

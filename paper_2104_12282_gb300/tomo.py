@@ -238,16 +238,28 @@ def _current_stream():
 
 
 def oc_step_noalloc(n_el, h, z, dcdz, dvdz, volfrac, move, z_new, change=None, stream=None):
-    """tomo_oc_step_noalloc: FP32 device arrays, no grid handle, no allocation."""
+    """tomo_oc_step_noalloc: FP32 device arrays, no grid handle, no allocation.  The call
+    runs with z's device current and (unless ``stream`` is given) on that device's current
+    torch stream; arrays on any other device are rejected by the library."""
     args = [_ptr(a, np.float32, n_el, nm) for a, nm in
             ((z, "z"), (dcdz, "dcdz"), (dvdz, "dvdz"))]
     zn = _ptr(z_new, np.float32, n_el, "z_new")
     ch = None
     if change is not None:
         ch = _ptr(change, np.float64, 1, "change")
-    st = lib().tomo_oc_step_noalloc(ctypes.c_int64(n_el), ctypes.c_double(h), *args,
-                                    ctypes.c_double(volfrac), ctypes.c_double(move), zn, ch,
-                                    stream if stream is not None else _current_stream())
+
+    def call():
+        return lib().tomo_oc_step_noalloc(
+            ctypes.c_int64(n_el), ctypes.c_double(h), *args, ctypes.c_double(volfrac),
+            ctypes.c_double(move), zn, ch, stream if stream is not None else _current_stream())
+
+    dev = getattr(z, "device", None)
+    if dev is not None and dev.type == "cuda":
+        import torch
+        with torch.cuda.device(dev):
+            st = call()
+    else:
+        st = call()
     if st != 0:
         raise TomoError(st, lib().tomo_last_error(None).decode())
 

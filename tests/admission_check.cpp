@@ -111,6 +111,31 @@ int main() {
   // a request larger than the whole budget is never admitted
   CHECK(A.admit(6, d8, 101, dead) == nullptr && A.slots.empty());
 
+  // a session grid taking a request that needs more than it reserved (an optimisation run
+  // on a grid made by a gradient request) reserves the difference, evicting other idle
+  // grids for it but never itself; when even that cannot make room the request waits
+  {
+    Admission B;
+    B.budget = 100;
+    Slot* s0 = B.admit(0, d8, 40, dead);
+    s0->grid = fake_grid(10);
+    Slot* s1 = B.admit(1, d8, 40, dead);
+    s1->grid = fake_grid(11);
+    B.release(s1, true, at(10), dead);
+    B.release(s0, true, at(11), dead);
+    Slot* r = B.admit(0, d8, 70, dead);  // +30: evicts session 1's idle grid (LRU), not s0
+    CHECK(r == s0 && r->busy && r->bytes == 70 && B.resident == 70);
+    CHECK(dead.size() == 1 && dead[0] == fake_grid(11) && B.evictions == 1);
+    dead.clear();
+    B.release(r, true, at(12), dead);
+    CHECK(B.admit(0, d8, 50, dead) == s0 && s0->bytes == 70 && B.resident == 70);  // fits
+    B.release(s0, true, at(13), dead);
+    Slot* o = B.admit(2, d8, 30, dead);
+    CHECK(o && B.resident == 100);
+    CHECK(B.admit(0, d8, 80, dead) == nullptr);  // +10 with only itself idle: waits
+    CHECK(dead.empty() && s0->bytes == 70 && !s0->busy && B.resident == 100);
+  }
+
   // problems that differ in any solver parameter are different problems
   tomo_grid_desc d8b = d8;
   d8b.rtol = 1e-8;

@@ -55,3 +55,20 @@ def test_noalloc_rejects_oversize_and_host_arrays():
     with pytest.raises(tomo.TomoError) as e:
         tomo.oc_step_noalloc(8, 1.0, z.cpu(), z, z.clone(), 0.3, 0.2, torch.zeros(8, device=DEV))
     assert e.value.status == 1 and "device" in str(e.value)
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs two visible devices")
+def test_noalloc_rejects_memory_of_another_device():
+    import ctypes
+    a1 = torch.zeros(8, device="cuda:1")
+    a0 = torch.zeros(8, device="cuda:0")
+    ch = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    lib = tomo.lib()
+    with torch.cuda.device(0):  # current device 0, z on device 1: rejected before any launch
+        st = lib.tomo_oc_step_noalloc(ctypes.c_int64(8), ctypes.c_double(1.0),
+                                      ctypes.c_void_p(a1.data_ptr()),
+                                      ctypes.c_void_p(a0.data_ptr()),
+                                      ctypes.c_void_p(a0.data_ptr()), ctypes.c_double(0.3),
+                                      ctypes.c_double(0.2), ctypes.c_void_p(a0.data_ptr()),
+                                      ctypes.c_void_p(ch.data_ptr()), ctypes.c_void_p(0))
+    assert st == 1 and "current device" in lib.tomo_last_error(None).decode()
