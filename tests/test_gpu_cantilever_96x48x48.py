@@ -4,6 +4,8 @@ start): 50 OC iterations on an FP32 grid (GMG-PCG, rtol 1e-6).
 * The compliance history follows the all-FP64 GPU run of the same algorithm at rtol 1e-10
   within 1e-5 relative at every iteration (the FP64 grid is itself held to the oracle at
   1e-10 on the grids the oracle solves).
+* The first gradient is held to the oracle's own 1e-12 solve of this workload (stored in
+  tests/golden/; the oracle takes about a minute for it, too long for a test).
 * At the first, a middle and the last iteration the oracle checks the step with its own
   FP64 operator (it cannot solve 698k DOFs in seconds): the residual of the displacement,
   compliance and energy identity, the gradient composed from the same displacement, and
@@ -75,6 +77,14 @@ def test_compliance_history_follows_the_fp64_run(runs):
     rel = np.abs(c32 / c64 - 1.0)
     assert rel.max() <= 1e-5, rel.max()
     assert c32[-1] < 0.5 * c32[0]     # the optimisation made progress
+
+
+def test_first_gradient_matches_the_oracle_golden(runs):
+    """Iteration 0 (uniform start) against the FP64 oracle's own 1e-12 solve, stored by
+    tests/golden/make_fullsize_goldens.py cant."""
+    p, _, _, _, kept = runs
+    L.check_golden("fullsize_cantilever_96x48x48_uniform.txt", kept[0]["c"], kept[0]["dcdz"],
+                   p.dims.n_el)
 
 
 @pytest.mark.parametrize("k", CHECK_AT)

@@ -7,7 +7,9 @@ the filter (S1), the product (S3), the sensitivities (S6), the filter adjoint an
 volume gradient (S7), the OC step (S8).  The oracle cannot solve a 4.3M-DOF system in
 seconds, so the solve (S3-S5) is checked through properties that hold at any size, with
 the oracle's own FP64 operator: the residual of the returned displacement, the compliance
-f^T u and the energy identity u^T K u = f^T u - u^T r (large_grid_checks.py).
+f^T u and the energy identity u^T K u = f^T u - u^T r (large_grid_checks.py); and the
+gradient's compliance and dc/dz against the oracle's own 1e-12 solve of this workload,
+stored in tests/golden/ by a script that calls only the oracle.
 """
 import os
 import sys
@@ -105,6 +107,13 @@ def test_solve_at_full_size_satisfies_the_oracle_equations(run):
     info = run["info"]
     assert info.status == 0 and info.rel_res <= 1e-6 and 0 < info.iters < 200
     L.check_solve(run["p"], run["m"], run["z"], run["u"], run["c"])
+
+
+def test_gradient_matches_the_oracle_golden(run):
+    """Compliance and dc/dz against the FP64 oracle's own solve of this workload (Jacobi-PCG
+    to 1e-12, stored by tests/golden/make_fullsize_goldens.py mbb)."""
+    L.check_golden("fullsize_mbb_192x96x76_seed0.txt", run["c"], run["dcdz"],
+                   run["p"].dims.n_el)
 
 
 def test_sensitivity_kernel_at_full_size(run):
