@@ -322,6 +322,9 @@ tomo_status march(tomo_grid* G, int level, int mode, MarchArgs<T> a, const T* s_
       m.skip = a.skip;
       m.xprev_zero = a.xprev_zero;
       m.tile_fixed = G->L[level].tile_fixed;
+      m.invd = (const float*)G->L[level].invd;
+      if (mode == M_CHEB && m.invd == nullptr)
+        return fail(G, TOMO_EINVAL, "Chebyshev step on a level without its diagonal");
       if (a.gate != nullptr) return fail(G, TOMO_EINVAL, "gated product needs the FP64 path");
       March2Const k{(float)G->kinds.a0, (float)G->kinds.b0, (float)G->kinds.a7,
                     (float)G->kinds.b7, (float)G->kinds.ta, (float)G->kinds.tb,
@@ -362,6 +365,11 @@ tomo_status setup_levels(tomo_grid* G) {
   for (size_t l = 1; l < G->L.size(); ++l) {
     CK(launch_coarsen_s<T>(G->stream, G->L[l - 1].g, G->L[l].g, (const T*)G->L[l - 1].s,
                            (T*)G->L[l].s));
+    G->launches += 1;
+  }
+  for (auto& Lv : G->L) {
+    if (!Lv.invd) continue;
+    CK(launch_invdiag<T>(G->stream, Lv.g, (const T*)Lv.s, (T)G->k0diag, (T*)Lv.invd));
     G->launches += 1;
   }
   if (G->L.size() > 1) {
@@ -434,10 +442,8 @@ tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_star
     if (s == 0 && zero_start) {
       if (!first_done) {  // (else the restriction or the CG update already wrote X)
         LevelTimer lt(G, l);
-        // on the finest level of a fused grid this also keeps D^-1 for the CG update
-        T* invd = (l == 0 && G->fuse_j0) ? (T*)G->invd : nullptr;
         CK(launch_jacobi<T>(G->stream, Lv.g, (const T*)Lv.s, Lv.mask, b, (T)c2, k0d, *X,
-                            nullptr, G->partials, G->counter, G->sc, dk, skip, invd));
+                            nullptr, G->partials, G->counter, G->sc, dk, skip));
         G->launches += 1;
       }
       // X = x1; x0 = 0 is implicit: the next step is told not to read Y
@@ -1271,6 +1277,7 @@ void free_grid(tomo_grid* G) {
     F(Lv.xp);
     F(Lv.t);
     F(Lv.tile_fixed);
+    F(Lv.invd);
   }
   F(G->d_taps);
   F(G->d_tapw);
@@ -1301,7 +1308,7 @@ void free_grid(tomo_grid* G) {
   G->loop_cache.clear();
   F(G->load_idx);
   F(G->load_val);
-  F(G->invd);
+  G->invd = nullptr;  // (level 0's D^-1, freed with the levels)
   F(G->adj_T);
   F(G->adj64);
   F(G->adj_hi);
@@ -1357,6 +1364,8 @@ size_t estimate_device_bytes(const tomo_grid_desc& d) {
   if (d.precond == TOMO_PRECOND_MG) {
     const size_t nc = 3 * (size_t)lv.back().nn;
     b += nc * nc * T + nc * T;
+    if (d.precision == TOMO_FP32)  // D^-1 per node on the smoothed levels
+      for (size_t l = 0; l + 1 < lv.size(); ++l) b += (size_t)lv[l].nn * T;
   }
   const size_t nv = 3 * (size_t)g.nn * T, ne = (size_t)g.nel * T;
   b += nv + 3 * (size_t)g.nn * 8 + 4 * nv + 4 * ne + 3 * ne;
@@ -1412,7 +1421,11 @@ tomo_status create_impl(tomo_grid* G) {
     }
   }
   if (G->coarse_n > 0 && sizeof(T) == 4) {
-    TRY(dalloc(G, &G->invd, sizeof(T) * (size_t)g.nn));
+    // D^-1 per node on every smoothed level (the Chebyshev steps of k_march2 read it; the
+    // finest one also serves the zero-start step fused into the CG update)
+    for (size_t l = 0; l + 1 < G->L.size(); ++l)
+      TRY(dalloc(G, &G->L[l].invd, sizeof(T) * (size_t)G->L[l].g.nn));
+    G->invd = G->L[0].invd;
     G->fuse_j0 = true;
   }
   if (G->coarse_n > 0) {
@@ -2071,6 +2084,7 @@ March2Args march2_args(const tomo_grid* G, int level, const float* x, const floa
   m.skip = &G->sc->done;
   m.xprev_zero = xprev_zero;
   m.tile_fixed = Lv.tile_fixed;
+  m.invd = (const float*)Lv.invd;
   return m;
 }
 
@@ -2205,7 +2219,7 @@ tomo_status batch_vcycle(tomo_batch* B, cudaStream_t st, const std::vector<tomo_
             const tomo_level& Lv = Gs[q]->L[0];
             ja.push_back(JacobiItem{Lv.g, (const float*)Lv.s, Lv.mask, rhs(q, 0), cf[q][0].c2,
                                     (float)Gs[q]->k0diag, X[q][0], &Gs[q]->sc->done,
-                                    Gs[q]->fuse_j0 ? (float*)Gs[q]->invd : nullptr});
+                                    nullptr});
           }
           BK(launch_jacobi_batch(st, ja.data(), (int)ja.size()));
           *launches += 1;

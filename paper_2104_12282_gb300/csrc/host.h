@@ -190,6 +190,7 @@ struct March2Args {
   int dot_kind;
   const int* skip;
   int xprev_zero;  // CHEB: the previous iterate is zero (first step after a zero start)
+  const float* invd;  // CHEB: D^-1 per node of this level
   // per x-y tile of the launch (32 x 16 node columns with halo): does any node of the
   // tile's columns have a fixed DOF?  nullptr: every tile reads the mask
   const uint8_t* tile_fixed;
@@ -235,6 +236,9 @@ cudaError_t launch_prolong_add(cudaStream_t st, Geom gf, Geom gc, const T* xc, T
                                const uint8_t* mask_f, const int* skip);
 template <typename T>
 cudaError_t launch_coarsen_s(cudaStream_t st, Geom gf, Geom gc, const T* sf, T* sc);
+// invd[n] = 1 / (k0diag * sum of the node's element moduli), 0 where that is not positive
+template <typename T>
+cudaError_t launch_invdiag(cudaStream_t st, Geom g, const T* s, T k0diag, T* invd);
 template <typename T>
 cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint8_t* mask,
                                  const DenseK0<T>& K0, T* A, T* dscale, unsigned* status);
@@ -301,6 +305,7 @@ struct tomo_level {
   void* xp = nullptr;       // T[3nn] previous iterate / ping-pong
   void* t = nullptr;        // T[3nn] residual
   uint8_t* tile_fixed = nullptr;  // FP32 grids: k_march2 tiles that hold fixed nodes
+  void* invd = nullptr;     // FP32 multigrid levels with a smoother: D^-1 per node
   std::vector<uint8_t> hmask;
 };
 

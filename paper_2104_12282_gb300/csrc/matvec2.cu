@@ -30,6 +30,10 @@ constexpr int TYP = 8;            // thread rows per CTA (two node rows each)
 #ifndef TOMO_MARCH2_MIN_BLOCKS
 #define TOMO_MARCH2_MIN_BLOCKS 2
 #endif
+#ifndef TOMO_MARCH2_CHEB_UNROLL
+#define TOMO_MARCH2_CHEB_UNROLL 1
+#endif
+constexpr int kChebUnroll = TOMO_MARCH2_CHEB_UNROLL;
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -56,13 +60,14 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
                                             unsigned nblk) {
   constexpr bool CHEBY = MODE == M_CHEB;
   PDL_ENTER();
-  if (A.skip != nullptr && *A.skip) return;
+  // the stop flag is tested after the first planes' loads are issued, so that its latency
+  // and theirs overlap (every CTA starts with them)
+  const int stop = A.skip != nullptr ? *A.skip : 0;
   const Geom g = A.g;
   const int l = threadIdx.x, t = threadIdx.y;
   const int i = bx * 30 - 1 + l;
   const int j0 = by * (2 * TYP - 2) - 1 + 2 * t;
   const int j1 = j0 + 1;
-  const bool tile_fixed = A.tile_fixed == nullptr || A.tile_fixed[bx + gx * by] != 0;
   const int kb = bz * A.kz;
   const int ke = min(kb + A.kz, g.nzn);
   const int nn = g.nn, plane = g.nxn * g.nyn, eplane = g.nx * g.ny;
@@ -80,7 +85,6 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
 
   __shared__ float sN[3][TYP][32];  // node row j0 of each thread row, plane k+1
   __shared__ float sV[6][TYP][32];  // sy = 1 half of the upper element, for the next row
-  __shared__ float sS[TYP][32];     // element modulus sums (diagonal), upper element
 
   auto load_plane = [&](int k, float2 (&v)[3]) {
     const bool in = k >= 0 && k < g.nzn;
@@ -101,6 +105,11 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
   float2 A0[3], C0[3];
   float N0[3], DN0[3];
   load_plane(kb - 1, A0);
+  float2 A1n[3];
+  load_plane(kb, A1n);
+  float2 sen = load_s(kb - 1);
+  const bool tile_fixed = A.tile_fixed == nullptr || A.tile_fixed[bx + gx * by] != 0;
+  if (stop) return;
 #pragma unroll
   for (int c = 0; c < 3; ++c) sN[c][t][l] = A0[c].x;
   __syncthreads();
@@ -111,12 +120,8 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
     DN0[c] = __shfl_down_sync(FULL, N0[c], 1);
   }
   __syncthreads();
-  float2 A1n[3];
-  load_plane(kb, A1n);
-  float2 sen = load_s(kb - 1);
 
   float2 carry[3] = {bc2(0.0f), bc2(0.0f), bc2(0.0f)};
-  float2 carryS = bc2(0.0f);
   // fused inner product: per step the three components are summed in FP32, then added to
   // the pair dhi + dlo with TwoSum (FP64 runs at 1/64 of the FP32 rate on this part)
   float2 dhi = bc2(0.0f), dlo = bc2(0.0f);
@@ -148,6 +153,11 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
         if (w0) bv[c].x = __ldg(A.b + (size_t)c * nn + n0);
         if (w1) bv[c].y = __ldg(A.b + (size_t)c * nn + n1);
       }
+    }
+    float2 inv = bc2(0.0f);  // CHEB: D^-1 of the two nodes (precomputed per level)
+    if (CHEBY) {
+      if (w0) inv.x = __ldg(A.invd + n0);
+      if (w1) inv.y = __ldg(A.invd + n1);
     }
     if (CHEBY && A.c1 != 0.0f && !A.xprev_zero) {
 #pragma unroll
@@ -268,12 +278,6 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
         sV[2 * c + mz][t][l] = v1.y;  // upper element's sy = 1 half -> node row j0 + 2
       }
     }
-    float2 Sx = bc2(0.0f);
-    if (CHEBY) {
-      const float2 fromleft = shup2(se);
-      Sx = (l > 0) ? add2(se, fromleft) : se;
-      sS[t][l] = Sx.y;
-    }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -285,11 +289,6 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
         T[c][mz] = add2(T[c][mz], make_float2(prev, V1keep[c][mz].x));
       }
     }
-    float2 Srow = bc2(0.0f);
-    if (CHEBY) {
-      const float prevS = (t > 0) ? sS[t - 1][l] : 0.0f;
-      Srow = add2(make_float2(Sx.x, Sx.x), make_float2(prevS, Sx.y));
-    }
     // z-stage: plane k (output) and plane k+1 (carried)
     float2 out[3];
 #pragma unroll
@@ -299,16 +298,9 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
       out[c] = add2(carry[c], y0);
       carry[c] = y1;
     }
-    const float2 Stot = add2(carryS, Srow);
-    carryS = Srow;
 
     // ---- epilogue ----
     if (w0 || w1) {
-      float2 inv = bc2(0.0f);
-      if (CHEBY) {
-        inv.x = Stot.x > 0.0f ? 1.0f / (K.k0diag * Stot.x) : 0.0f;
-        inv.y = Stot.y > 0.0f ? 1.0f / (K.k0diag * Stot.y) : 0.0f;
-      }
       float2 pc = bc2(0.0f);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -351,8 +343,10 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
     };
   // The product and the residual run unrolled by two (the plane buffers swap roles without
   // register copies: 8 % on the product at the benchmark size, measured); the Chebyshev
-  // step keeps one step per iteration (unrolled it spills).
+  // step keeps one step per iteration unless TOMO_MARCH2_CHEB_UNROLL says otherwise
+  // (unrolled it spills).
   if constexpr (CHEBY) {
+#pragma unroll kChebUnroll
     for (int k = kb - 1; k < ke; ++k) step(k);
   } else {
 #pragma unroll 2

@@ -253,6 +253,36 @@ __global__ void k_coarsen_s(Geom gf, Geom gc, const T* __restrict__ sf, T* __res
   }
 }
 
+// D^-1 per node, D = k0diag * (sum of s_e over the node's elements), 0 where that sum is not
+// positive: the same sum, in the same order, as the zero-start Jacobi step above, for the
+// Chebyshev steps of the product kernel (computed once per level and gradient).
+template <typename T>
+__global__ void k_invdiag(Geom g, const T* __restrict__ s, T k0diag, T* __restrict__ invd) {
+  PDL_ENTER();
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nn; n += gridDim.x * blockDim.x) {
+    const int i = n % g.nxn, j = (n / g.nxn) % g.nyn, k = n / (g.nxn * g.nyn);
+    const int xa = max(i - 1, 0), xb = min(i, g.nx - 1);
+    const int ya = g.nx * max(j - 1, 0), yb = g.nx * min(j, g.ny - 1);
+    const int za = g.nx * g.ny * max(k - 1, 0), zb = g.nx * g.ny * min(k, g.nz - 1);
+    const T wxa = i > 0 ? T(1) : T(0), wxb = i < g.nx ? T(1) : T(0);
+    const T wya = j > 0 ? T(1) : T(0), wyb = j < g.ny ? T(1) : T(0);
+    const T wza = k > 0 ? T(1) : T(0), wzb = k < g.nz ? T(1) : T(0);
+    auto row = [&](int off) { return wxa * s[off + xa] + wxb * s[off + xb]; };
+    const T S = wza * (wya * row(za + ya) + wyb * row(za + yb)) +
+                wzb * (wya * row(zb + ya) + wyb * row(zb + yb));
+    const T dg = k0diag * S;
+    invd[n] = dg > T(0) ? T(1) / dg : T(0);
+  }
+}
+
+template <typename T>
+cudaError_t launch_invdiag(cudaStream_t st, Geom g, const T* s, T k0diag, T* invd) {
+  int blocks = (g.nn + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  pdl_launch(k_invdiag<T>, blocks, 256, 0, st, g, s, k0diag, invd);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_coarsen_s(cudaStream_t st, Geom gf, Geom gc, const T* sf, T* sc) {
   int blocks = (gc.nel + 255) / 256;
@@ -391,8 +421,10 @@ cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint
   return cudaGetLastError();
 }
 
-// z = D^-1/2 Ainv D^-1/2 r.  Ainv is symmetric, so thread `row` walks column `row`
-// (Ainv[c * n + row], consecutive threads read consecutive addresses); accumulated in T.
+// z = D^-1/2 Ainv D^-1/2 r.  One warp per row: the lanes split the row's columns (row-major
+// reads of the stored inverse, coalesced; every warp's row loads are independent, so a row
+// costs about one L2 round trip instead of one per few columns), then a fixed-order warp
+// sum; accumulated in T.
 template <typename T>
 __device__ __forceinline__ void coarse_apply_body(int n, const T* __restrict__ Ainv,
                                                   const T* __restrict__ dsc,
@@ -404,17 +436,14 @@ __device__ __forceinline__ void coarse_apply_body(int n, const T* __restrict__ A
   T* rs = reinterpret_cast<T*>(smem_raw);
   for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = dsc[q] * r[q];
   __syncthreads();
-  for (int row = threadIdx.x; row < n; row += blockDim.x) {
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    int c = 0;
-    for (; c + 3 < n; c += 4) {
-      a0 += __ldg(Ainv + (size_t)(c + 0) * n + row) * rs[c + 0];
-      a1 += __ldg(Ainv + (size_t)(c + 1) * n + row) * rs[c + 1];
-      a2 += __ldg(Ainv + (size_t)(c + 2) * n + row) * rs[c + 2];
-      a3 += __ldg(Ainv + (size_t)(c + 3) * n + row) * rs[c + 3];
-    }
-    for (; c < n; ++c) a0 += __ldg(Ainv + (size_t)c * n + row) * rs[c];
-    z[row] = dsc[row] * ((a0 + a1) + (a2 + a3));
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = threadIdx.x >> 5; row < n; row += nw) {
+    const T* a = Ainv + (size_t)row * n;
+    T acc = T(0);
+    for (int c = lane; c < n; c += 32) acc += __ldg(a + c) * rs[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[row] = dsc[row] * acc;
   }
 }
 
@@ -1018,6 +1047,7 @@ cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo,
   template cudaError_t launch_prolong_add<T>(cudaStream_t, Geom, Geom, const T*, T*,          \
                                              const uint8_t*, const int*);                    \
   template cudaError_t launch_coarsen_s<T>(cudaStream_t, Geom, Geom, const T*, T*);           \
+  template cudaError_t launch_invdiag<T>(cudaStream_t, Geom, const T*, T, T*);               \
   template cudaError_t launch_coarse_factor<T>(cudaStream_t, Geom, const T*, const uint8_t*,  \
                                                const DenseK0<T>&, T*, T*, unsigned*);        \
   template cudaError_t launch_coarse_apply<T>(cudaStream_t, int, const T*, const T*, const T*, \
