@@ -347,7 +347,10 @@ tomo_status march(tomo_grid* G, int level, int mode, MarchArgs<T> a, const T* s_
     if (a.xlo) bytes += nv;
     if (mode == M_APPLY) bytes += nv;                  // y
     else if (mode == M_RESID) bytes += 2 * nv;         // b, y
-    else bytes += ((a.c1 != T(0) && !a.xprev_zero) ? 3 : 2) * nv;  // b, (xprev), x_new
+    else {
+      bytes += ((a.c1 != T(0) && !a.xprev_zero) ? 3 : 2) * nv;  // b, (xprev), x_new
+      if (fused_kernel) bytes += a.g.nn * (double)sizeof(T);       // D^-1 per node
+    }
     TRY(prof_end(G, bytes));
   }
   return TOMO_OK;
