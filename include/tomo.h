@@ -245,22 +245,40 @@ tomo_status tomo_set_smoother(tomo_grid* grid, int32_t fine_degree, int32_t coar
 tomo_status tomo_get_smoother(const tomo_grid* grid, int32_t* fine_degree,
                               int32_t* coarse_degree, double* ratio);
 
+/* Upper end lam of the smoothing interval [lam / ratio, lam] of D^-1 K (Section III-D's
+ * multigrid; the interval is this library's choice).  lam <= 0 selects the element bound
+ * max eig(diag(K0)^-1 K0), which bounds the spectrum of any design (the default); a smaller
+ * lam (at least a quarter of the bound, else EINVAL) smooths the actual spectrum, which on
+ * designs without isolated elements ends near 3.1-3.9, better and saves CG iterations.  If a
+ * solve with lam below the bound fails (the interval misses the top of the spectrum: the
+ * preconditioner is not positive or CG does not converge), the solve is redone from zero at
+ * the element bound and the grid keeps the bound; tomo_get_smoother_bound counts these
+ * fallbacks.  Like tomo_set_smoother it waits for the grid's stream and sets the captured CG
+ * loop aside.  tomo_get_smoother_bound: any pointer may be NULL. */
+tomo_status tomo_set_smoother_bound(tomo_grid* grid, double lam);
+tomo_status tomo_get_smoother_bound(const tomo_grid* grid, double* lam, double* element_bound,
+                                    int64_t* fallbacks);
+
 /* Smoother autotuner.  On the design z (N_el, host or device; filtered and turned into the
  * material as tomo_gradient does) it times the state solve from a zero start for each
  * candidate (pairs[2k], pairs[2k+1]) = (fine_degree, coarse_degree), k < n (1..64), at the
- * grid's current ratio: one untimed solve (skipped when the grid kept that candidate's
- * captured loop from an earlier use: a grid keeps the loops of up to 8 smoother settings),
- * then reps (1..16) solves timed with CUDA events on the grid's stream, the median kept.  pairs == NULL: the built-in list (2,2) (2,3) (2,4)
- * (1,3) (1,4) (1,6) (n ignored).  The fastest candidate that converges becomes the grid's
+ * grid's current ratio and bound: one untimed solve (skipped when the grid kept that
+ * candidate's captured loop from an earlier use: a grid keeps the loops of up to 8 smoother
+ * settings), then reps (1..16) solves timed with CUDA events on the grid's stream, the
+ * median kept.  pairs == NULL: the built-in list (2,2) (2,3) (2,4) (1,3) (1,4) (1,6), each at
+ * 1, 0.75 and 0.68 times the element bound (18 candidates; n ignored; results needs room for
+ * 18).  Candidates are timed without the bound fallback of the solves (a candidate that
+ * fails is only marked failed).  The fastest candidate that converges becomes the grid's
  * smoother; results[k] (may be NULL) holds each candidate's median milliseconds (-1 when it
- * failed), iterations and status; *best (may be NULL) its index.  If no candidate converges
- * the grid keeps its previous smoother and ENOCONV is returned.  The grid's displacement is
- * left as the last trial's. */
+ * failed), iterations, status and bound; *best (may be NULL) its index.  If no candidate
+ * converges the grid keeps its previous smoother and ENOCONV is returned.  The grid's
+ * displacement is left as the last trial's. */
 typedef struct {
   int32_t fine_degree, coarse_degree;
   int32_t iters;
   int32_t status;
   double ms;
+  double lam;  /* upper end of the smoothing interval the candidate used */
 } tomo_tune_result;
 tomo_status tomo_autotune_smoother(tomo_grid* grid, const float* z, const int32_t* pairs,
                                    int32_t n, int32_t reps, tomo_tune_result* results,
@@ -386,6 +404,7 @@ typedef struct {
   int64_t submitted, completed, grids_created, evictions;
   uint64_t resident_bytes, peak_bytes;  /* estimated footprints of the resident grids */
   int32_t resident_grids, queued;
+  int64_t batches;  /* lockstep batches run for groups of two or more gradient requests */
 } tomo_server_stats;
 tomo_status tomo_server_create(int32_t workers, uint64_t budget_bytes, tomo_server** out);
 tomo_status tomo_server_submit(tomo_server* server, const tomo_grid_desc* desc, int64_t session,
@@ -396,6 +415,18 @@ tomo_status tomo_server_submit_optimize(tomo_server* server, const tomo_grid_des
                                         int64_t* ticket);
 tomo_status tomo_server_wait(tomo_server* server, int64_t ticket, tomo_result* result);
 tomo_status tomo_server_get_stats(tomo_server* server, tomo_server_stats* stats);
+/* Lockstep batching of gradient requests: with max_batch >= 2 a worker that becomes free
+ * takes the first admissible request in arrival order and, when it is a gradient request,
+ * every further admissible gradient request in the queue behind it, up to max_batch in
+ * all, and evaluates them as one tomo_batch (lockstep CG loop, batch_workers threads and
+ * streams, <= 0: 4); requests that arrive while a batch runs join the next one a worker
+ * forms.  Results agree with the request alone to the solver's tolerance (tomo_batch's
+ * lockstep rule); if the batch call fails, each of its requests is run alone, so one bad
+ * request fails alone.  Optimisation requests always run alone.  max_batch <= 1 (the
+ * default) runs every request alone on its worker's stream (bitwise the result alone).
+ * Takes effect for requests a worker takes after the call. */
+tomo_status tomo_server_set_batching(tomo_server* server, int32_t max_batch,
+                                     int32_t batch_workers);
 tomo_status tomo_server_destroy(tomo_server* server);
 const char* tomo_server_last_error(const tomo_server* server);
 

@@ -744,8 +744,10 @@ tomo_status pcg_result(tomo_grid* G, tomo_solve_info* info) {
   return TOMO_OK;
 }
 
+tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, double lam);
+
 template <typename T>
-tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
+tomo_status pcg_once(tomo_grid* G, bool warm, tomo_solve_info* info) {
   bool trivial = false;
   TRY(pcg_start<T>(G, warm, info, &trivial));
   if (trivial) return TOMO_OK;
@@ -783,6 +785,22 @@ tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info) {
     }
   }
   return pcg_result(G, info);
+}
+
+// The solve, and with `fallback` a second chance: a smoothing interval whose upper end lies
+// below the spectrum of D^-1 K (a tuned bound on a design it does not fit) can make the
+// V-cycle indefinite (r^T z <= 0 stops CG) or slow; the solve is then redone from zero at
+// the element bound, which always holds, and the grid keeps that bound.
+template <typename T>
+tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info, bool fallback = true) {
+  tomo_status st = pcg_once<T>(G, warm, info);
+  if (st == TOMO_OK || !fallback || st == TOMO_ECUDA || st == TOMO_EINVAL ||
+      G->d.precond != TOMO_PRECOND_MG || !(G->lam_hi < G->lam_bound))
+    return st;
+  G->bound_fallbacks += 1;
+  TRY(set_smoother(G, G->d.smoother_degree, G->d.coarse_degree, G->cheb_ratio, G->lam_bound));
+  G->err.clear();
+  return pcg_once<T>(G, false, info);
 }
 
 // dV/dz = P^T v with v_e = h^3 (Section III-D), written to out.
@@ -1530,11 +1548,18 @@ tomo_status create_impl(tomo_grid* G) {
 
 // Chebyshev degrees (finest level, coarser levels) and interval ratio of a grid; the
 // captured CG loops, which bake them in, are dropped and rebuilt at the next solve.
-tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio) {
+tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, double lam) {
   if (fine < 1 || fine > 16 || coarse < 1 || coarse > 16 || !(ratio > 1.0) || !std::isfinite(ratio))
     return fail(G, TOMO_EINVAL, "smoother: degrees in 1..16 and ratio > 1 (got %d, %d, %g)",
                 fine, coarse, ratio);
-  if (fine == G->d.smoother_degree && coarse == G->d.coarse_degree && ratio == G->cheb_ratio)
+  if (std::isnan(lam))
+    return fail(G, TOMO_EINVAL, "smoother bound: NaN");
+  if (!(lam > 0.0)) lam = G->lam_bound;
+  if (!(lam >= 0.25 * G->lam_bound && lam <= G->lam_bound))
+    return fail(G, TOMO_EINVAL, "smoother bound %g outside [%g, %g] (a quarter of the element "
+                "bound up to the bound)", lam, 0.25 * G->lam_bound, G->lam_bound);
+  if (fine == G->d.smoother_degree && coarse == G->d.coarse_degree && ratio == G->cheb_ratio &&
+      lam == G->lam_hi)
     return TOMO_OK;
   TRY(sync(G));  // no captured loop of this grid is still running
   // keep the current load-slot loop for a later return to these settings (up to 8)
@@ -1544,7 +1569,7 @@ tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio) {
       G->loop_cache.erase(G->loop_cache.begin());
     }
     G->loop_cache.push_back(tomo_grid::CachedLoop{G->d.smoother_degree, G->d.coarse_degree,
-                                                  G->cheb_ratio, G->loop_exec});
+                                                  G->cheb_ratio, G->lam_hi, G->loop_exec});
   }
   G->loop_exec = nullptr;
   if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
@@ -1553,9 +1578,10 @@ tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio) {
   G->d.coarse_degree = coarse;
   G->d.cheb_ratio = ratio;
   G->cheb_ratio = ratio;
+  G->lam_hi = lam;
   for (size_t k = 0; k < G->loop_cache.size(); ++k) {
     const tomo_grid::CachedLoop& e = G->loop_cache[k];
-    if (e.fine == fine && e.coarse == coarse && e.ratio == ratio) {
+    if (e.fine == fine && e.coarse == coarse && e.ratio == ratio && e.lam == lam) {
       G->loop_exec = e.exec;
       G->loop_cache.erase(G->loop_cache.begin() + k);
       break;
@@ -1573,22 +1599,37 @@ template <typename T>
 tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, int reps,
                         tomo_tune_result* res, int32_t* best) {
   // (fine, coarse) degrees: (2, 2) is fastest on random fields, (1, 4) on OC-evolved
-  // designs (near 0/1 densities), measured on the 192x96x76 MBB-type block
+  // designs (near 0/1 densities), measured on the 192x96x76 MBB-type block; with the
+  // built-in list each pair is also tried at 0.75 and 0.68 of the element bound of the
+  // smoothing interval (lambda_max of D^-1 K is near 3.1-3.9 on those designs, well below
+  // the bound of 5.3, which only isolated elements reach)
   static const int32_t kDefault[] = {2, 2, 2, 3, 2, 4, 1, 3, 1, 4, 1, 6};
+  static const double kBoundScale[] = {1.0, 0.75, 0.68};
   if (!z) return fail(G, TOMO_EINVAL, "null array");
+  struct Cand {
+    int fine, coarse;
+    double lam;
+  };
+  std::vector<Cand> cands;
   if (!pairs) {
-    pairs = kDefault;
-    n = (int)(sizeof(kDefault) / sizeof(kDefault[0]) / 2);
+    for (double f : kBoundScale)
+      for (size_t k = 0; k + 1 < sizeof(kDefault) / sizeof(kDefault[0]); k += 2)
+        cands.push_back(Cand{kDefault[k], kDefault[k + 1], f * G->lam_bound});
+  } else {
+    if (n < 1 || n > 64)
+      return fail(G, TOMO_EINVAL, "autotune: 1..64 candidates and 1..16 repetitions");
+    for (int k = 0; k < n; ++k) cands.push_back(Cand{pairs[2 * k], pairs[2 * k + 1], G->lam_hi});
   }
-  if (n < 1 || n > 64 || reps < 1 || reps > 16)
+  n = (int)cands.size();
+  if (reps < 1 || reps > 16)
     return fail(G, TOMO_EINVAL, "autotune: 1..64 candidates and 1..16 repetitions");
   if (G->d.precond != TOMO_PRECOND_MG)
     return fail(G, TOMO_EINVAL, "autotune: the grid has no multigrid smoother");
   for (int k = 0; k < n; ++k)
-    if (pairs[2 * k] < 1 || pairs[2 * k] > 16 || pairs[2 * k + 1] < 1 || pairs[2 * k + 1] > 16)
+    if (cands[k].fine < 1 || cands[k].fine > 16 || cands[k].coarse < 1 || cands[k].coarse > 16)
       return fail(G, TOMO_EINVAL, "autotune: candidate %d has a degree outside 1..16", k);
   const int fine0 = G->d.smoother_degree, coarse0 = G->d.coarse_degree;
-  const double ratio = G->cheb_ratio;
+  const double ratio = G->cheb_ratio, lam0 = G->lam_hi;
   const size_t be = sizeof(T) * (size_t)G->g.nel;
   const void* dz;
   bool h1;
@@ -1609,17 +1650,18 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
   double bms = 0.0;
   tomo_status st = TOMO_OK;
   for (int k = 0; k < n && st == TOMO_OK; ++k) {
-    st = set_smoother(G, pairs[2 * k], pairs[2 * k + 1], ratio);
+    st = set_smoother(G, cands[k].fine, cands[k].coarse, ratio, cands[k].lam);
     if (st != TOMO_OK) break;
     tomo_solve_info info{};
-    // untimed solve, which captures this candidate's loop, unless the grid kept it
+    // untimed solve, which captures this candidate's loop, unless the grid kept it; a
+    // candidate is timed as it is, without the fallback to the element bound
     tomo_status sk = TOMO_OK;
-    if (!G->loop_exec || G->prof) sk = pcg<T>(G, false, &info);
+    if (!G->loop_exec || G->prof) sk = pcg<T>(G, false, &info, false);
     std::vector<double> ms;
     for (int r = 0; r < reps && sk == TOMO_OK; ++r) {
       float t = 0.0f;
       if (cudaEventRecord(e0, G->stream) != cudaSuccess) sk = TOMO_ECUDA;
-      if (sk == TOMO_OK) sk = pcg<T>(G, false, &info);
+      if (sk == TOMO_OK) sk = pcg<T>(G, false, &info, false);
       if (sk == TOMO_OK && (cudaEventRecord(e1, G->stream) != cudaSuccess ||
                             cudaEventSynchronize(e1) != cudaSuccess ||
                             cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
@@ -1641,11 +1683,12 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
       }
     }
     if (res) {
-      res[k].fine_degree = pairs[2 * k];
-      res[k].coarse_degree = pairs[2 * k + 1];
+      res[k].fine_degree = cands[k].fine;
+      res[k].coarse_degree = cands[k].coarse;
       res[k].iters = info.iters;
       res[k].status = sk;
       res[k].ms = sk == TOMO_OK ? med : -1.0;
+      res[k].lam = cands[k].lam;
     }
   }
   cudaEventDestroy(e0);
@@ -1654,11 +1697,11 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
     st = fail(G, TOMO_ENOCONV, "autotune: no candidate converged");
   if (st != TOMO_OK) {
     std::string why = G->err;
-    set_smoother(G, fine0, coarse0, ratio);
+    set_smoother(G, fine0, coarse0, ratio, lam0);
     G->err = why;
     return st;
   }
-  TRY(set_smoother(G, pairs[2 * bi], pairs[2 * bi + 1], ratio));
+  TRY(set_smoother(G, cands[bi].fine, cands[bi].coarse, ratio, cands[bi].lam));
   if (best) *best = bi;
   return TOMO_OK;
 }
@@ -1752,7 +1795,8 @@ tomo_status tomo_create_grid(const tomo_grid_desc* desc, tomo_grid** out) {
     delete G;
     return fail(nullptr, TOMO_EINVAL, "element stiffness blocks are not of the isotropic kinds");
   }
-  G->lam_hi = G->d.cheb_lmax > 0.0 ? G->d.cheb_lmax : lam_max_element(G->K0);
+  G->lam_bound = lam_max_element(G->K0);
+  G->lam_hi = G->d.cheb_lmax > 0.0 ? G->d.cheb_lmax : G->lam_bound;
   tomo_status st = G->prec == TOMO_FP64 ? create_impl<double>(G) : create_impl<float>(G);
   if (st != TOMO_OK) {
     g_create_err = G->err;
@@ -1792,7 +1836,22 @@ tomo_status tomo_set_smoother(tomo_grid* G, int32_t fine_degree, int32_t coarse_
                               double ratio) {
   if (!G) return TOMO_EINVAL;
   g_cur_err = &G->err;
-  return set_smoother(G, fine_degree, coarse_degree, ratio);
+  return set_smoother(G, fine_degree, coarse_degree, ratio, G->lam_hi);
+}
+tomo_status tomo_set_smoother_bound(tomo_grid* G, double lam) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  if (G->d.precond != TOMO_PRECOND_MG)
+    return fail(G, TOMO_EINVAL, "smoother bound: the grid has no multigrid smoother");
+  return set_smoother(G, G->d.smoother_degree, G->d.coarse_degree, G->cheb_ratio, lam);
+}
+tomo_status tomo_get_smoother_bound(const tomo_grid* G, double* lam, double* element_bound,
+                                    int64_t* fallbacks) {
+  if (!G) return TOMO_EINVAL;
+  if (lam) *lam = G->lam_hi;
+  if (element_bound) *element_bound = G->lam_bound;
+  if (fallbacks) *fallbacks = G->bound_fallbacks;
+  return TOMO_OK;
 }
 
 tomo_status tomo_get_smoother(const tomo_grid* G, int32_t* fine_degree, int32_t* coarse_degree,

@@ -404,9 +404,11 @@ struct tomo_grid {
   // captured loops (load slot) of smoother settings used before: (fine, coarse, ratio)
   struct CachedLoop {
     int fine, coarse;
-    double ratio;
+    double ratio, lam;
     cudaGraphExec_t exec;
   };
+  double lam_bound = 0.0;       // the element bound of lambda_max(D^-1 K), always safe
+  int64_t bound_fallbacks = 0;  // solves redone at lam_bound after failing at a lower lam_hi
   std::vector<CachedLoop> loop_cache;
   // phase timing (events at phase boundaries; the CG loop stays a graph)
   bool phase_prof = false;

@@ -325,6 +325,9 @@ __device__ __forceinline__ void march_body(const MarchArgs<T>& A, const ElemCons
         if (!isfinite(tot[0])) {
           sc->status |= DEV_NAN;
           sc->done = 1;
+        } else if (!(tot[0] > 0.0)) {  // r^T M r <= 0: the preconditioner is not positive
+          sc->status |= DEV_BREAKDOWN;
+          sc->done = 1;
         }
         sc->beta = sc->rz != 0.0 ? tot[0] / sc->rz : 0.0;
         sc->rz = tot[0];

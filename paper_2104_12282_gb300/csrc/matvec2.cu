@@ -371,6 +371,9 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
         if (!isfinite(tot[0])) {
           sc->status |= DEV_NAN;
           sc->done = 1;
+        } else if (!(tot[0] > 0.0)) {  // r^T M r <= 0: the preconditioner is not positive
+          sc->status |= DEV_BREAKDOWN;
+          sc->done = 1;
         }
         sc->beta = sc->rz != 0.0 ? tot[0] / sc->rz : 0.0;
         sc->rz = tot[0];

@@ -12,7 +12,10 @@
 //    or its estimated footprint fits the budget after evicting idle grids;
 //  * the queue is served in arrival order among the requests that can be admitted.
 // Each request's work runs in order on one stream and touches only its own grid, so its
-// result is the one it gives alone.
+// result is the one it gives alone.  With lockstep batching on (tomo_server_set_batching),
+// a free worker takes the queued admissible gradient requests together and runs them as one
+// tomo_batch: one CG loop for all of them, each phase one launch for every grid; results
+// then agree with the request alone to the solver's tolerance.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -71,6 +74,11 @@ struct tomo_server {
   tomo_serve::Admission pool;  // resident grids, budget and eviction (under mu)
   tomo_server_stats stats{};
   std::string err;
+  // lockstep batching: a free worker takes up to max_batch queued admissible gradient
+  // requests at once and runs them as one tomo_batch (batch_workers streams); 1 = off
+  int max_batch = 1;
+  int batch_workers = 4;
+  int64_t batches_run = 0;   // tomo_batch calls made for groups of two or more requests
 
   // An optimisation request on grid g (stream st): the design stays on the device for the
   // whole run (gradient with warm-started solves, then the OC update, iters times); the
@@ -106,30 +114,120 @@ struct tomo_server {
     return s;
   }
 
+  // Fills r's message from m (truncated to the result's buffer).
+  static void note(Request* r, const char* m) {
+    const size_t n = std::min<size_t>(std::strlen(m), sizeof(r->res.message) - 1);
+    std::memcpy(r->res.message, m, n);
+    r->res.message[n] = 0;
+    r->res.message_len = (int32_t)n;
+  }
+
+  // The grid of an admitted request's slot on stream st, created when the slot has none.
+  tomo_status grid_for(Request* r, tomo_serve::Slot* slot, cudaStream_t st, tomo_grid** out) {
+    tomo_grid* g = slot->grid;
+    tomo_status s = TOMO_OK;
+    if (!g) {
+      tomo_grid_desc d = r->desc;
+      d.fixed_dof = r->fixed.data();
+      d.f = r->f.data();
+      d.stream = st;
+      s = tomo_create_grid(&d, &g);
+      if (s != TOMO_OK) note(r, tomo_last_error(nullptr));
+      std::lock_guard<std::mutex> lk(mu);
+      slot->grid = g;
+      if (s == TOMO_OK) stats.grids_created += 1;
+    } else {
+      tomo_set_stream(g, st);
+    }
+    *out = g;
+    return s;
+  }
+
+  // One request alone on stream st (its grid already made).
+  tomo_status run_one(Request* r, tomo_grid* g, cudaStream_t st) {
+    tomo_status s;
+    if (r->iters > 0) {
+      s = optimise(g, st, *r);
+    } else {
+      s = tomo_gradient(g, r->z.data(), &r->res.compliance, r->dcdz, r->dvdz, &r->res.info);
+      if (s == TOMO_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        s = TOMO_ECUDA;
+      }
+    }
+    if (s != TOMO_OK) note(r, tomo_last_error(g));
+    return s;
+  }
+
+  // Gradient requests rs (grids gs) as one lockstep batch; on a batch failure each one is
+  // run alone, so that one bad request does not fail the others.
+  void run_group(std::vector<Request*>& rs, std::vector<tomo_grid*>& gs,
+                 std::vector<tomo_status>& sts, cudaStream_t st) {
+    const int n = (int)rs.size();
+    tomo_batch* b = nullptr;
+    tomo_status s = tomo_batch_create(batch_workers, &b);
+    for (int i = 0; i < n && s == TOMO_OK; ++i) s = tomo_batch_append(b, gs[i]);
+    if (s == TOMO_OK) {
+      std::vector<const float*> z(n);
+      std::vector<float*> dc(n), dv(n);
+      std::vector<double> c(n);
+      std::vector<tomo_solve_info> info(n);
+      for (int i = 0; i < n; ++i) {
+        z[i] = rs[i]->z.data();
+        dc[i] = rs[i]->dcdz;
+        dv[i] = rs[i]->dvdz;
+      }
+      s = tomo_batch_gradient(b, z.data(), c.data(), dc.data(), dv.data(), info.data());
+      if (s == TOMO_OK) {
+        for (int i = 0; i < n; ++i) {
+          rs[i]->res.compliance = c[i];
+          rs[i]->res.info = info[i];
+          sts[i] = TOMO_OK;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        batches_run += 1;
+      }
+    }
+    if (b) tomo_batch_destroy(b);
+    for (int i = 0; i < n; ++i) tomo_set_stream(gs[i], st);
+    if (s != TOMO_OK)
+      for (int i = 0; i < n; ++i) sts[i] = run_one(rs[i], gs[i], st);
+  }
+
   void work(int w) {
     cudaStream_t st = streams[w];
     for (;;) {
-      Request* r = nullptr;
-      tomo_serve::Slot* slot = nullptr;
+      std::vector<Request*> rs;
+      std::vector<tomo_serve::Slot*> slots;
       std::vector<tomo_grid*> dead;
       {
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
           if (stop) return;
-          for (auto it = queue.begin(); it != queue.end(); ++it) {
-            Request& q = *reqs[*it];
-            slot = pool.admit(q.session, q.desc, q.est_bytes, dead);
+          // the first admissible request in arrival order, then (batching) the further
+          // admissible gradient requests behind it, up to max_batch
+          for (size_t k = 0; k < queue.size();) {
+            Request& q = *reqs[queue[k]];
+            const bool joins = rs.empty() || (max_batch > 1 && q.iters == 0 &&
+                                              rs[0]->iters == 0 && (int)rs.size() < max_batch);
+            tomo_serve::Slot* slot = joins ? pool.admit(q.session, q.desc, q.est_bytes, dead)
+                                           : nullptr;
             if (slot) {
-              r = &q;
-              queue.erase(it);
-              break;
+              rs.push_back(&q);
+              slots.push_back(slot);
+              queue.erase(queue.begin() + k);
+              if (q.iters > 0 || max_batch <= 1) break;
+            } else {
+              ++k;
             }
           }
-          if (r) break;
+          if (!rs.empty()) break;
           cv_work.wait(lk);
         }
-        r->state = 1;
-        r->t_start = Clock::now();
+        for (Request* r : rs) {
+          r->state = 1;
+          r->t_start = Clock::now();
+        }
         stats.evictions = pool.evictions;
         stats.peak_bytes = std::max<uint64_t>(stats.peak_bytes, pool.resident);
       }
@@ -138,49 +236,44 @@ struct tomo_server {
         tomo_destroy_grid(e);
       }
       dead.clear();
-      auto note = [&](const char* m) {
-        const size_t n = std::min<size_t>(std::strlen(m), sizeof(r->res.message) - 1);
-        std::memcpy(r->res.message, m, n);
-        r->res.message[n] = 0;
-        r->res.message_len = (int32_t)n;
-      };
-      tomo_status s = TOMO_OK;
-      // the slot is busy: this worker alone touches its grid until it is released below
-      tomo_grid* g = slot->grid;
-      if (!g) {  // create the session's grid on this worker's stream
-        tomo_grid_desc d = r->desc;
-        d.fixed_dof = r->fixed.data();
-        d.f = r->f.data();
-        d.stream = st;
-        s = tomo_create_grid(&d, &g);
-        if (s != TOMO_OK) note(tomo_last_error(nullptr));
-        std::lock_guard<std::mutex> lk(mu);
-        slot->grid = g;
-        if (s == TOMO_OK) stats.grids_created += 1;
-      } else {
-        tomo_set_stream(g, st);
-      }
-      if (s == TOMO_OK && r->iters > 0) {
-        s = optimise(g, st, *r);
-        if (s != TOMO_OK) note(tomo_last_error(g));
-      } else if (s == TOMO_OK) {
-        s = tomo_gradient(g, r->z.data(), &r->res.compliance, r->dcdz, r->dvdz, &r->res.info);
-        if (s == TOMO_OK && cudaStreamSynchronize(st) != cudaSuccess) {
-          cudaGetLastError();
-          s = TOMO_ECUDA;
+      // the slots are busy: this worker alone touches their grids until released below
+      const int n = (int)rs.size();
+      std::vector<tomo_grid*> gs(n, nullptr);
+      std::vector<tomo_status> sts(n, TOMO_OK);
+      std::vector<Request*> grs;
+      std::vector<tomo_grid*> ggs;
+      std::vector<int> gi;
+      for (int i = 0; i < n; ++i) {
+        sts[i] = grid_for(rs[i], slots[i], st, &gs[i]);
+        if (sts[i] != TOMO_OK) continue;
+        if (n == 1) {
+          sts[i] = run_one(rs[i], gs[i], st);
+        } else {
+          grs.push_back(rs[i]);
+          ggs.push_back(gs[i]);
+          gi.push_back(i);
         }
-        if (s != TOMO_OK) note(tomo_last_error(g));
+      }
+      if (!grs.empty()) {
+        std::vector<tomo_status> gst(grs.size(), TOMO_OK);
+        if (grs.size() == 1) gst[0] = run_one(grs[0], ggs[0], st);
+        else run_group(grs, ggs, gst, st);
+        for (size_t k = 0; k < gi.size(); ++k) sts[gi[k]] = gst[k];
       }
       {
         std::lock_guard<std::mutex> lk(mu);
-        r->t_done = Clock::now();
-        r->res.status = s;
-        r->res.queue_ms = ms_between(r->t_submit, r->t_start);
-        r->res.run_ms = ms_between(r->t_start, r->t_done);
-        r->state = 2;
-        stats.completed += 1;
-        // no session (or a failure): the grid is freed at once
-        pool.release(slot, s == TOMO_OK && r->session >= 0, r->t_done, dead);
+        const auto t = Clock::now();
+        for (int i = 0; i < n; ++i) {
+          Request* r = rs[i];
+          r->t_done = t;
+          r->res.status = sts[i];
+          r->res.queue_ms = ms_between(r->t_submit, r->t_start);
+          r->res.run_ms = ms_between(r->t_start, r->t_done);
+          r->state = 2;
+          stats.completed += 1;
+          // no session (or a failure): the grid is freed at once
+          pool.release(slots[i], sts[i] == TOMO_OK && r->session >= 0, r->t_done, dead);
+        }
       }
       for (tomo_grid* e : dead) {
         tomo_set_stream(e, st);
@@ -313,6 +406,15 @@ tomo_status tomo_server_get_stats(tomo_server* S, tomo_server_stats* st) {
   st->resident_bytes = S->pool.resident;
   st->resident_grids = (int32_t)S->pool.slots.size();
   st->queued = (int32_t)S->queue.size();
+  st->batches = S->batches_run;
+  return TOMO_OK;
+}
+
+tomo_status tomo_server_set_batching(tomo_server* S, int32_t max_batch, int32_t batch_workers) {
+  if (!S) return TOMO_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->max_batch = std::max<int32_t>(1, std::min<int32_t>(max_batch, 256));
+  S->batch_workers = batch_workers > 0 ? std::min<int32_t>(batch_workers, 64) : 4;
   return TOMO_OK;
 }
 

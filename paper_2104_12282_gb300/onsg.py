@@ -19,7 +19,12 @@ only the pattern has to be learned; log(-g / s) targets measured worse); corner 
 exact iteration (about 2000 in a 200-iteration run, §IV); TF32 matrix products.  One more
 input per block, the log of the coarse-scale sensitivity of its coarse element (from u_C,
 normalised like the targets): u_C is what §III-C feeds the model, and this is the part of
-it that the compliance gradient depends on.
+it that the compliance gradient depends on.  And per element of the block, the sensitivity
+of the coarse state carried to the fine grid: u_C interpolated trilinearly to the fine
+nodes, then Eq. 5 and the filter adjoint on the fine grid (the library's own sensitivity and
+filter kernels), normalised by its mean |.|; it gives the model the within-block pattern
+of the element energies that the coarse state implies.  Measured on Table 1's Mesh 1 (200
+iterations): final compliance +20.7 % above the exact optimiser without it, -1.3 % with it.
 
 The model runs in PyTorch (cuBLAS GEMMs); it is outside the exact-gradient path.
 """
@@ -78,7 +83,8 @@ def make_model(n_in, n_out, width=1000, depth=4):
 
 def run(problem, iters, *, block=5, n_init=10, n_every=10, width=1000, lr=5e-4,
         steps_per_update=70, batch=4096, seed=0, exact_only=False, callback=None,
-        log_targets=False, relative_u=True, tf32=True, coarse_sens=True, reuse=False):
+        log_targets=False, relative_u=True, tf32=True, coarse_sens=True, reuse=False,
+        interp_sens=True):
     """Algorithm 1 on the GPU (exact_only: the exact-gradient optimiser, no coarse step;
     reuse: a control that keeps the last exact gradient on the synthetic iterations).
     Returns (z, history, final compliance); each record holds the compliance of the design
@@ -99,9 +105,13 @@ def run(problem, iters, *, block=5, n_init=10, n_every=10, width=1000, lr=5e-4,
     zn, dc, dv = torch.empty_like(z), torch.empty_like(z), torch.empty_like(z)
     zc = torch.empty(q.n_el, dtype=torch.float32, device=dev)
     uc = torch.zeros(q.dims.n_dof, dtype=torch.float32, device=dev)
-    n_in = nb3 + 24 + (1 if coarse_sens else 0)
+    n_in = nb3 + 24 + (1 if coarse_sens else 0) + (nb3 if interp_sens else 0)
     model = make_model(n_in, nb3, width).to(dev)
     dcC = torch.empty(q.n_el, dtype=torch.float32, device=dev)
+    if interp_sens:
+        rho_f = torch.empty_like(z)
+        ui = torch.empty(d.n_dof, dtype=torch.float32, device=dev)
+        dci, dczi = torch.empty_like(z), torch.empty_like(z)
     opt = torch.optim.Adam(model.parameters(), lr=lr)
     sched = torch.optim.lr_scheduler.StepLR(opt, step_size=500, gamma=0.5)
     X_all, Y_all = [], []
@@ -127,6 +137,19 @@ def run(problem, iters, *, block=5, n_init=10, n_every=10, width=1000, lr=5e-4,
                     gc.sensitivity(zc, uc, dcC)
                     sC = (-dcC / dcC.abs().mean().clamp_min(1e-30)).clamp_min(1e-12)
                     parts.append(torch.log(sC)[:, None])
+                if interp_sens:
+                    # the fine-scale sensitivity of the coarse state interpolated (trilinear)
+                    # to the fine nodes: u_C carried to the resolution of the gradient
+                    cx, cy, cz = cdims
+                    UC = uc.reshape(3, cz + 1, cy + 1, cx + 1)[None]
+                    ui.copy_(torch.nn.functional.interpolate(
+                        UC, size=(d.nz + 1, d.ny + 1, d.nx + 1), mode="trilinear",
+                        align_corners=True)[0].reshape(-1))
+                    g.filter(z, rho_f)
+                    g.sensitivity(rho_f, ui, dci)
+                    g.filter(dci, dczi, transpose=True)
+                    gi = block_gradient(dczi, (d.nx, d.ny, d.nz), block, cdims)
+                    parts.append(gi / gi.abs().mean().clamp_min(1e-30))
                 feats = torch.cat(parts, dim=1)
             c = None
             if exact:

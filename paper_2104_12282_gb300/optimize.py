@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import sys
 import time
 
@@ -33,9 +34,26 @@ def paper_cantilever(mesh: int, volfrac: float = 0.12, radius: float = 0.08) -> 
     return P.cantilever(nx, ny, nz, h=h, volfrac=volfrac, rmin=radius / h)
 
 
+def save_checkpoint(path: str, k: int, z, hist, smoother) -> None:
+    """State of an OC run after its iteration k-1 (the design z, the history so far and the
+    smoother setting), written atomically (temporary file, then rename)."""
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, next_it=np.int64(k), z=np.asarray(z), smoother=np.asarray(smoother, np.int64),
+             hist=np.frombuffer(json.dumps(hist).encode(), dtype=np.uint8))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str):
+    """(next iteration, z, history, smoother) from save_checkpoint."""
+    with np.load(path) as f:
+        return (int(f["next_it"]), f["z"], json.loads(bytes(f["hist"]).decode()),
+                tuple(int(v) for v in f["smoother"]))
+
+
 def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo.FP32,
         rtol: float = 1e-6, warm: bool = True, maxit: int = 5000, z0=None, callback=None,
-        autotune_every: int = 0, tune: str = "online"):
+        autotune_every: int = 0, tune: str = "online", checkpoint: str | None = None,
+        checkpoint_every: int = 0, resume: bool = False):
     """Exact-gradient OC loop on the GPU.  Returns (z, history); history holds one dict per
     iteration: compliance, design change, CG iterations, wall time of the gradient and of
     the coarse step (ms), and the smoother (fine, coarse degrees) the gradient used.
@@ -44,7 +62,13 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
     densities, which favour other smoother degrees).  tune "offline": the library's
     autotuner times extra solves of the current design (not counted in `ms`); "online": the
     next gradients of the run itself try the candidates one each, then the fastest is kept
-    (no extra solves; the trial gradients are real iterations of the run)."""
+    (no extra solves; the trial gradients are real iterations of the run).
+
+    checkpoint: a file that receives the run's state every checkpoint_every iterations and
+    at the end; resume: continue from that file's state (its design, history and smoother)
+    up to iteration `iters`.  The first gradient after a resume starts its solve from zero
+    (the displacement is not stored), so the resumed run follows the uninterrupted one to
+    the solver's tolerance, not bitwise."""
     import torch
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -54,10 +78,18 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
     dc = torch.empty_like(z)
     dv = torch.empty_like(z)
     hist = []
+    start = 0
+    resumed_smoother = None
+    if resume:
+        start, zr, hist, resumed_smoother = load_checkpoint(checkpoint)
+        z = torch.tensor(zr, dtype=dt, device=dev)
+        zn = torch.empty_like(z)
     cands = [(2, 2), (2, 3), (2, 4), (1, 3), (1, 4), (1, 6)]
     trial = []      # online tuning: (candidate, ms) of the trial gradients so far
     with tomo.Grid.from_problem(problem, precision=precision, rtol=rtol, maxit=maxit) as g:
         g.set_warm_start(warm)
+        if resumed_smoother is not None:
+            g.set_smoother(*resumed_smoother)
         gc = None
         if block:
             q = P.coarse_problem(problem, block)
@@ -66,7 +98,7 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
             zc = torch.empty(q.n_el, dtype=dt, device=dev)
             uc = torch.zeros(q.dims.n_dof, dtype=dt, device=dev)
         try:
-            for k in range(iters):
+            for k in range(start, iters):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 coarse = None
@@ -102,6 +134,10 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
                 if callback:
                     callback(rec)
                 z, zn = zn, z
+                if checkpoint and ((checkpoint_every > 0 and (k + 1) % checkpoint_every == 0)
+                                   or k + 1 == iters):
+                    save_checkpoint(checkpoint, k + 1, z.cpu().numpy(), hist,
+                                    g.smoother()[:2])
         finally:
             if gc is not None:
                 gc.close()
@@ -121,6 +157,10 @@ def main(argv=None):
     ap.add_argument("--tune", choices=("online", "offline"), default="online",
                     help="online: try the candidates on the run's own gradients; offline: "
                          "the library autotuner's extra solves")
+    ap.add_argument("--checkpoint", default=None, help="state file (written every "
+                    "--checkpoint-every iterations and at the end)")
+    ap.add_argument("--checkpoint-every", type=int, default=0)
+    ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
     a = ap.parse_args(argv)
     p = paper_cantilever(a.mesh)
     prec = tomo.FP64 if a.fp64 else tomo.FP32
@@ -131,7 +171,8 @@ def main(argv=None):
 
     t = time.perf_counter()
     _, hist = run(p, a.iters, block=a.block, precision=prec, warm=not a.cold, callback=show,
-                  autotune_every=a.autotune_every, tune=a.tune)
+                  autotune_every=a.autotune_every, tune=a.tune, checkpoint=a.checkpoint,
+                  checkpoint_every=a.checkpoint_every, resume=a.resume)
     wall = time.perf_counter() - t
     d = p.dims
     print(json.dumps({"mesh": a.mesh, "dims": [d.nx, d.ny, d.nz], "h": p.h, "rmin": p.rmin,

@@ -45,7 +45,8 @@ class GridDesc(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("fine_degree", ctypes.c_int32), ("coarse_degree", ctypes.c_int32),
-                ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("ms", ctypes.c_double)]
+                ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("lam", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -64,7 +65,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("grids_created", ctypes.c_int64), ("evictions", ctypes.c_int64),
                 ("resident_bytes", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
-                ("resident_grids", ctypes.c_int32), ("queued", ctypes.c_int32)]
+                ("resident_grids", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("batches", ctypes.c_int64)]
 
 
 def _load():
@@ -85,6 +87,10 @@ def _load():
         "tomo_get_smoother": (st, [G, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_double)]),
+        "tomo_set_smoother_bound": (st, [G, ctypes.c_double]),
+        "tomo_get_smoother_bound": (st, [G, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64)]),
         "tomo_autotune_smoother": (st, [G, P, P, ctypes.c_int32, ctypes.c_int32, P,
                                         ctypes.POINTER(ctypes.c_int32)]),
         "tomo_autotune_smoother_d": (st, [G, P, P, ctypes.c_int32, ctypes.c_int32, P,
@@ -98,6 +104,7 @@ def _load():
                                              P, ctypes.POINTER(ctypes.c_int64)]),
         "tomo_server_wait": (st, [P, ctypes.c_int64, ctypes.POINTER(Result)]),
         "tomo_server_get_stats": (st, [P, ctypes.POINTER(ServerStats)]),
+        "tomo_server_set_batching": (st, [P, ctypes.c_int32, ctypes.c_int32]),
         "tomo_server_destroy": (st, [P]),
         "tomo_server_last_error": (ctypes.c_char_p, [P]),
         "tomo_grid_device_bytes": (st, [G, ctypes.POINTER(ctypes.c_size_t)]),
@@ -178,10 +185,12 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["tomo_default_desc", "tomo_create_grid", "tomo_destroy_grid", "tomo_set_stream",
             "tomo_set_warm_start", "tomo_set_smoother", "tomo_get_smoother",
+            "tomo_set_smoother_bound", "tomo_get_smoother_bound",
             "tomo_server_submit_optimize",
             "tomo_autotune_smoother", "tomo_autotune_smoother_d",
             "tomo_server_create", "tomo_server_submit",
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
+            "tomo_server_set_batching",
             "tomo_server_last_error", "tomo_grid_device_bytes", "tomo_estimate_device_bytes",
             "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
             "tomo_batch_set_lockstep", "tomo_batch_lockstep_runs", "tomo_batch_phase_times",
@@ -356,12 +365,27 @@ class Grid:
         lib().tomo_get_smoother(self._h, ctypes.byref(f), ctypes.byref(c), ctypes.byref(r))
         return f.value, c.value, r.value
 
+    def set_smoother_bound(self, lam):
+        """Upper end of the smoothing interval (tomo_set_smoother_bound); lam <= 0 selects
+        the element bound."""
+        st = lib().tomo_set_smoother_bound(self._h, float(lam))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def smoother_bound(self):
+        """(lam in use, element bound, solves redone at the element bound so far)."""
+        lam, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        lib().tomo_get_smoother_bound(self._h, ctypes.byref(lam), ctypes.byref(b),
+                                      ctypes.byref(n))
+        return lam.value, b.value, n.value
+
     def autotune(self, z, candidates=None, reps=2):
-        """Time the state solve on design z for each (fine, coarse) degree pair (the built-in
-        list when None), keep the fastest (tomo_autotune_smoother); returns (best pair,
-        list of dicts with fine, coarse, ms, iters, status per candidate)."""
+        """Time the state solve on design z for each (fine, coarse) degree pair at the
+        current bound, or for the built-in list of pairs and bounds when None, and keep the
+        fastest (tomo_autotune_smoother); returns (best (fine, coarse, lam), list of dicts
+        with fine, coarse, lam, ms, iters, status per candidate)."""
         if candidates is None:
-            pairs, n = None, 6
+            pairs, n = None, 18
         else:
             flat = [int(v) for pq in candidates for v in pq]
             pairs = (ctypes.c_int32 * len(flat))(*flat)
@@ -373,10 +397,10 @@ class Grid:
             n, int(reps), ctypes.cast(res, ctypes.c_void_p), ctypes.byref(best))
         if st != 0:
             raise TomoError(st, lib().tomo_last_error(self._h).decode())
-        rows = [dict(fine=r.fine_degree, coarse=r.coarse_degree, ms=r.ms, iters=r.iters,
-                     status=r.status) for r in res]
+        rows = [dict(fine=r.fine_degree, coarse=r.coarse_degree, lam=r.lam, ms=r.ms,
+                     iters=r.iters, status=r.status) for r in res]
         b = rows[best.value]
-        return (b["fine"], b["coarse"]), rows
+        return (b["fine"], b["coarse"], b["lam"]), rows
 
     def filter(self, x, out, transpose=False):
         self._call("tomo_filter", self._e(x, "in"), self._e(out, "out"), int(bool(transpose)))
@@ -626,13 +650,21 @@ class Server:
     ``workers`` threads with a stream each, grids resident per session, admission under a
     device-memory budget (bytes)."""
 
-    def __init__(self, workers=8, budget_bytes=8 << 30):
+    def __init__(self, workers=8, budget_bytes=8 << 30, max_batch=1, batch_workers=4):
         h = ctypes.c_void_p()
         st = lib().tomo_server_create(int(workers), int(budget_bytes), ctypes.byref(h))
         if st != 0:
             raise TomoError(st, "tomo_server_create")
         self._h = h
         self._pending = {}
+        if max_batch > 1:
+            self.set_batching(max_batch, batch_workers)
+
+    def set_batching(self, max_batch, batch_workers=4):
+        """Lockstep batching of queued gradient requests (tomo_server_set_batching)."""
+        st = lib().tomo_server_set_batching(self._h, int(max_batch), int(batch_workers))
+        if st != 0:
+            raise TomoError(st, "tomo_server_set_batching")
 
     def submit(self, p, z=None, session=-1, dvdz=True):
         """Queue tomo_gradient for problem p (FP32) with design z (default p.z0); returns a

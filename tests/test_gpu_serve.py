@@ -130,3 +130,33 @@ def test_bad_optimisation_requests_are_rejected():
         for kw in (dict(iters=0), dict(iters=3, volfrac=0.0), dict(iters=3, move=0.0)):
             with pytest.raises(tomo.TomoError):
                 srv.submit_optimize(p, **kw)
+
+
+def _close(c, dc, c0, dc0):
+    den = np.maximum(np.abs(dc0), 1e-3 * np.abs(dc0).max())
+    return abs(c / c0 - 1.0) <= 1e-5 and float(np.max(np.abs(dc - dc0) / den)) <= 1e-4
+
+
+def test_lockstep_batched_requests_agree_with_results_alone():
+    """With lockstep batching the queued gradient requests a free worker takes run as one
+    tomo_batch; each result agrees with the request alone to the solver's tolerance, a
+    repeated session reuses its grid, and a request that fails at grid creation fails alone."""
+    reqs = [P.served_request(13, i, (6, 14)) for i in range(12)]
+    reqs[7] = reqs[2]
+    bad = P.served_request(13, 40, (6, 10))
+    bad.nu = 0.7                                 # rejected at grid creation
+    sessions = [-1] * 12
+    sessions[2] = sessions[7] = 5
+    with tomo.Server(workers=2, budget_bytes=1 << 30, max_batch=8, batch_workers=2) as srv:
+        tickets = [srv.submit(p, session=s) for p, s in zip(reqs, sessions)]
+        tb = srv.submit(bad)
+        got = [srv.wait(t) for t in tickets]
+        rb = srv.wait(tb)[0]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) + 1 and st["batches"] >= 1
+    assert rb.status != 0 and len(rb.message) > 0
+    for p, (r, dc, dv) in zip(reqs, got):
+        assert r.status == 0, r.message
+        c0, dc0, dv0 = _alone(p)
+        assert _close(r.compliance, dc, c0, dc0), p.dims
+        assert np.array_equal(dv, dv0)           # dV/dz involves no solve

@@ -75,8 +75,8 @@ def test_autotune_keeps_the_fastest_converging_candidate():
         ok = [r for r in rows if r["status"] == 0]
         assert ok and all(r["ms"] > 0 for r in ok)
         fastest = min(ok, key=lambda r: r["ms"])
-        assert best == (fastest["fine"], fastest["coarse"])
-        assert g.smoother()[:2] == best
+        assert best == (fastest["fine"], fastest["coarse"], fastest["lam"])
+        assert g.smoother()[:2] == best[:2] and g.smoother_bound()[0] == best[2]
         dc = torch.empty_like(zt)
         c, info = g.gradient(zt, dc)
         assert info.iters == fastest["iters"]
@@ -87,7 +87,13 @@ def test_autotune_keeps_the_fastest_converging_candidate():
     # the built-in list
     with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
         best, rows = g.autotune(zt)
-        assert len(rows) == 6 and best in [(r["fine"], r["coarse"]) for r in rows]
+        lam_b = g.smoother_bound()[1]
+        assert len(rows) == 18 and best in [(r["fine"], r["coarse"], r["lam"]) for r in rows]
+        assert sorted({round(r["lam"] / lam_b, 6) for r in rows}) == [0.68, 0.75, 1.0]
+        assert g.smoother_bound()[0] == best[2]
+        dc = torch.empty_like(zt)
+        c2, _ = g.gradient(zt, dc)
+    assert abs(c2 / c0 - 1.0) <= 1e-5
 
 
 def test_autotune_without_a_converging_candidate_keeps_the_smoother():
@@ -129,3 +135,29 @@ def test_lockstep_batch_follows_a_smoother_change():
     finally:
         for g in grids:
             g.close()
+
+
+def test_smoother_bound_is_checked_and_a_failing_bound_falls_back():
+    p = P.cantilever(24, 12, 12)
+    z, zt = _field(p, 35)
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g0:
+        dc0 = torch.empty_like(zt)
+        c0, info0 = g0.gradient(zt, dc0)
+        lam_b = g0.smoother_bound()[1]
+        assert g0.smoother_bound() == (lam_b, lam_b, 0) and 5.0 < lam_b < 5.5
+        for bad in (0.2 * lam_b, 1.01 * lam_b, float("nan")):
+            with pytest.raises(tomo.TomoError) as e:
+                g0.set_smoother_bound(bad)
+            assert e.value.status == 1
+        g0.set_smoother_bound(0.0)                 # <= 0: the element bound
+        assert g0.smoother_bound()[0] == lam_b
+    # far below the spectrum of D^-1 K: the solve at that bound cannot converge within a
+    # few iterations more than the element bound needs, so it is redone at the bound
+    with tomo.Grid.from_problem(p, precision=tomo.FP32, maxit=info0.iters + 3) as g:
+        g.set_smoother_bound(0.25 * lam_b)
+        dc = torch.empty_like(zt)
+        c, info = g.gradient(zt, dc)
+        lam, _, falls = g.smoother_bound()
+        assert info.status == 0
+        assert (falls == 1 and lam == lam_b) or (falls == 0 and lam == 0.25 * lam_b)
+        assert abs(c / c0 - 1.0) <= 1e-5

@@ -145,17 +145,19 @@ def test_optimisation_driver_follows_the_oracle():
 
 
 def test_synthetic_gradients_follow_the_exact_optimiser():
-    """Algorithm 1 (ONSG) on a small cantilever: exact gradients on iterations 0-9 and every
-    10th after, synthetic ones (model trained online) in between.  The run completes with a
-    design whose compliance is finite and of the exact optimiser's order: the quality of
-    the synthetic gradients depends on readings the paper leaves open (features, training),
-    and measured at the paper's meshes it stays 11-38 % above the exact optimiser."""
+    """Algorithm 1 (ONSG) on Table 1's Mesh 1 (70x35x35 cantilever, block 5, 200
+    iterations, N_I = N_F = 10): exact gradients on iterations 0-9 and every 10th after,
+    synthetic ones (model trained online) in between.  Table 2 puts the paper's final
+    compliance within 0.5 % of its standard optimiser on the cantilever meshes; this reading
+    of the model's inputs (features documented in onsg.py) is held to 3 % of the exact
+    optimiser run with the same library (measured -1.3 %)."""
     from paper_2104_12282_gb300 import onsg
+    from paper_2104_12282_gb300.optimize import paper_cantilever
 
-    p = P.cantilever(40, 20, 20, volfrac=0.12, rmin=2.0)
-    _, h_ex, c_ex = onsg.run(p, 40, block=5, exact_only=True)
-    _, h_sg, c_sg = onsg.run(p, 40, block=5)
-    assert sum(r["exact"] for r in h_ex) == 40
-    assert sum(r["exact"] for r in h_sg) == 10 + 3
+    p = paper_cantilever(1)
+    _, h_ex, c_ex = onsg.run(p, 200, block=5, exact_only=True)
+    _, h_sg, c_sg = onsg.run(p, 200, block=5)
+    assert sum(r["exact"] for r in h_ex) == 200
+    assert sum(r["exact"] for r in h_sg) == 10 + 19
     assert all(r["c"] is not None for r in h_sg if r["exact"])
-    assert np.isfinite(c_sg) and 0.5 * c_ex <= c_sg <= 10.0 * c_ex
+    assert np.isfinite(c_sg) and abs(c_sg / c_ex - 1.0) <= 0.03, (c_sg, c_ex)
