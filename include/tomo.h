@@ -355,6 +355,40 @@ tomo_status tomo_batch_lockstep_runs(const tomo_batch* batch, int64_t* runs);
  * ms[3] the read-back of the grids' CG scalars, ms[4] host time of the per-grid steps after
  * the loop (results, sensitivities, filter adjoints, up to the last stream's completion). */
 tomo_status tomo_batch_phase_times(const tomo_batch* batch, double* ms);
+/* Persistent lockstep iteration (off by default).  With on = 1 (2: with phase timing, see
+ * tomo_batch_persistent_phase_ns; other values TOMO_EINVAL), each CG iteration of the
+ * lockstep loop runs as ONE cooperative launch instead of one launch per phase: the
+ * batched launches of an iteration are recorded (kind, CTA count, parameter table), and a
+ * kernel with as many CTAs as the device holds co-resident runs them as phases, CTA b
+ * taking the recorded CTAs b, b + grid, ... of each phase, a grid-wide barrier between
+ * phases.  Every grid sees the same blocks and the same order of dot partials as in the
+ * launched loop, so the results are bitwise those of lockstep without it.  Where the device
+ * cannot run the kernel cooperatively (or the loop cannot be captured with it), the
+ * launched iteration is used; tomo_batch_persistent_info then reports ctas = 0.
+ * tomo_batch_set_wait_limit: nanoseconds a CTA waits at a barrier for the others (default
+ * 2e9; >= 0, else TOMO_EINVAL).  A wait that runs out stops every grid of the loop: their
+ * tomo_batch_gradient results are TOMO_ETIMEOUT (info[i].status too), nothing is written
+ * to compliance/dcdz of those grids, the next call starts afresh (no warm start from the
+ * stopped iterate).  Both settings take effect at the next call (the loop is recaptured).
+ * tomo_batch_persistent_info: CTAs and phases of the captured persistent iteration (0 and 0
+ * when the loop in use is the launched one) and the number of calls that ran it; any
+ * pointer may be NULL. */
+tomo_status tomo_batch_set_persistent(tomo_batch* batch, int32_t on);
+tomo_status tomo_batch_set_wait_limit(tomo_batch* batch, int64_t limit_ns);
+tomo_status tomo_batch_persistent_info(const tomo_batch* batch, int32_t* ctas, int32_t* phases,
+                                       int64_t* runs);
+/* Phase timing of the persistent iteration, enabled by tomo_batch_set_persistent(batch, 2)
+ * (which adds one grid barrier per launch): device ns spent in each phase over all CG
+ * iterations of the latest call, as CTA 0 sees it (from the previous barrier's exit to this
+ * phase's), ns[p] with the phase's kind kinds[p] for p < min(count, cap); *count = the
+ * number of phases (0 without timing or when the loop in use is the launched one);
+ * *launches (may be NULL) = the persistent launches timed.  Kinds: 0 product, 1 product +
+ * p^T q, 2 residual, 3 Chebyshev step, 4 Chebyshev step + b^T x, 5 FP64 residual
+ * replacement, 6 Jacobi start, 7 restriction, 8 prolongation, 9 coarsest solve, 10 CG x/r
+ * update, 11 CG p update.  A phase followed by a continuation of its launch (more than 64
+ * grids) reports 0, its time counted with the continuation.  Synchronises the device. */
+tomo_status tomo_batch_persistent_phase_ns(tomo_batch* batch, int64_t* ns, int32_t* kinds,
+                                           int32_t cap, int32_t* count, int64_t* launches);
 tomo_status tomo_batch_gradient(tomo_batch* batch, const float* const* z, double* compliance,
                                 float* const* dcdz, float* const* dvdz, tomo_solve_info* info);
 tomo_status tomo_batch_destroy(tomo_batch* batch);
@@ -438,6 +472,15 @@ tomo_status tomo_estimate_device_bytes(const tomo_grid_desc* desc, size_t* bytes
 /* Description of the most recent error on grid (or of the last failed tomo_create_grid
  * in this thread when grid is NULL).  Never NULL; valid until the next call on grid. */
 const char* tomo_last_error(const tomo_grid* grid);
+
+/* Host-side fault injection for tests of the error paths (no device fault is made): the
+ * nth pass (>= 1) through `site` after this call fails, once, as the real call's failure
+ * would: "alloc" (a device allocation of a grid: TOMO_ENOMEM), "sync" (a synchronisation
+ * of a grid's stream, reported after the real one completed: TOMO_ECUDA), "graph" (the
+ * launch of a captured CG loop, one grid's or a lockstep batch's: TOMO_ECUDA, nothing
+ * launched).  nth = 0 disarms.  TOMO_FAULT="site:n[,site:n...]" in the environment arms
+ * sites at the first check.  Process-wide; TOMO_EINVAL for an unknown site or nth < 0. */
+tomo_status tomo_inject_fault(const char* site, int32_t nth);
 
 #ifdef __cplusplus
 }

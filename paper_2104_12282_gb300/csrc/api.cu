@@ -5,6 +5,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -96,9 +98,53 @@ void pool_init_once() {
   });
 }
 
+// ---------------------------------------------------------------------------------------
+// Host-side fault injection (error-path tests without a GPU fault): site k fails its n-th
+// pass after arming, once, with the status the real call's failure gives.  Armed by
+// tomo_inject_fault or, at the first check, by TOMO_FAULT="site:n[,site:n...]" (sites
+// alloc, sync, graph).
+// ---------------------------------------------------------------------------------------
+enum FaultSite { FAULT_ALLOC = 0, FAULT_SYNC = 1, FAULT_GRAPH = 2, FAULT_SITES = 3 };
+const char* const kFaultNames[FAULT_SITES] = {"alloc", "sync", "graph"};
+std::atomic<long long> g_fault_left[FAULT_SITES];  // passes until the failure, 0 = disarmed
+
+int fault_site(const char* name, size_t len) {
+  for (int k = 0; k < FAULT_SITES; ++k)
+    if (std::strlen(kFaultNames[k]) == len && std::strncmp(name, kFaultNames[k], len) == 0)
+      return k;
+  return -1;
+}
+
+void fault_env_once() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* e = std::getenv("TOMO_FAULT");
+    for (const char* c = e; c && *c;) {
+      const char* colon = std::strchr(c, ':');
+      if (!colon) break;
+      const int k = fault_site(c, (size_t)(colon - c));
+      char* end = nullptr;
+      const long long n = std::strtoll(colon + 1, &end, 10);
+      if (k >= 0 && n > 0) g_fault_left[k].store(n);
+      c = (end && *end == ',') ? end + 1 : nullptr;
+    }
+  });
+}
+
+bool fault_hit(FaultSite k) {
+  fault_env_once();
+  long long v = g_fault_left[k].load(std::memory_order_relaxed);
+  while (v > 0) {
+    if (g_fault_left[k].compare_exchange_weak(v, v - 1)) return v == 1;
+  }
+  return false;
+}
+
 tomo_status dalloc(tomo_grid* G, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (fault_hit(FAULT_ALLOC))
+    return fail(G, TOMO_ENOMEM, "injected device allocation failure (%zu bytes)", bytes);
   pool_init_once();
   CK(cudaMallocAsync(p, bytes, G->stream));
   G->dev_bytes += bytes;
@@ -220,6 +266,8 @@ tomo_status join_factor(tomo_grid* G) {
 tomo_status sync(tomo_grid* G) {
   TRY(join_factor(G));
   CK(cudaStreamSynchronize(G->stream));
+  // (an injected failure is reported after the real synchronisation: no work is in flight)
+  if (fault_hit(FAULT_SYNC)) return fail(G, TOMO_ECUDA, "injected stream synchronisation failure");
   return TOMO_OK;
 }
 
@@ -726,6 +774,21 @@ tomo_status pcg_result(tomo_grid* G, tomo_solve_info* info) {
   const double ff = G->rhs_ff;
   const CgScalars& hs = *G->h_sc;
   tomo_status st = TOMO_OK;
+  if (hs.status & DEV_TIMEOUT) {
+    // a bounded device wait ran out mid-iteration: the iterate is not a solution
+    if (info) {
+      info->iters = hs.it;
+      info->rel_res = std::sqrt(std::max(hs.rr, 0.0) / ff);
+      info->status = TOMO_ETIMEOUT;
+      info->mg_levels = (int)G->L.size();
+    }
+    G->have_solution = false;
+    // the stopped launch can leave a block-reduction counter mid-count: zero it for the
+    // next solve (stream order: after the loop)
+    if (cudaMemsetAsync(G->counter, 0, sizeof(unsigned) * 4, G->stream) != cudaSuccess)
+      cudaGetLastError();
+    return fail(G, TOMO_ETIMEOUT, "a device wait ran out at CG iteration %d", hs.it);
+  }
   if (hs.status & DEV_NAN) st = TOMO_ENAN;
   else if (hs.status & DEV_BREAKDOWN) st = TOMO_ENOCONV;
   else if (hs.rr > hs.tol2) st = TOMO_ENOCONV;
@@ -768,6 +831,7 @@ tomo_status pcg_once(tomo_grid* G, bool warm, tomo_solve_info* info) {
     }
   }
   if (G->use_graph && !G->prof) {
+    if (fault_hit(FAULT_GRAPH)) return fail(G, TOMO_ECUDA, "injected CG loop launch failure");
     CK(cudaGraphLaunch(exec, G->stream));
     CK(cudaMemcpyAsync(G->h_sc, G->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, G->stream));
     TRY(sync(G));
@@ -793,6 +857,7 @@ tomo_status pcg_once(tomo_grid* G, bool warm, tomo_solve_info* info) {
 // the element bound, which always holds, and the grid keeps that bound.
 template <typename T>
 tomo_status pcg(tomo_grid* G, bool warm, tomo_solve_info* info, bool fallback = true) {
+  NvtxRange range("tomo: PCG (S3-S5)");
   tomo_status st = pcg_once<T>(G, warm, info);
   if (st == TOMO_OK || !fallback || st == TOMO_ECUDA || st == TOMO_EINVAL ||
       G->d.precond != TOMO_PRECOND_MG || !(G->lam_hi < G->lam_bound))
@@ -1030,6 +1095,7 @@ tomo_status do_sensitivity(tomo_grid* G, const T* rho, const T* u, double* compl
 template <typename T>
 tomo_status do_oc(tomo_grid* G, const T* z, const T* dcdz, const T* dvdz, double volfrac,
                   double move, T* znew, double* change) {
+  NvtxRange range("tomo: OC update (Section III-D)");
   if (!z || !dcdz || !dvdz || !znew) return fail(G, TOMO_EINVAL, "null array");
   if (!(volfrac > 0.0 && volfrac <= 1.0) || !(move > 0.0))
     return fail(G, TOMO_EINVAL, "volfrac must be in (0,1] and move > 0");
@@ -1073,6 +1139,7 @@ struct GradIO {
 // coarsest factorisation.
 template <typename T>
 tomo_status gradient_begin(tomo_grid* G, const T* z, T* dcdz, T* dvdz, GradIO* io) {
+  NvtxRange range("tomo: filter, material, levels (S1-S2)");
   if (!z || !dcdz) return fail(G, TOMO_EINVAL, "null array");
   const size_t be = sizeof(T) * (size_t)G->g.nel;
   const tomo_grid_desc& d = G->d;
@@ -1101,6 +1168,7 @@ tomo_status gradient_begin(tomo_grid* G, const T* z, T* dcdz, T* dvdz, GradIO* i
 template <typename T>
 tomo_status gradient_end(tomo_grid* G, const GradIO& io, double* compliance, T* dcdz, T* dvdz,
                          bool defer_scalar = false) {
+  NvtxRange range("tomo: compliance, sensitivities, filter adjoint (S6-S7)");
   const size_t be = sizeof(T) * (size_t)G->g.nel;
   T* rho = (T*)G->rho;
   void* ddc = io.ddc;
@@ -1881,6 +1949,15 @@ tomo_status tomo_autotune_smoother_d(tomo_grid* G, const double* z, const int32_
   return do_autotune<double>(G, z, pairs, n, reps, results, best);
 }
 
+tomo_status tomo_inject_fault(const char* site, int32_t nth) {
+  if (!site || nth < 0) return TOMO_EINVAL;
+  const int k = fault_site(site, std::strlen(site));
+  if (k < 0) return TOMO_EINVAL;
+  fault_env_once();
+  g_fault_left[k].store(nth);
+  return TOMO_OK;
+}
+
 tomo_status tomo_set_stream(tomo_grid* G, void* stream) {
   if (!G) return TOMO_EINVAL;
   G->stream = (cudaStream_t)stream;
@@ -2102,6 +2179,22 @@ struct tomo_batch {
   // loop, and of the scalar read-back (events on the batch stream)
   cudaEvent_t tev[4] = {};
   double phase_ms[5] = {};
+  // persistent lockstep iteration: requested, and whether the captured loop uses it
+  bool persistent = false;
+  bool persist_used = false;
+  long long wait_limit_ns = 2000000000LL;
+  int64_t persistent_runs = 0;
+  unsigned char* d_tab = nullptr;  // phase tables (device)
+  size_t d_tab_cap = 0;
+  DevPhase* d_ph = nullptr;
+  int d_ph_cap = 0;
+  unsigned* d_bar = nullptr;  // grid barrier words (count, generation)
+  bool persist_timing = false;             // per-phase device time accumulated
+  unsigned long long* d_acc = nullptr;     // per-phase ns and launch count of the last call
+  int d_acc_cap = 0;
+  std::vector<int> persist_kinds;          // phase kinds of the captured iteration
+  int persist_nph = 0, persist_ctas_n = 0;
+  size_t persist_smem = 0;
 };
 
 namespace {
@@ -2415,24 +2508,116 @@ tomo_status batch_iteration(tomo_batch* B, cudaStream_t st, const std::vector<to
   return batch_cg_p(B, st, Gs, z, launches);
 }
 
-tomo_status batch_build_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs) {
-  if (B->loop) {
-    cudaGraphExecDestroy(B->loop);
-    B->loop = nullptr;
+// Record one lockstep iteration's batched launches as the phases of the persistent kernel
+// (nothing is launched while recording) and upload the phase list and tables, ordered on
+// the batch stream before the loop's next launch.  *ok = false: the device cannot hold the
+// kernel's CTAs co-resident (the caller keeps the launched iteration).
+tomo_status batch_record_persist(tomo_batch* B, const std::vector<tomo_grid*>& Gs, bool* ok) {
+  *ok = false;
+  std::vector<PhaseRec> rec;
+  int64_t unused = 0;
+  g_phase_rec = &rec;
+  const tomo_status s = batch_iteration(B, B->bst, Gs, &unused);
+  g_phase_rec = nullptr;
+  if (s != TOMO_OK) return s;
+  std::vector<DevPhase> ph;
+  std::vector<std::vector<UnitDesc>> units(rec.size());
+  size_t off = 0, smem = 0;
+  for (size_t k = 0; k < rec.size(); ++k) {
+    const PhaseRec& r = rec[k];
+    // every table starts with the grid count and the block offsets cta0; the product
+    // tables follow them with the tile counts gx, gy
+    int n = 0;
+    std::vector<int> cta0(kBatchMax + 1, 0);
+    std::vector<short> gx(kBatchMax, 0), gy(kBatchMax, 0);
+    std::memcpy(&n, r.table.data(), sizeof(int));
+    std::memcpy(cta0.data(), r.table.data() + sizeof(int), sizeof(int) * (kBatchMax + 1));
+    const bool prod = r.kind <= PH_RR;
+    if (prod) {
+      static_assert(offsetof(March2Batch, gx) == offsetof(MarchRrBatch, gx) &&
+                        offsetof(March2Batch, gy) == offsetof(MarchRrBatch, gy),
+                    "product tables share their head");
+      std::memcpy(gx.data(), r.table.data() + offsetof(March2Batch, gx),
+                  sizeof(short) * kBatchMax);
+      std::memcpy(gy.data(), r.table.data() + offsetof(March2Batch, gy),
+                  sizeof(short) * kBatchMax);
+    }
+    for (int q = 0; q < n; ++q)
+      for (int b = cta0[q]; b < cta0[q + 1]; ++b)
+        units[k].push_back(UnitDesc{q, b - cta0[q], cta0[q + 1] - cta0[q], gx[q], gy[q]});
+    if ((int)units[k].size() != r.units) return TOMO_OK;  // not a table of this layout
+    int nunits = r.units;
+    if (r.kind == PH_COARSE) {
+      // a grid's 1024-thread coarsest solve as four 256-thread units, each a quarter of
+      // the block's warps (the persistent kernel's CTAs have 256 threads)
+      std::vector<UnitDesc> four;
+      for (const UnitDesc& d : units[k])
+        for (int part = 0; part < 4; ++part) four.push_back(UnitDesc{d.q, part, 4, 0, 0});
+      units[k].swap(four);
+      nunits = (int)units[k].size();
+    }
+    off = (off + 255) & ~(size_t)255;
+    const size_t uoff = off;
+    off += sizeof(UnitDesc) * units[k].size();
+    off = (off + 255) & ~(size_t)255;
+    ph.push_back(DevPhase{r.kind, nunits, r.join, 0, (long long)uoff, (long long)off});
+    off += r.table.size();
+    if (r.kind == PH_COARSE) {
+      FlatBatch<CoarseItem> t;
+      std::memcpy(&t, r.table.data(), sizeof t);
+      for (int q = 0; q < t.n; ++q) smem = std::max(smem, sizeof(float) * (size_t)t.a[q].n);
+    }
   }
-  const int n = (int)Gs.size();
-  if (B->d_scs_n < n) {
-    if (B->d_scs) cudaFree(B->d_scs);
-    B->d_scs = nullptr;
-    B->d_scs_n = 0;
-    BK(cudaMalloc(&B->d_scs, sizeof(CgScalars*) * (size_t)n));
-    B->d_scs_n = n;
+  if (ph.empty()) return TOMO_OK;
+  const int ctas = persist_ctas(Gs[0]->num_sms, smem);
+  if (ctas <= 0) return TOMO_OK;
+  std::vector<unsigned char> host(off);
+  for (size_t k = 0; k < rec.size(); ++k) {
+    std::memcpy(host.data() + ph[k].units_offset, units[k].data(),
+                sizeof(UnitDesc) * units[k].size());
+    std::memcpy(host.data() + ph[k].offset, rec[k].table.data(), rec[k].table.size());
   }
-  std::vector<CgScalars*> h(n);
-  for (int q = 0; q < n; ++q) h[q] = Gs[q]->sc;
-  BK(cudaMemcpyAsync(B->d_scs, h.data(), sizeof(CgScalars*) * (size_t)n, cudaMemcpyHostToDevice,
+  if (off > B->d_tab_cap) {
+    if (B->d_tab) cudaFree(B->d_tab);
+    B->d_tab = nullptr;
+    B->d_tab_cap = 0;
+    BK(cudaMalloc(&B->d_tab, off));
+    B->d_tab_cap = off;
+  }
+  if ((int)ph.size() > B->d_ph_cap) {
+    if (B->d_ph) cudaFree(B->d_ph);
+    B->d_ph = nullptr;
+    B->d_ph_cap = 0;
+    BK(cudaMalloc(&B->d_ph, sizeof(DevPhase) * ph.size()));
+    B->d_ph_cap = (int)ph.size();
+  }
+  if (!B->d_bar) BK(cudaMalloc(&B->d_bar, 4 * sizeof(unsigned)));
+  if ((int)ph.size() + 1 > B->d_acc_cap) {
+    if (B->d_acc) cudaFree(B->d_acc);
+    B->d_acc = nullptr;
+    B->d_acc_cap = 0;
+    BK(cudaMalloc(&B->d_acc, sizeof(unsigned long long) * (ph.size() + 1)));
+    B->d_acc_cap = (int)ph.size() + 1;
+  }
+  BK(cudaMemsetAsync(B->d_acc, 0, sizeof(unsigned long long) * (ph.size() + 1), B->bst));
+  B->persist_kinds.clear();
+  for (const DevPhase& d : ph) B->persist_kinds.push_back(d.kind);
+  // pageable sources: each call returns once its bytes are staged
+  BK(cudaMemcpyAsync(B->d_tab, host.data(), off, cudaMemcpyHostToDevice, B->bst));
+  BK(cudaMemcpyAsync(B->d_ph, ph.data(), sizeof(DevPhase) * ph.size(), cudaMemcpyHostToDevice,
                      B->bst));
-  if (!B->cap) BK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  B->persist_nph = (int)ph.size();
+  B->persist_ctas_n = ctas;
+  B->persist_smem = smem;
+  *ok = true;
+  return TOMO_OK;
+}
+
+// Capture the device-side CG loop (a conditional while node) whose body is one lockstep
+// iteration: the persistent kernel (persist) or the batched launches, then the loop test.
+tomo_status batch_capture_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs, bool persist,
+                               int64_t* launches, cudaGraphExec_t* out) {
+  const int n = (int)Gs.size();
   cudaGraph_t graph;
   BK(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle hc;
@@ -2453,12 +2638,26 @@ tomo_status batch_build_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs) {
   e = cudaStreamBeginCaptureToGraph(B->cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                     cudaStreamCaptureModeThreadLocal);
   tomo_status st = TOMO_OK;
-  int64_t launches = 0;
+  *launches = 0;
   if (e == cudaSuccess) {
-    st = batch_iteration(B, B->cap, Gs, &launches);
+    if (persist) {
+      const tomo_grid* G0 = Gs[0];
+      cudaError_t e1 = launch_persist(B->cap, B->d_ph, B->persist_nph, B->d_tab,
+                                      march2_const(G0), elem_const<double>(G0), B->d_bar,
+                                      B->wait_limit_ns, B->d_scs, n, B->persist_ctas_n,
+                                      B->persist_smem,
+                                      B->persist_timing ? B->d_acc : nullptr);
+      *launches += 1;
+      if (e1 != cudaSuccess) {
+        B->err = std::string("persistent iteration launch failed: ") + cudaGetErrorString(e1);
+        st = TOMO_ECUDA;
+      }
+    } else {
+      st = batch_iteration(B, B->cap, Gs, launches);
+    }
     if (st == TOMO_OK) {
       cudaError_t e2 = launch_loop_cond_batch(B->cap, hc, B->d_scs, n);
-      launches += 1;
+      *launches += 1;
       if (e2 != cudaSuccess) {
         B->err = std::string("loop control launch failed: ") + cudaGetErrorString(e2);
         st = TOMO_ECUDA;
@@ -2474,9 +2673,48 @@ tomo_status batch_build_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs) {
     if (st != TOMO_OK) return st;
     BK(e);
   }
-  e = cudaGraphInstantiate(&B->loop, graph, 0);
+  e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   BK(e);
+  return TOMO_OK;
+}
+
+tomo_status batch_build_loop(tomo_batch* B, const std::vector<tomo_grid*>& Gs) {
+  if (B->loop) {
+    cudaGraphExecDestroy(B->loop);
+    B->loop = nullptr;
+  }
+  B->persist_used = false;
+  const int n = (int)Gs.size();
+  if (B->d_scs_n < n) {
+    if (B->d_scs) cudaFree(B->d_scs);
+    B->d_scs = nullptr;
+    B->d_scs_n = 0;
+    BK(cudaMalloc(&B->d_scs, sizeof(CgScalars*) * (size_t)n));
+    B->d_scs_n = n;
+  }
+  std::vector<CgScalars*> h(n);
+  for (int q = 0; q < n; ++q) h[q] = Gs[q]->sc;
+  BK(cudaMemcpyAsync(B->d_scs, h.data(), sizeof(CgScalars*) * (size_t)n, cudaMemcpyHostToDevice,
+                     B->bst));
+  if (!B->cap) BK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  int64_t launches = 0;
+  if (B->persistent) {
+    bool ok = false;
+    TRY(batch_record_persist(B, Gs, &ok));
+    if (ok) {
+      const tomo_status s = batch_capture_loop(B, Gs, true, &launches, &B->loop);
+      if (s == TOMO_OK) {
+        B->persist_used = true;
+      } else if (s == TOMO_ECUDA) {  // not capturable here: the launched iteration
+        cudaGetLastError();
+        B->err.clear();
+      } else {
+        return s;
+      }
+    }
+  }
+  if (!B->persist_used) TRY(batch_capture_loop(B, Gs, false, &launches, &B->loop));
   B->plan = Gs;
   B->plan_gen.clear();
   for (auto* G : Gs) B->plan_gen.push_back(G->gen);
@@ -2565,6 +2803,7 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
   const auto h1 = std::chrono::steady_clock::now();
   BK(cudaEventRecord(B->tev[0], B->bst));
   // phase B: one CG loop for the grids that have a system to solve
+  NvtxRange range_b("tomo batch: lockstep CG loop");
   std::vector<tomo_grid*> act;
   for (int i = 0; i < n; ++i)
     if (st[i] == TOMO_OK && !trivial[i]) act.push_back(B->grids[i]);
@@ -2581,7 +2820,14 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
     for (size_t q = 0; !stale && q < act.size(); ++q) stale = B->plan_gen[q] != act[q]->gen;
     if (bs == TOMO_OK && stale) bs = batch_build_loop(B, act);
     if (bs == TOMO_OK) {
-      cudaError_t e = cudaGraphLaunch(B->loop, B->bst);
+      cudaError_t e = cudaSuccess;
+      if (B->persist_used)  // barrier words from zero (a timed-out call leaves them mid-count)
+        e = cudaMemsetAsync(B->d_bar, 0, 4 * sizeof(unsigned), B->bst);
+      if (e == cudaSuccess && B->persist_used && B->persist_timing)
+        e = cudaMemsetAsync(B->d_acc, 0, sizeof(unsigned long long) * (B->persist_nph + 1),
+                            B->bst);
+      const bool injected = e == cudaSuccess && fault_hit(FAULT_GRAPH);
+      if (e == cudaSuccess && !injected) e = cudaGraphLaunch(B->loop, B->bst);
       if (e == cudaSuccess) e = cudaEventRecord(B->tev[2], B->bst);
       for (size_t q = 0; q < act.size() && e == cudaSuccess; ++q)
         e = cudaMemcpyAsync(act[q]->h_sc, act[q]->sc, sizeof(CgScalars),
@@ -2590,6 +2836,9 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
       if (e == cudaSuccess) e = cudaStreamSynchronize(B->bst);
       if (e != cudaSuccess) {
         B->err = std::string("lockstep CG loop: ") + cudaGetErrorString(e);
+        bs = TOMO_ECUDA;
+      } else if (injected) {
+        B->err = "injected CG loop launch failure";
         bs = TOMO_ECUDA;
       }
       float t01 = 0.f, t12 = 0.f, t23 = 0.f;
@@ -2603,8 +2852,10 @@ tomo_status batch_lockstep(tomo_batch* B, const float* const* z, double* complia
       B->phase_ms[2] = t12;
       B->phase_ms[3] = t23;
     }
-    if (bs == TOMO_OK)
+    if (bs == TOMO_OK) {
       for (auto* G : act) G->launches += launches + (int64_t)G->h_sc->loops * B->iter_launches;
+      if (B->persist_used) B->persistent_runs += 1;
+    }
   }
   const auto h2 = std::chrono::steady_clock::now();
   if (bs == TOMO_OK) {
@@ -2702,6 +2953,49 @@ tomo_status tomo_batch_set_lockstep(tomo_batch* B, int32_t on) {
   return TOMO_OK;
 }
 
+tomo_status tomo_batch_set_persistent(tomo_batch* B, int32_t on) {
+  if (!B || on < 0 || on > 2) return TOMO_EINVAL;
+  if (B->persistent != (on != 0) || B->persist_timing != (on == 2))
+    B->plan.clear();  // recapture the loop
+  B->persistent = on != 0;
+  B->persist_timing = on == 2;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_set_wait_limit(tomo_batch* B, int64_t limit_ns) {
+  if (!B || limit_ns < 0) return TOMO_EINVAL;
+  if (B->wait_limit_ns != limit_ns) B->plan.clear();  // the limit is a launch argument
+  B->wait_limit_ns = limit_ns;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_persistent_info(const tomo_batch* B, int32_t* ctas, int32_t* phases,
+                                       int64_t* runs) {
+  if (!B) return TOMO_EINVAL;
+  if (ctas) *ctas = B->persist_used ? B->persist_ctas_n : 0;
+  if (phases) *phases = B->persist_used ? B->persist_nph : 0;
+  if (runs) *runs = B->persistent_runs;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_persistent_phase_ns(tomo_batch* B, int64_t* ns, int32_t* kinds,
+                                           int32_t cap, int32_t* count, int64_t* launches) {
+  if (!B || !count || cap < 0 || (cap > 0 && (!ns || !kinds))) return TOMO_EINVAL;
+  const int nph = (B->persist_used && B->persist_timing) ? B->persist_nph : 0;
+  *count = nph;
+  if (launches) *launches = 0;
+  if (nph == 0) return TOMO_OK;
+  std::vector<unsigned long long> t(nph + 1);
+  BK(cudaMemcpy(t.data(), B->d_acc, sizeof(unsigned long long) * (nph + 1),
+                cudaMemcpyDeviceToHost));
+  if (launches) *launches = (int64_t)t[nph];
+  for (int p = 0; p < std::min(nph, (int)cap); ++p) {
+    ns[p] = (int64_t)t[p];
+    kinds[p] = B->persist_kinds[p];
+  }
+  return TOMO_OK;
+}
+
 tomo_status tomo_batch_phase_times(const tomo_batch* B, double* ms) {
   if (!B || !ms) return TOMO_EINVAL;
   for (int k = 0; k < 5; ++k) ms[k] = B->phase_ms[k];
@@ -2769,6 +3063,10 @@ tomo_status tomo_batch_destroy(tomo_batch* B) {
   if (B->cap) cudaStreamDestroy(B->cap);
   if (B->loop) cudaGraphExecDestroy(B->loop);
   if (B->d_scs) cudaFree(B->d_scs);
+  if (B->d_tab) cudaFree(B->d_tab);
+  if (B->d_ph) cudaFree(B->d_ph);
+  if (B->d_bar) cudaFree(B->d_bar);
+  if (B->d_acc) cudaFree(B->d_acc);
   for (auto e : B->wev) cudaEventDestroy(e);
   if (B->bev) cudaEventDestroy(B->bev);
   for (auto e : B->tev)

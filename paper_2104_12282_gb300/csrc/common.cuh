@@ -115,6 +115,15 @@ inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Load of data that does not change while the kernel runs (NC: the read-only path), or, in
+// the persistent lockstep iteration, where earlier phases of the same kernel write it, a
+// load cached in L2 only (coherent across the SMs after the phase barrier).
+template <bool NC, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if constexpr (NC) return __ldg(p);
+  else return __ldcg(p);
+}
+
 // A thread's sum of FP32 terms kept as the unevaluated pair hi + lo (Knuth's TwoSum per
 // term): ~44 significant bits from FP32 arithmetic alone.  FP64 runs at 1/64 of the FP32
 // rate on this part, so accumulating every element in FP64 would bound the streaming

@@ -2,8 +2,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -11,6 +13,15 @@
 #include "common.cuh"
 
 namespace tomo {
+
+// Named host range around a step of the path, visible to NVTX-aware profilers (a no-op
+// unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct FilterTap {
   int di, dj, dk;
@@ -35,6 +46,9 @@ constexpr int kMaxDenseDofs = 648;
 // Upper bound of lambda_max(D^-1 K) over any grid: max over one element of
 // lambda_max(diag(K0)^-1 K0) (x^T K x <= lam_e x^T D x element by element).
 constexpr int kTY = 16;  // rows of node columns per CTA in the marching product
+// rows per CTA of the batched FP64 residual replacement (256 threads, the CTA size of the
+// other batched phases; the per-node result does not depend on the tiling)
+constexpr int kRrTY = 8;
 
 enum MarchMode { M_APPLY = 0, M_RESID = 1, M_CHEB = 2 };
 
@@ -216,6 +230,59 @@ cudaError_t launch_march2_batch(cudaStream_t st, int mode, const March2Args* a, 
                                 const March2Const& c, int num_sms);
 cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const March2Const& c,
                           int num_sms);
+
+// Persistent lockstep iteration (one cooperative kernel per CG iteration): the batched
+// launches of one iteration are recorded instead of launched (kind, unit count and the
+// launch's parameter table), then replayed as phases of one kernel, each phase's units
+// spread over the co-resident CTAs and the phases separated by grid barriers.
+enum PhaseKind : int {
+  PH_M2_APPLY = 0, PH_M2_APPLY_DOT, PH_M2_RESID, PH_M2_CHEB, PH_M2_CHEB_DOT, PH_RR,
+  PH_JACOBI, PH_RESTRICT, PH_PROLONG, PH_COARSE, PH_CGXR, PH_CGP, PH_COUNT
+};
+struct PhaseRec {
+  int kind;
+  int units;
+  int join;                          // 1: a further table of the same launch (no barrier)
+  std::vector<unsigned char> table;  // the launch's parameter table, bytes
+};
+// while non-null, the batched launch wrappers append their launch here instead of launching
+extern thread_local std::vector<PhaseRec>* g_phase_rec;
+template <class Table>
+inline void record_phase(int kind, int units, const Table& t, bool cont) {
+  PhaseRec r{kind, units, cont ? 1 : 0, std::vector<unsigned char>(sizeof(Table))};
+  std::memcpy(r.table.data(), &t, sizeof(Table));
+  g_phase_rec->push_back(std::move(r));
+}
+// Place of one unit (one CTA of the recorded launch) of a phase: grid q of the table, its
+// block vb of vnb, and for the products the grid's tile counts gx, gy.
+struct UnitDesc {
+  int q;
+  int vb;
+  int vnb;
+  short gx, gy;
+};
+struct DevPhase {
+  int kind;
+  int units;
+  int join;            // no grid barrier before this phase
+  int pad;
+  long long units_offset;  // of the phase's UnitDesc[units] in the table buffer
+  long long offset;  // of the phase's table in the table buffer (256-byte aligned)
+};
+// Co-resident CTAs of the persistent kernel on this device (occupancy x SMs), 0 if it
+// cannot be launched cooperatively.
+int persist_ctas(int num_sms, size_t smem);
+// One CG iteration of a lockstep batch as one cooperative launch of `ctas` CTAs: phases
+// [0, nph) with their tables in `tables`; barrier = two zeroed unsigned words (count,
+// generation); a CTA that waits longer than limit_ns at a barrier marks every grid of
+// scs[0..nscs) stopped with DEV_TIMEOUT and leaves.  acc (nph + 1 words, may be null):
+// acc[p] += the device ns of phase p as CTA 0 sees it, acc[nph] += 1 (adds a barrier after
+// the last phase).
+cudaError_t launch_persist(cudaStream_t st, const DevPhase* phases, int nph,
+                           const unsigned char* tables, const March2Const& k2,
+                           const ElemConst<double>& k1, unsigned* barrier, long long limit_ns,
+                           CgScalars* const* scs, int nscs, int ctas, size_t smem, unsigned long long* acc);
+
 
 // All kernels are launched on `st`.  Wrappers return 0 or a cudaError_t.
 template <typename T>

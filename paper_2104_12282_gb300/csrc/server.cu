@@ -29,6 +29,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/tomo.h"
 #include "admission.h"
@@ -145,6 +146,8 @@ struct tomo_server {
 
   // One request alone on stream st (its grid already made).
   tomo_status run_one(Request* r, tomo_grid* g, cudaStream_t st) {
+    nvtxRangePushA(r->iters > 0 ? "tomo server: optimisation request"
+                                : "tomo server: gradient request");
     tomo_status s;
     if (r->iters > 0) {
       s = optimise(g, st, *r);
@@ -156,6 +159,7 @@ struct tomo_server {
       }
     }
     if (s != TOMO_OK) note(r, tomo_last_error(g));
+    nvtxRangePop();
     return s;
   }
 

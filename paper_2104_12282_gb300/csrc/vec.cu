@@ -6,10 +6,15 @@
 
 #include "common.cuh"
 #include "host.h"
+#include "march2_body.cuh"
+#include "march_body.cuh"
 
 namespace tomo {
 
 constexpr int kRedBlocks = 304;  // reduction grid (2 x 152 SMs)
+// float4 groups a thread loads before using them (the x/r update moves five arrays per
+// group, the p update two)
+constexpr int kIlpXr = 2, kIlpP = 4;
 constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ bool skipped(const int* skip) { return skip != nullptr && *skip; }
@@ -425,19 +430,25 @@ cudaError_t launch_coarse_factor(cudaStream_t st, Geom g, const T* s, const uint
 // reads of the stored inverse, coalesced; every warp's row loads are independent, so a row
 // costs about one L2 round trip instead of one per few columns), then a fixed-order warp
 // sum; accumulated in T.
+// (w0, nw): the warp's place among the warps that share the rows (default: this block's
+// warps); a row's result does not depend on which warp computes it.
 template <typename T>
 __device__ __forceinline__ void coarse_apply_body(int n, const T* __restrict__ Ainv,
                                                   const T* __restrict__ dsc,
                                                   const T* __restrict__ r, T* __restrict__ z,
-                                                  const int* skip) {
+                                                  const int* skip, int w0 = -1, int nw = 0) {
   PDL_ENTER();
   if (skipped(skip)) return;
   extern __shared__ unsigned char smem_raw[];
   T* rs = reinterpret_cast<T*>(smem_raw);
   for (int q = threadIdx.x; q < n; q += blockDim.x) rs[q] = dsc[q] * r[q];
   __syncthreads();
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int row = threadIdx.x >> 5; row < n; row += nw) {
+  const int lane = threadIdx.x & 31;
+  if (w0 < 0) {
+    w0 = threadIdx.x >> 5;
+    nw = blockDim.x >> 5;
+  }
+  for (int row = w0; row < n; row += nw) {
     const T* a = Ainv + (size_t)row * n;
     T acc = T(0);
     for (int c = lane; c < n; c += 32) acc += __ldg(a + c) * rs[c];
@@ -501,49 +512,64 @@ __device__ __forceinline__ void cg_xr_body(int vb, int vnb, int n, T* __restrict
   const int tid = vb * blockDim.x + threadIdx.x, nt = vnb * blockDim.x;
   int i0 = 0;
   if constexpr (sizeof(T) == 4) {
-    // float4 body: 16-byte accesses keep enough bytes in flight to stream at HBM rate
+    // float4 body: 16-byte accesses, and up to kIlpXr of a thread's float4 groups loaded
+    // before any is used, keep enough bytes in flight to stream at HBM rate also with few
+    // resident warps; every group is then updated (and added to the dot) in index order
     const int n4 = n >> 2;
-    for (int v = tid; v < n4; v += nt) {
-      const float4 pv = reinterpret_cast<const float4*>(p)[v];
-      const float4 qv = reinterpret_cast<const float4*>(q)[v];
-      float4 rv = reinterpret_cast<const float4*>(r)[v];
-      float4 hv = reinterpret_cast<const float4*>(xhi)[v];
-      if constexpr (PAIRX) {
-        float4 lv = reinterpret_cast<const float4*>(xlo)[v];
-        pair_axpy(alpha, pv.x, hv.x, lv.x);
-        pair_axpy(alpha, pv.y, hv.y, lv.y);
-        pair_axpy(alpha, pv.z, hv.z, lv.z);
-        pair_axpy(alpha, pv.w, hv.w, lv.w);
-        reinterpret_cast<float4*>(xlo)[v] = lv;
-      } else {
-        hv.x += alpha * pv.x;
-        hv.y += alpha * pv.y;
-        hv.z += alpha * pv.z;
-        hv.w += alpha * pv.w;
+    for (int v0 = tid; v0 < n4; v0 += kIlpXr * nt) {
+      float4 pv[kIlpXr], qv[kIlpXr], rv[kIlpXr], hv[kIlpXr], lv[kIlpXr];
+#pragma unroll
+      for (int u = 0; u < kIlpXr; ++u) {
+        const int v = v0 + u * nt;
+        if (v < n4) {
+          pv[u] = reinterpret_cast<const float4*>(p)[v];
+          qv[u] = reinterpret_cast<const float4*>(q)[v];
+          rv[u] = reinterpret_cast<const float4*>(r)[v];
+          hv[u] = reinterpret_cast<const float4*>(xhi)[v];
+          if constexpr (PAIRX) lv[u] = reinterpret_cast<const float4*>(xlo)[v];
+        }
       }
-      reinterpret_cast<float4*>(xhi)[v] = hv;
-      rv.x = rv.x - alpha * qv.x;
-      rv.y = rv.y - alpha * qv.y;
-      rv.z = rv.z - alpha * qv.z;
-      rv.w = rv.w - alpha * qv.w;
-      reinterpret_cast<float4*>(r)[v] = rv;
-      if (x1) {
-        const int i = v << 2;
-        int m = i - (i / nn) * nn;   // node of DOF i; the next three follow (wrapping at nn)
-        float4 xv;
-        xv.x = c2 * rv.x * invd[m];
-        m = (m + 1 == nn) ? 0 : m + 1;
-        xv.y = c2 * rv.y * invd[m];
-        m = (m + 1 == nn) ? 0 : m + 1;
-        xv.z = c2 * rv.z * invd[m];
-        m = (m + 1 == nn) ? 0 : m + 1;
-        xv.w = c2 * rv.w * invd[m];
-        reinterpret_cast<float4*>(x1)[v] = xv;
+#pragma unroll
+      for (int u = 0; u < kIlpXr; ++u) {
+        const int v = v0 + u * nt;
+        if (v >= n4) break;
+        if constexpr (PAIRX) {
+          pair_axpy(alpha, pv[u].x, hv[u].x, lv[u].x);
+          pair_axpy(alpha, pv[u].y, hv[u].y, lv[u].y);
+          pair_axpy(alpha, pv[u].z, hv[u].z, lv[u].z);
+          pair_axpy(alpha, pv[u].w, hv[u].w, lv[u].w);
+          reinterpret_cast<float4*>(xlo)[v] = lv[u];
+        } else {
+          hv[u].x += alpha * pv[u].x;
+          hv[u].y += alpha * pv[u].y;
+          hv[u].z += alpha * pv[u].z;
+          hv[u].w += alpha * pv[u].w;
+        }
+        reinterpret_cast<float4*>(xhi)[v] = hv[u];
+        float4 rr = rv[u];
+        rr.x = rr.x - alpha * qv[u].x;
+        rr.y = rr.y - alpha * qv[u].y;
+        rr.z = rr.z - alpha * qv[u].z;
+        rr.w = rr.w - alpha * qv[u].w;
+        reinterpret_cast<float4*>(r)[v] = rr;
+        if (x1) {
+          const int i = v << 2;
+          int m = i - (i / nn) * nn;   // node of DOF i; the next three follow (wrapping at nn)
+          float4 xv;
+          xv.x = c2 * rr.x * invd[m];
+          m = (m + 1 == nn) ? 0 : m + 1;
+          xv.y = c2 * rr.y * invd[m];
+          m = (m + 1 == nn) ? 0 : m + 1;
+          xv.z = c2 * rr.z * invd[m];
+          m = (m + 1 == nn) ? 0 : m + 1;
+          xv.w = c2 * rr.w * invd[m];
+          reinterpret_cast<float4*>(x1)[v] = xv;
+        }
+        accf.add(__fmul_rn(rr.x, rr.x));
+        accf.add(__fmul_rn(rr.y, rr.y));
+        accf.add(__fmul_rn(rr.z, rr.z));
+        accf.add(__fmul_rn(rr.w, rr.w));
       }
-      accf.add(__fmul_rn(rv.x, rv.x));
-      accf.add(__fmul_rn(rv.y, rv.y));
-      accf.add(__fmul_rn(rv.z, rv.z));
-      accf.add(__fmul_rn(rv.w, rv.w));
     }
     i0 = n4 << 2;
   }
@@ -635,14 +661,24 @@ __device__ __forceinline__ void cg_p_body(int vb, int vnb, int n, T* __restrict_
   int i0 = 0;
   if constexpr (sizeof(T) == 4) {
     const int n4 = n >> 2;
-    for (int v = tid; v < n4; v += nt) {
-      const float4 zv = reinterpret_cast<const float4*>(z)[v];
-      float4 pv = reinterpret_cast<const float4*>(p)[v];
-      pv.x = zv.x + beta * pv.x;
-      pv.y = zv.y + beta * pv.y;
-      pv.z = zv.z + beta * pv.z;
-      pv.w = zv.w + beta * pv.w;
-      reinterpret_cast<float4*>(p)[v] = pv;
+    for (int v0 = tid; v0 < n4; v0 += kIlpP * nt) {
+      float4 zv[kIlpP], pv[kIlpP];
+#pragma unroll
+      for (int u = 0; u < kIlpP; ++u)
+        if (v0 + u * nt < n4) {
+          zv[u] = reinterpret_cast<const float4*>(z)[v0 + u * nt];
+          pv[u] = reinterpret_cast<const float4*>(p)[v0 + u * nt];
+        }
+#pragma unroll
+      for (int u = 0; u < kIlpP; ++u)
+        if (v0 + u * nt < n4) {
+          float4 w = pv[u];
+          w.x = zv[u].x + beta * w.x;
+          w.y = zv[u].y + beta * w.y;
+          w.z = zv[u].z + beta * w.z;
+          w.w = zv[u].w + beta * w.w;
+          reinterpret_cast<float4*>(p)[v0 + u * nt] = w;
+        }
     }
     i0 = n4 << 2;
   }
@@ -903,7 +939,7 @@ cudaError_t flat_batches(const Item* a, int n, Blocks blocks, Work work, Launch 
     }
     B.cta0[B.n] = ctas;
     if (ctas > 0) {
-      launch(B, ctas);
+      launch(B, ctas, q0 > 0);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -921,24 +957,27 @@ int clamp_blocks(int n, int cap) {
 cudaError_t launch_jacobi_batch(cudaStream_t st, const JacobiItem* a, int n) {
   return flat_batches(a, n, [](const JacobiItem& it) { return clamp_blocks(it.g.nn, 4096); },
                       [](const JacobiItem& it) { return it.g.nn; },
-                      [st](const FlatBatch<JacobiItem>& B, int ctas) {
-                        pdl_launch(k_jacobi_batch, ctas, 256, 0, st, B);
+                      [st](const FlatBatch<JacobiItem>& B, int ctas, bool cont) {
+                        if (g_phase_rec) record_phase(PH_JACOBI, ctas, B, cont);
+                        else pdl_launch(k_jacobi_batch, ctas, 256, 0, st, B);
                       });
 }
 
 cudaError_t launch_restrict_batch(cudaStream_t st, const RestrictItem* a, int n) {
   return flat_batches(a, n, [](const RestrictItem& it) { return clamp_blocks(it.gc.nn, 8192); },
                       [](const RestrictItem& it) { return it.gc.nn; },
-                      [st](const FlatBatch<RestrictItem>& B, int ctas) {
-                        pdl_launch(k_restrict_batch, ctas, 256, 0, st, B);
+                      [st](const FlatBatch<RestrictItem>& B, int ctas, bool cont) {
+                        if (g_phase_rec) record_phase(PH_RESTRICT, ctas, B, cont);
+                        else pdl_launch(k_restrict_batch, ctas, 256, 0, st, B);
                       });
 }
 
 cudaError_t launch_prolong_batch(cudaStream_t st, const ProlongItem* a, int n) {
   return flat_batches(a, n, [](const ProlongItem& it) { return clamp_blocks(it.gf.nn, 16384); },
                       [](const ProlongItem& it) { return it.gf.nn; },
-                      [st](const FlatBatch<ProlongItem>& B, int ctas) {
-                        pdl_launch(k_prolong_batch, ctas, 256, 0, st, B);
+                      [st](const FlatBatch<ProlongItem>& B, int ctas, bool cont) {
+                        if (g_phase_rec) record_phase(PH_PROLONG, ctas, B, cont);
+                        else pdl_launch(k_prolong_batch, ctas, 256, 0, st, B);
                       });
 }
 
@@ -948,24 +987,27 @@ cudaError_t launch_coarse_apply_batch(cudaStream_t st, const CoarseItem* a, int 
   const size_t smem = sizeof(float) * (size_t)nmax;
   return flat_batches(a, n, [](const CoarseItem&) { return 1; },
                       [](const CoarseItem&) { return 0; },
-                      [st, smem](const FlatBatch<CoarseItem>& B, int ctas) {
-                        pdl_launch(k_coarse_apply_batch, ctas, 1024, smem, st, B);
+                      [st, smem](const FlatBatch<CoarseItem>& B, int ctas, bool cont) {
+                        if (g_phase_rec) record_phase(PH_COARSE, ctas, B, cont);
+                        else pdl_launch(k_coarse_apply_batch, ctas, 1024, smem, st, B);
                       });
 }
 
 cudaError_t launch_cg_xr_batch(cudaStream_t st, const CgXrItem* a, int n) {
   return flat_batches(a, n, [](const CgXrItem& it) { return cg_xr_blocks(it.n); },
                       [](const CgXrItem& it) { return it.n; },
-                      [st](const FlatBatch<CgXrItem>& B, int ctas) {
-                        pdl_launch(k_cg_xr_batch, ctas, kRedThreads, 0, st, B);
+                      [st](const FlatBatch<CgXrItem>& B, int ctas, bool cont) {
+                        if (g_phase_rec) record_phase(PH_CGXR, ctas, B, cont);
+                        else pdl_launch(k_cg_xr_batch, ctas, kRedThreads, 0, st, B);
                       });
 }
 
 cudaError_t launch_cg_p_batch(cudaStream_t st, const CgPItem* a, int n) {
   return flat_batches(a, n, [](const CgPItem& it) { return clamp_blocks(it.n, 8 * 152); },
                       [](const CgPItem& it) { return it.n; },
-                      [st](const FlatBatch<CgPItem>& B, int ctas) {
-                        pdl_launch(k_cg_p_batch, ctas, 256, 0, st, B);
+                      [st](const FlatBatch<CgPItem>& B, int ctas, bool cont) {
+                        if (g_phase_rec) record_phase(PH_CGP, ctas, B, cont);
+                        else pdl_launch(k_cg_p_batch, ctas, 256, 0, st, B);
                       });
 }
 
@@ -1073,5 +1115,219 @@ template cudaError_t launch_convert<float, double>(cudaStream_t, int, const doub
                                                    const double*, float*, const CgScalars*);
 template cudaError_t launch_convert<double, double>(cudaStream_t, int, const double*,
                                                     const double*, double*, const CgScalars*);
+
+
+// ---------------------------------------------------------------------------------------
+// Persistent lockstep iteration: the recorded batched launches of one CG iteration run as
+// the phases of one cooperative kernel of 256-thread CTAs (every phase's CTA work is 256
+// threads: the product's 32 x 8, the FP64 residual replacement's 32 x 8, the flat kernels'
+// 256; the coarsest apply, launched with 1024 threads, strides over its rows with 256).
+// Unit u of a phase is CTA u of the launch it replaces, so every grid sees the same blocks
+// (and dot partials, in the same order) as in the launched loop: the results are bitwise
+// the launched loop's.  Data written by an earlier phase is read through L2 (ldcg) or by
+// plain loads after the barrier's fences, never through the read-only path.
+// ---------------------------------------------------------------------------------------
+thread_local std::vector<PhaseRec>* g_phase_rec = nullptr;
+
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier over all CTAs of the launch (count, generation words).  Returns false if
+// this CTA waited longer than limit_ns for the others.
+__device__ bool grid_barrier(unsigned* bar, long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();  // the CTA's writes happen before thread 0's fence (cumulative)
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g) {
+        if ((long long)(global_ns() - t0) > limit_ns) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();  // ... and thread 0's acquire happens before the CTA's later reads
+  return s_ok != 0;
+}
+
+// One unit of each phase kind (a CTA of the recorded launch).
+template <int MODE, bool DOT>
+__device__ __forceinline__ void m2_unit(const unsigned char* tab, const UnitDesc& ud,
+                                     const March2Const& K) {
+  const March2Batch& B = *reinterpret_cast<const March2Batch*>(tab);
+  const int loc = ud.vb, gx = ud.gx, gy = ud.gy;
+  march2_body<MODE, DOT, false>(B.a[ud.q], K, loc % gx, (loc / gx) % gy, loc / (gx * gy), gx,
+                                (unsigned)loc, (unsigned)ud.vnb, threadIdx.x & 31,
+                                threadIdx.x >> 5);
+}
+
+template <class Item>
+__device__ __forceinline__ const Item& flat_item(const unsigned char* tab, int q) {
+  return reinterpret_cast<const FlatBatch<Item>*>(tab)->a[q];
+}
+
+__device__ __forceinline__ void rr_unit(const unsigned char* tab, const UnitDesc& ud,
+                                     const ElemConst<double>& K1) {
+  const MarchRrBatch& B = *reinterpret_cast<const MarchRrBatch*>(tab);
+  const int loc = ud.vb, gx = ud.gx, gy = ud.gy;
+  march_body<double, M_RESID, true, false, kRrTY, false>(
+      B.a[ud.q], K1, loc % gx, (loc / gx) % gy, loc / (gx * gy), (unsigned)loc,
+      (unsigned)ud.vnb, threadIdx.x & 31, threadIdx.x >> 5);
+}
+
+__device__ __forceinline__ void jacobi_unit(const unsigned char* tab, const UnitDesc& ud) {
+  const JacobiItem& a = flat_item<JacobiItem>(tab, ud.q);
+  jacobi_body<float, false>(ud.vb, ud.vnb, a.g, a.s, a.mask, a.b, a.c2, a.k0diag, a.x1,
+                            nullptr, nullptr, nullptr, nullptr, a.skip, a.invd);
+}
+
+__device__ __forceinline__ void restrict_unit(const unsigned char* tab, const UnitDesc& ud) {
+  const RestrictItem& a = flat_item<RestrictItem>(tab, ud.q);
+  restrict_body<float>(ud.vb, ud.vnb, a.gf, a.gc, a.rf, a.rc, a.mask_c, a.skip, a.x1, a.sc,
+                       a.c2, a.k0diag);
+}
+
+__device__ __forceinline__ void prolong_unit(const unsigned char* tab, const UnitDesc& ud) {
+  const ProlongItem& a = flat_item<ProlongItem>(tab, ud.q);
+  prolong_body<float>(ud.vb, ud.vnb, a.gf, a.gc, a.xc, a.xf, a.mask_f, a.skip);
+}
+
+__device__ __forceinline__ void coarse_unit(const unsigned char* tab, const UnitDesc& ud) {
+  const CoarseItem& a = flat_item<CoarseItem>(tab, ud.q);
+  // the launched coarsest solve is one 1024-thread block per grid: unit vb of vnb takes
+  // its warps vb * 8 .. vb * 8 + 7 (of vnb * 8)
+  coarse_apply_body<float>(a.n, a.Ainv, a.dsc, a.r, a.z, a.skip,
+                           ud.vb * 8 + (int)(threadIdx.x >> 5), ud.vnb * 8);
+}
+
+__device__ __forceinline__ void cgxr_unit(const unsigned char* tab, const UnitDesc& ud) {
+  const CgXrItem& a = flat_item<CgXrItem>(tab, ud.q);
+  cg_xr_body<float, true>(ud.vb, ud.vnb, a.n, a.xhi, a.xlo, a.r, a.p, a.q, a.partials,
+                          a.counter, a.sc, a.x1, a.invd, a.c2);
+}
+
+__device__ __forceinline__ void cgp_unit(const unsigned char* tab, const UnitDesc& ud) {
+  const CgPItem& a = flat_item<CgPItem>(tab, ud.q);
+  cg_p_body<float>(ud.vb, ud.vnb, a.n, a.p, a.z, a.sc);
+}
+
+__global__ void __launch_bounds__(256, 2)
+    k_persist(const DevPhase* __restrict__ phases, int nph,
+              const unsigned char* __restrict__ tables, const __grid_constant__ March2Const K2,
+              const __grid_constant__ ElemConst<double> K1, unsigned* barrier,
+              long long limit_ns, CgScalars* const* scs, int nscs,
+              unsigned long long* acc) {
+  // acc (optional): acc[p] += device ns of phase p as CTA 0 sees it (start or previous
+  // barrier exit to this phase's barrier exit; a final barrier closes the last phase),
+  // acc[nph] += 1 per launch
+  unsigned long long t_last = 0;
+  if (acc != nullptr && blockIdx.x == 0 && threadIdx.x == 0) t_last = global_ns();
+  // The loop state lives in shared memory across a unit (one slot pair per thread, reread
+  // after the unit), so that no register is held across the bodies: the product body alone
+  // uses all but one of the 128 registers two CTAs per SM allow.
+  __shared__ int s_loop[2][256];
+  volatile int* const sp = &s_loop[0][threadIdx.x];
+  volatile int* const su = &s_loop[1][threadIdx.x];
+  for (int p = 0; p < nph; ++p) {
+    for (int u = blockIdx.x;; u += gridDim.x) {
+      const DevPhase ph = phases[p];
+      if (u >= ph.units) break;
+      const unsigned char* tab = tables + ph.offset;
+      // the unit's place, precomputed on the host: grid q, block vb of vnb, product tile
+      // counts gx, gy
+      const UnitDesc ud = reinterpret_cast<const UnitDesc*>(tables + ph.units_offset)[u];
+      *sp = p;
+      *su = u;
+      switch (ph.kind) {
+        case PH_M2_APPLY: m2_unit<M_APPLY, false>(tab, ud, K2); break;
+        case PH_M2_APPLY_DOT: m2_unit<M_APPLY, true>(tab, ud, K2); break;
+        case PH_M2_RESID: m2_unit<M_RESID, false>(tab, ud, K2); break;
+        case PH_M2_CHEB: m2_unit<M_CHEB, false>(tab, ud, K2); break;
+        case PH_M2_CHEB_DOT: m2_unit<M_CHEB, true>(tab, ud, K2); break;
+        case PH_RR: rr_unit(tab, ud, K1); break;
+        case PH_JACOBI: jacobi_unit(tab, ud); break;
+        case PH_RESTRICT: restrict_unit(tab, ud); break;
+        case PH_PROLONG: prolong_unit(tab, ud); break;
+        case PH_COARSE: coarse_unit(tab, ud); break;
+        case PH_CGXR: cgxr_unit(tab, ud); break;
+        case PH_CGP: cgp_unit(tab, ud); break;
+        default: break;
+      }
+      __syncthreads();  // the next unit reuses this CTA's shared memory
+      p = *sp;
+      u = *su;
+    }
+    if (p + 1 < nph && phases[p + 1].join) continue;
+    if (p + 1 == nph && acc == nullptr) break;  // the launch's end closes the last phase
+    if (!grid_barrier(barrier, limit_ns)) {
+      // a CTA did not arrive in time: every grid stops with the timeout status (the
+      // remaining CTAs time out at their own next barrier and leave too)
+      if (threadIdx.x == 0)
+        for (int q = 0; q < nscs; ++q) {
+          atomicOr(&scs[q]->status, DEV_TIMEOUT);
+          scs[q]->done = 1;
+        }
+      return;
+    }
+    if (acc != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned long long t = global_ns();
+      acc[p] += t - t_last;
+      t_last = t;
+      if (p + 1 == nph) acc[nph] += 1;
+    }
+  }
+}
+
+}  // namespace
+
+int persist_ctas(int num_sms, size_t smem) {
+  int per_sm = 0;
+  int dev = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, 256, smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * (num_sms > 0 ? num_sms : 152);
+}
+
+cudaError_t launch_persist(cudaStream_t st, const DevPhase* phases, int nph,
+                           const unsigned char* tables, const March2Const& k2,
+                           const ElemConst<double>& k1, unsigned* barrier, long long limit_ns,
+                           CgScalars* const* scs, int nscs, int ctas, size_t smem,
+                           unsigned long long* acc) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persist, phases, nph, tables, k2, k1, barrier, limit_ns,
+                            scs, nscs, acc);
+}
 
 }  // namespace tomo

@@ -116,6 +116,15 @@ def _load():
         "tomo_batch_set_lockstep": (st, [P, ctypes.c_int32]),
         "tomo_batch_lockstep_runs": (st, [P, ctypes.POINTER(ctypes.c_int64)]),
         "tomo_batch_phase_times": (st, [P, P]),
+        "tomo_inject_fault": (st, [ctypes.c_char_p, ctypes.c_int32]),
+        "tomo_batch_set_persistent": (st, [P, ctypes.c_int32]),
+        "tomo_batch_set_wait_limit": (st, [P, ctypes.c_int64]),
+        "tomo_batch_persistent_phase_ns": (st, [P, P, P, ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(ctypes.c_int64)]),
+        "tomo_batch_persistent_info": (st, [P, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int64)]),
         "tomo_batch_gradient": (st, [P, P, ctypes.POINTER(ctypes.c_double), P, P,
                                      ctypes.POINTER(SolveInfo)]),
         "tomo_batch_destroy": (st, [P]),
@@ -194,6 +203,8 @@ def exported_symbols():
             "tomo_server_last_error", "tomo_grid_device_bytes", "tomo_estimate_device_bytes",
             "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
             "tomo_batch_set_lockstep", "tomo_batch_lockstep_runs", "tomo_batch_phase_times",
+            "tomo_batch_set_persistent", "tomo_batch_set_wait_limit", "tomo_inject_fault",
+            "tomo_batch_persistent_info", "tomo_batch_persistent_phase_ns",
             "tomo_batch_gradient", "tomo_batch_destroy", "tomo_batch_last_error",
             "tomo_filter", "tomo_filter_d", "tomo_coarse_grain", "tomo_coarse_grain_d",
             "tomo_adjoint_gradient", "tomo_adjoint_gradient_d",
@@ -234,6 +245,14 @@ def _ptr(a, dtype, count, name):
             raise ValueError(f"{name}: expected {count} values, got {a.size}")
         return ctypes.c_void_p(a.ctypes.data)
     raise TypeError(f"{name}: expected a torch tensor or numpy array")
+
+
+def inject_fault(site, nth=1):
+    """Arm host-side fault injection (tomo_inject_fault): the nth pass through site
+    ("alloc", "sync" or "graph") fails once; nth = 0 disarms."""
+    st = lib().tomo_inject_fault(str(site).encode(), int(nth))
+    if st != 0:
+        raise TomoError(st, f"unknown fault site {site!r} or nth < 0")
 
 
 def _current_stream():
@@ -547,7 +566,7 @@ class Batch:
     loop for all grids, each phase one launch for every grid.  The batch does not own its
     grids."""
 
-    def __init__(self, workers=8, lockstep=True):
+    def __init__(self, workers=8, lockstep=True, persistent=False):
         h = ctypes.c_void_p()
         st = lib().tomo_batch_create(int(workers), ctypes.byref(h))
         if st != 0:
@@ -555,6 +574,53 @@ class Batch:
         self._h = h
         self.grids = []
         lib().tomo_batch_set_lockstep(self._h, int(bool(lockstep)))
+        lib().tomo_batch_set_persistent(self._h, int(bool(persistent)))
+
+    def set_persistent(self, on=True):
+        """Each lockstep CG iteration as one cooperative launch (tomo_batch_set_persistent);
+        on = 2 also times the phases (persistent_phase_times)."""
+        st = lib().tomo_batch_set_persistent(self._h, int(on))
+        if st != 0:
+            raise TomoError(st, "persistent mode must be 0, 1 or 2")
+
+    def set_wait_limit(self, ns):
+        """Barrier wait limit of the persistent iteration in ns (tomo_batch_set_wait_limit)."""
+        if int(ns) < 0:
+            raise ValueError("wait limit must be >= 0")
+        st = lib().tomo_batch_set_wait_limit(self._h, int(ns))
+        if st != 0:
+            raise TomoError(st, "wait limit rejected")
+
+    PHASE_KINDS = ("product", "product+pTq", "residual", "chebyshev", "chebyshev+bTx",
+                   "fp64 residual replacement", "jacobi start", "restriction",
+                   "prolongation", "coarsest solve", "cg x/r", "cg p")
+
+    def persistent_phase_times(self):
+        """([(kind, total microseconds)], launches) of the latest call's persistent
+        iterations (tomo_batch_persistent_phase_ns; needs set_persistent(2)); ([], 0)
+        without timing or when the loop in use is the launched one."""
+        cnt, nl = ctypes.c_int32(), ctypes.c_int64()
+        lib().tomo_batch_persistent_phase_ns(self._h, None, None, 0, ctypes.byref(cnt), None)
+        n = cnt.value
+        if n == 0:
+            return [], 0
+        ns = (ctypes.c_int64 * n)()
+        kinds = (ctypes.c_int32 * n)()
+        st = lib().tomo_batch_persistent_phase_ns(self._h, ctypes.cast(ns, ctypes.c_void_p),
+                                                  ctypes.cast(kinds, ctypes.c_void_p), n,
+                                                  ctypes.byref(cnt), ctypes.byref(nl))
+        if st != 0:
+            raise TomoError(st, lib().tomo_batch_last_error(self._h).decode())
+        return [(self.PHASE_KINDS[k], t / 1e3) for k, t in zip(kinds, ns)], nl.value
+
+    @property
+    def persistent_info(self):
+        """(ctas, phases, runs) of the persistent iteration (tomo_batch_persistent_info);
+        ctas = phases = 0 when the captured loop is the launched one."""
+        c, p, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        lib().tomo_batch_persistent_info(self._h, ctypes.byref(c), ctypes.byref(p),
+                                         ctypes.byref(r))
+        return c.value, p.value, r.value
 
     def phase_times(self):
         """Phases of the last lockstep call in ms (tomo_batch_phase_times): issue of the
