@@ -377,6 +377,7 @@ def extras(args, dev, stream):
         ms_t, (c_t, info_t) = timed(lambda: g.gradient(z, dc, dv), 3)
         g.set_smoother(2, 2)
         g.set_smoother_bound(0.0)
+        g.set_cycle(0)
         out["evolved_field"] = {
             "recipe": "50 OC iterations from the uniform start (volfrac 0.12), warm-started "
                       "solves; then cold-start gradients on that design",
@@ -384,7 +385,7 @@ def extras(args, dev, stream):
             "oc_loop_s_50_iters": loop_s, "warm_cg_iters_last": warm_its[-1],
             "warm_cg_iters_mean": statistics.mean(warm_its),
             "autotuned": {"fine_degree": best[0], "coarse_degree": best[1],
-                          "smoothing_bound": best[2],
+                          "smoothing_bound": best[2], "w_cycle_levels": best[3],
                           "cold_ms_per_grad": ms_t, "cold_cg_iters": info_t.iters}}
         # two-scale step of Algorithm 1 at N_B = 4 on the bumpy field
         nb = 4
@@ -525,6 +526,7 @@ def run_ours(args):
     # the same steps with the default smoother (degrees 2, 2 on the element bound)
     g.set_smoother(2, 2)
     g.set_smoother_bound(0.0)
+    g.set_cycle(0)
     for w in range(2):
         step(g, zs[w % 2], dc, dv, zn)
     ev_def = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -542,6 +544,7 @@ def run_ours(args):
     value_def = whole_job_rate(world, args.steps, slowest(sum(ms_def)))
     g.set_smoother(tuned[0], tuned[1])
     g.set_smoother_bound(tuned[2])
+    g.set_cycle(tuned[3])
 
     # ---------------- roofline of the smoother/product kernel ----------------
     g.profile_enable(True)
@@ -643,7 +646,8 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}", "cg_iters": iters[0],
                    "smoother": {"fine_degree": tuned[0], "coarse_degree": tuned[1],
-                                "bound": tuned[2], "bound_fallbacks": fallbacks,
+                                "bound": tuned[2], "w_cycle_levels": tuned[3],
+                                "bound_fallbacks": fallbacks,
                                 "chosen_by": "tomo_autotune_smoother on the seed-2 field of "
                                              "the same recipe, untimed"}},
         "default_smoother": {"value": value_def, "unit": UNIT,

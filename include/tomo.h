@@ -256,6 +256,17 @@ tomo_status tomo_get_smoother(const tomo_grid* grid, int32_t* fine_degree,
  * fallbacks.  Like tomo_set_smoother it waits for the grid's stream and sets the captured CG
  * loop aside.  tomo_get_smoother_bound: any pointer may be NULL. */
 tomo_status tomo_set_smoother_bound(tomo_grid* grid, double lam);
+/* Cycle shape of the multigrid preconditioner: bit l of w_levels set makes the cycle
+ * correct twice from level l + 1 at level l (x += P M P^T (b - A x) once more after the
+ * first correction, before the post-smoothing): a W-cycle at that level, which can save CG
+ * iterations where the rediscretised coarse operators are weak (designs evolved towards
+ * 0/1 densities) at the price of running the coarser levels twice.  0 (the default) is the V-cycle.  Bits of the two coarsest levels have no
+ * effect (the level above the coarsest corrects exactly).  The cycle stays symmetric, so it
+ * remains a valid CG preconditioner.  A grid with W-cycle levels runs alone in a batch (one
+ * grid per worker stream, not lockstep).  Like tomo_set_smoother it waits for the grid's
+ * stream and sets the captured loop aside.  tomo_get_cycle reads the mask. */
+tomo_status tomo_set_cycle(tomo_grid* grid, uint32_t w_levels);
+tomo_status tomo_get_cycle(const tomo_grid* grid, uint32_t* w_levels);
 tomo_status tomo_get_smoother_bound(const tomo_grid* grid, double* lam, double* element_bound,
                                     int64_t* fallbacks);
 
@@ -266,19 +277,23 @@ tomo_status tomo_get_smoother_bound(const tomo_grid* grid, double* lam, double* 
  * candidate's captured loop from an earlier use: a grid keeps the loops of up to 8 smoother
  * settings), then reps (1..16) solves timed with CUDA events on the grid's stream, the
  * median kept.  pairs == NULL: the built-in list (2,2) (2,3) (2,4) (1,3) (1,4) (1,6), each at
- * 1, 0.75 and 0.68 times the element bound (18 candidates; n ignored; results needs room for
- * 18).  Candidates are timed without the bound fallback of the solves (a candidate that
- * fails is only marked failed).  The fastest candidate that converges becomes the grid's
- * smoother; results[k] (may be NULL) holds each candidate's median milliseconds (-1 when it
- * failed), iterations, status and bound; *best (may be NULL) its index.  If no candidate
- * converges the grid keeps its previous smoother and ENOCONV is returned.  The grid's
- * displacement is left as the last trial's. */
+ * 1, 0.75 and 0.68 times the element bound, as V-cycles (18 candidates), then the fastest
+ * of these with a W-cycle at level 1 and at levels 1 and 2 (tomo_set_cycle masks 2 and 6):
+ * 20 candidates, n ignored, results needs room for 20.  A caller's list keeps the grid's
+ * bound and cycle.  Candidates are timed without the bound fallback of the solves (a
+ * candidate that fails is only marked failed).  The fastest candidate that converges
+ * becomes the grid's smoother and cycle; results[k] (may be NULL) holds each candidate's
+ * median milliseconds (-1 when it failed), iterations, status, bound and cycle mask; *best
+ * (may be NULL) its index.  If no candidate converges the grid keeps its previous setting
+ * and ENOCONV is returned.  The grid's displacement is left as the last trial's. */
 typedef struct {
   int32_t fine_degree, coarse_degree;
   int32_t iters;
   int32_t status;
   double ms;
-  double lam;  /* upper end of the smoothing interval the candidate used */
+  double lam;         /* upper end of the smoothing interval the candidate used */
+  uint32_t w_levels;  /* the candidate's cycle (tomo_set_cycle mask) */
+  uint32_t reserved;
 } tomo_tune_result;
 tomo_status tomo_autotune_smoother(tomo_grid* grid, const float* z, const int32_t* pairs,
                                    int32_t n, int32_t reps, tomo_tune_result* results,

@@ -560,6 +560,30 @@ tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int
     CK(launch_prolong_add<T>(G->stream, Lv.g, Lc.g, zc, X, Lv.mask, skip));
   }
   G->launches += 1;
+  if (((G->wlevels >> l) & 1u) && l + 2 < nl) {
+    // W-cycle at this level: a second coarse-grid correction from the corrected iterate
+    // (x += P M_c P^T (b - A x); symmetric, so the cycle stays an SPD preconditioner); the
+    // level above the coarsest is left out (its exact coarse solve leaves nothing to correct)
+    MarchArgs<T> a{};
+    a.x = X;
+    a.b = b;
+    a.y = (T*)Lv.t;
+    a.skip = skip;
+    TRY(march<T>(G, l, M_RESID, a));
+    {
+      LevelTimer lt(G, l);
+      CK(launch_restrict<T>(G->stream, Lv.g, Lc.g, (const T*)Lv.t, (T*)Lc.b, Lc.mask, skip,
+                            fuse ? (T*)Lc.x : nullptr, (const T*)Lc.s, (T)(1.0 / cb.theta),
+                            (T)G->k0diag));
+      G->launches += 1;
+    }
+    TRY(vcycle<T>(G, l + 1, (const T*)Lc.b, &zc, false, skip, fuse));
+    {
+      LevelTimer lt(G, l);
+      CK(launch_prolong_add<T>(G->stream, Lv.g, Lc.g, zc, X, Lv.mask, skip));
+    }
+    G->launches += 1;
+  }
   TRY(smooth<T>(G, l, b, &X, &Y, false, dot, skip));
   *out = X;
   return TOMO_OK;
@@ -807,7 +831,8 @@ tomo_status pcg_result(tomo_grid* G, tomo_solve_info* info) {
   return TOMO_OK;
 }
 
-tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, double lam);
+tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, double lam,
+                         int64_t wlevels = -1);
 
 template <typename T>
 tomo_status pcg_once(tomo_grid* G, bool warm, tomo_solve_info* info) {
@@ -1616,7 +1641,10 @@ tomo_status create_impl(tomo_grid* G) {
 
 // Chebyshev degrees (finest level, coarser levels) and interval ratio of a grid; the
 // captured CG loops, which bake them in, are dropped and rebuilt at the next solve.
-tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, double lam) {
+// wlevels < 0 keeps the grid's cycle shape
+tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, double lam,
+                         int64_t wlevels) {
+  const uint32_t w = wlevels < 0 ? G->wlevels : (uint32_t)wlevels;
   if (fine < 1 || fine > 16 || coarse < 1 || coarse > 16 || !(ratio > 1.0) || !std::isfinite(ratio))
     return fail(G, TOMO_EINVAL, "smoother: degrees in 1..16 and ratio > 1 (got %d, %d, %g)",
                 fine, coarse, ratio);
@@ -1627,7 +1655,7 @@ tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, doubl
     return fail(G, TOMO_EINVAL, "smoother bound %g outside [%g, %g] (a quarter of the element "
                 "bound up to the bound)", lam, 0.25 * G->lam_bound, G->lam_bound);
   if (fine == G->d.smoother_degree && coarse == G->d.coarse_degree && ratio == G->cheb_ratio &&
-      lam == G->lam_hi)
+      lam == G->lam_hi && w == G->wlevels)
     return TOMO_OK;
   TRY(sync(G));  // no captured loop of this grid is still running
   // keep the current load-slot loop for a later return to these settings (up to 8)
@@ -1637,7 +1665,8 @@ tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, doubl
       G->loop_cache.erase(G->loop_cache.begin());
     }
     G->loop_cache.push_back(tomo_grid::CachedLoop{G->d.smoother_degree, G->d.coarse_degree,
-                                                  G->cheb_ratio, G->lam_hi, G->loop_exec});
+                                                  G->cheb_ratio, G->lam_hi, G->wlevels,
+                                                  G->loop_exec});
   }
   G->loop_exec = nullptr;
   if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
@@ -1647,9 +1676,11 @@ tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, doubl
   G->d.cheb_ratio = ratio;
   G->cheb_ratio = ratio;
   G->lam_hi = lam;
+  G->wlevels = w;
   for (size_t k = 0; k < G->loop_cache.size(); ++k) {
     const tomo_grid::CachedLoop& e = G->loop_cache[k];
-    if (e.fine == fine && e.coarse == coarse && e.ratio == ratio && e.lam == lam) {
+    if (e.fine == fine && e.coarse == coarse && e.ratio == ratio && e.lam == lam &&
+        e.wlevels == w) {
       G->loop_exec = e.exec;
       G->loop_cache.erase(G->loop_cache.begin() + k);
       break;
@@ -1674,30 +1705,39 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
   static const int32_t kDefault[] = {2, 2, 2, 3, 2, 4, 1, 3, 1, 4, 1, 6};
   static const double kBoundScale[] = {1.0, 0.75, 0.68};
   if (!z) return fail(G, TOMO_EINVAL, "null array");
+  // after the V-cycle candidates of the built-in list, the best of them is tried with a
+  // W-cycle at level 1 and at levels 1 and 2 (bit masks 2 and 6)
+  static const uint32_t kWStage[] = {2u, 6u};
   struct Cand {
     int fine, coarse;
     double lam;
+    uint32_t w;
   };
   std::vector<Cand> cands;
+  int n_v = 0;  // candidates before the W stage (all of them with a caller's list)
   if (!pairs) {
     for (double f : kBoundScale)
       for (size_t k = 0; k + 1 < sizeof(kDefault) / sizeof(kDefault[0]); k += 2)
-        cands.push_back(Cand{kDefault[k], kDefault[k + 1], f * G->lam_bound});
+        cands.push_back(Cand{kDefault[k], kDefault[k + 1], f * G->lam_bound, 0u});
+    n_v = (int)cands.size();
+    n = n_v + (int)(sizeof(kWStage) / sizeof(kWStage[0]));
   } else {
     if (n < 1 || n > 64)
       return fail(G, TOMO_EINVAL, "autotune: 1..64 candidates and 1..16 repetitions");
-    for (int k = 0; k < n; ++k) cands.push_back(Cand{pairs[2 * k], pairs[2 * k + 1], G->lam_hi});
+    for (int k = 0; k < n; ++k)
+      cands.push_back(Cand{pairs[2 * k], pairs[2 * k + 1], G->lam_hi, G->wlevels});
+    n_v = n;
   }
-  n = (int)cands.size();
   if (reps < 1 || reps > 16)
     return fail(G, TOMO_EINVAL, "autotune: 1..64 candidates and 1..16 repetitions");
   if (G->d.precond != TOMO_PRECOND_MG)
     return fail(G, TOMO_EINVAL, "autotune: the grid has no multigrid smoother");
-  for (int k = 0; k < n; ++k)
+  for (int k = 0; k < n_v; ++k)
     if (cands[k].fine < 1 || cands[k].fine > 16 || cands[k].coarse < 1 || cands[k].coarse > 16)
       return fail(G, TOMO_EINVAL, "autotune: candidate %d has a degree outside 1..16", k);
   const int fine0 = G->d.smoother_degree, coarse0 = G->d.coarse_degree;
   const double ratio = G->cheb_ratio, lam0 = G->lam_hi;
+  const uint32_t w0 = G->wlevels;
   const size_t be = sizeof(T) * (size_t)G->g.nel;
   const void* dz;
   bool h1;
@@ -1718,7 +1758,12 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
   double bms = 0.0;
   tomo_status st = TOMO_OK;
   for (int k = 0; k < n && st == TOMO_OK; ++k) {
-    st = set_smoother(G, cands[k].fine, cands[k].coarse, ratio, cands[k].lam);
+    if (k == n_v) {  // the W stage, from the best V candidate
+      if (bi < 0) break;
+      const Cand b = cands[bi];
+      for (uint32_t w : kWStage) cands.push_back(Cand{b.fine, b.coarse, b.lam, w});
+    }
+    st = set_smoother(G, cands[k].fine, cands[k].coarse, ratio, cands[k].lam, cands[k].w);
     if (st != TOMO_OK) break;
     tomo_solve_info info{};
     // untimed solve, which captures this candidate's loop, unless the grid kept it; a
@@ -1757,6 +1802,7 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
       res[k].status = sk;
       res[k].ms = sk == TOMO_OK ? med : -1.0;
       res[k].lam = cands[k].lam;
+      res[k].w_levels = cands[k].w;
     }
   }
   cudaEventDestroy(e0);
@@ -1765,11 +1811,11 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
     st = fail(G, TOMO_ENOCONV, "autotune: no candidate converged");
   if (st != TOMO_OK) {
     std::string why = G->err;
-    set_smoother(G, fine0, coarse0, ratio, lam0);
+    set_smoother(G, fine0, coarse0, ratio, lam0, w0);
     G->err = why;
     return st;
   }
-  TRY(set_smoother(G, cands[bi].fine, cands[bi].coarse, ratio, cands[bi].lam));
+  TRY(set_smoother(G, cands[bi].fine, cands[bi].coarse, ratio, cands[bi].lam, cands[bi].w));
   if (best) *best = bi;
   return TOMO_OK;
 }
@@ -1947,6 +1993,22 @@ tomo_status tomo_autotune_smoother_d(tomo_grid* G, const double* z, const int32_
   g_cur_err = &G->err;
   TRY(check_prec(G, true));
   return do_autotune<double>(G, z, pairs, n, reps, results, best);
+}
+
+tomo_status tomo_set_cycle(tomo_grid* G, uint32_t w_levels) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  G->err.clear();
+  if (G->d.precond != TOMO_PRECOND_MG && w_levels != 0)
+    return fail(G, TOMO_EINVAL, "cycle: the grid has no multigrid preconditioner");
+  return set_smoother(G, G->d.smoother_degree, G->d.coarse_degree, G->cheb_ratio, G->lam_hi,
+                      (int64_t)w_levels);
+}
+
+tomo_status tomo_get_cycle(const tomo_grid* G, uint32_t* w_levels) {
+  if (!G || !w_levels) return TOMO_EINVAL;
+  *w_levels = G->wlevels;
+  return TOMO_OK;
 }
 
 tomo_status tomo_inject_fault(const char* site, int32_t nth) {
@@ -2249,8 +2311,8 @@ bool lockstep_compatible(const std::vector<tomo_grid*>& Gs) {
   const tomo_grid* A = Gs[0];
   for (const tomo_grid* G : Gs) {
     if (G->prec != TOMO_FP32 || G->d.precond != TOMO_PRECOND_MG || !G->use_graph || G->prof ||
-        G->phase_prof || G->rhs_id != 0 || G->L.size() < 2 || !G->fuse_j0)
-      return false;
+        G->phase_prof || G->rhs_id != 0 || G->L.size() < 2 || !G->fuse_j0 || G->wlevels != 0)
+      return false;  // (the lockstep V-cycle has no W-cycle levels)
     if (G->d.smoother_degree != A->d.smoother_degree ||
         G->d.coarse_degree != A->d.coarse_degree || G->d.rr_every != A->d.rr_every ||
         G->k0diag != A->k0diag || std::memcmp(G->blk, A->blk, sizeof G->blk) != 0 ||

@@ -472,8 +472,11 @@ struct tomo_grid {
   struct CachedLoop {
     int fine, coarse;
     double ratio, lam;
+    uint32_t wlevels;
     cudaGraphExec_t exec;
   };
+  // bit l: the V-cycle makes two coarse-grid corrections at level l (a W-cycle there)
+  uint32_t wlevels = 0;
   double lam_bound = 0.0;       // the element bound of lambda_max(D^-1 K), always safe
   int64_t bound_fallbacks = 0;  // solves redone at lam_bound after failing at a lower lam_hi
   std::vector<CachedLoop> loop_cache;

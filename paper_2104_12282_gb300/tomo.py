@@ -46,7 +46,8 @@ class GridDesc(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("fine_degree", ctypes.c_int32), ("coarse_degree", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("ms", ctypes.c_double),
-                ("lam", ctypes.c_double)]
+                ("lam", ctypes.c_double), ("w_levels", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -88,6 +89,8 @@ def _load():
                                    ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_double)]),
         "tomo_set_smoother_bound": (st, [G, ctypes.c_double]),
+        "tomo_set_cycle": (st, [G, ctypes.c_uint32]),
+        "tomo_get_cycle": (st, [G, ctypes.POINTER(ctypes.c_uint32)]),
         "tomo_get_smoother_bound": (st, [G, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64)]),
@@ -196,7 +199,8 @@ def exported_symbols():
             "tomo_set_warm_start", "tomo_set_smoother", "tomo_get_smoother",
             "tomo_set_smoother_bound", "tomo_get_smoother_bound",
             "tomo_server_submit_optimize",
-            "tomo_autotune_smoother", "tomo_autotune_smoother_d",
+            "tomo_autotune_smoother", "tomo_autotune_smoother_d", "tomo_set_cycle",
+            "tomo_get_cycle",
             "tomo_server_create", "tomo_server_submit",
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
             "tomo_server_set_batching",
@@ -398,13 +402,27 @@ class Grid:
                                       ctypes.byref(n))
         return lam.value, b.value, n.value
 
+    def set_cycle(self, w_levels):
+        """Multigrid cycle (tomo_set_cycle): bit l set = two coarse-grid corrections at
+        level l (a W-cycle there); 0 = V-cycle."""
+        st = lib().tomo_set_cycle(self._h, int(w_levels))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def cycle(self):
+        """The W-cycle level mask (tomo_get_cycle)."""
+        w = ctypes.c_uint32()
+        lib().tomo_get_cycle(self._h, ctypes.byref(w))
+        return w.value
+
     def autotune(self, z, candidates=None, reps=2):
         """Time the state solve on design z for each (fine, coarse) degree pair at the
-        current bound, or for the built-in list of pairs and bounds when None, and keep the
-        fastest (tomo_autotune_smoother); returns (best (fine, coarse, lam), list of dicts
-        with fine, coarse, lam, ms, iters, status per candidate)."""
+        current bound and cycle, or for the built-in list of pairs, bounds and cycles when
+        None, and keep the fastest (tomo_autotune_smoother); returns (best (fine, coarse,
+        lam, w_levels), list of dicts with fine, coarse, lam, w, ms, iters, status per
+        candidate)."""
         if candidates is None:
-            pairs, n = None, 18
+            pairs, n = None, 20
         else:
             flat = [int(v) for pq in candidates for v in pq]
             pairs = (ctypes.c_int32 * len(flat))(*flat)
@@ -416,10 +434,10 @@ class Grid:
             n, int(reps), ctypes.cast(res, ctypes.c_void_p), ctypes.byref(best))
         if st != 0:
             raise TomoError(st, lib().tomo_last_error(self._h).decode())
-        rows = [dict(fine=r.fine_degree, coarse=r.coarse_degree, lam=r.lam, ms=r.ms,
-                     iters=r.iters, status=r.status) for r in res]
+        rows = [dict(fine=r.fine_degree, coarse=r.coarse_degree, lam=r.lam, w=r.w_levels,
+                     ms=r.ms, iters=r.iters, status=r.status) for r in res]
         b = rows[best.value]
-        return (b["fine"], b["coarse"], b["lam"]), rows
+        return (b["fine"], b["coarse"], b["lam"], b["w"]), rows
 
     def filter(self, x, out, transpose=False):
         self._call("tomo_filter", self._e(x, "in"), self._e(out, "out"), int(bool(transpose)))

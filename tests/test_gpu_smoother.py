@@ -75,7 +75,7 @@ def test_autotune_keeps_the_fastest_converging_candidate():
         ok = [r for r in rows if r["status"] == 0]
         assert ok and all(r["ms"] > 0 for r in ok)
         fastest = min(ok, key=lambda r: r["ms"])
-        assert best == (fastest["fine"], fastest["coarse"], fastest["lam"])
+        assert best == (fastest["fine"], fastest["coarse"], fastest["lam"], 0)
         assert g.smoother()[:2] == best[:2] and g.smoother_bound()[0] == best[2]
         dc = torch.empty_like(zt)
         c, info = g.gradient(zt, dc)
@@ -88,9 +88,15 @@ def test_autotune_keeps_the_fastest_converging_candidate():
     with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
         best, rows = g.autotune(zt)
         lam_b = g.smoother_bound()[1]
-        assert len(rows) == 18 and best in [(r["fine"], r["coarse"], r["lam"]) for r in rows]
+        assert len(rows) == 20
+        assert best in [(r["fine"], r["coarse"], r["lam"], r["w"]) for r in rows]
         assert sorted({round(r["lam"] / lam_b, 6) for r in rows}) == [0.68, 0.75, 1.0]
-        assert g.smoother_bound()[0] == best[2]
+        assert [r["w"] for r in rows] == [0] * 18 + [2, 6]
+        v = [r for r in rows[:18] if r["status"] == 0]
+        vbest = min(v, key=lambda r: r["ms"])       # the W stage starts from the best V row
+        assert all((r["fine"], r["coarse"], r["lam"]) == (vbest["fine"], vbest["coarse"],
+                                                          vbest["lam"]) for r in rows[18:])
+        assert g.smoother_bound()[0] == best[2] and g.cycle() == best[3]
         dc = torch.empty_like(zt)
         c2, _ = g.gradient(zt, dc)
     assert abs(c2 / c0 - 1.0) <= 1e-5
