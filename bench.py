@@ -416,10 +416,18 @@ def extras(args, dev, stream):
         with tomo.Batch(workers=8) as b:
             for gg in grids:
                 b.append(gg)
-            # the lockstep loop with one launch per phase, then with one cooperative launch
-            # per CG iteration (tomo_batch_set_persistent)
+            # product tiles (rows per CTA, waves) chosen by the library's tile autotuner on
+            # other fields of the same recipe, untimed
+            zt = [torch.tensor(P.random_field(q.dims, args.seed + 100 + i, 0.05, 1.0),
+                               dtype=torch.float32, device=dev) for i, q in enumerate(ps)]
+            tiles, tile_rows = b.autotune_tiles(zt, dcs, reps=2)
+            del zt
+            # the lockstep loop with one launch per phase at the tuned tiles, then with one
+            # cooperative launch per CG iteration (tomo_batch_set_persistent), which runs
+            # 8-row tiles
             for persist in (False, True):
                 b.set_persistent(persist)
+                b.set_tiles(*(tiles if not persist else (8, tiles[1])))
                 b.gradient(zs, dcs)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -443,11 +451,15 @@ def extras(args, dev, stream):
             "grad_evals_per_s": 64 / batch_s, "sequential_grad_evals_per_s": 64 / seq_s,
             "workers": 8, "mode": mode, "elements": sum(q.n_el for q in ps),
             "cg_iters_mean": statistics.mean(i.iters for i in infos),
+            "tiles": {"rows": tiles[0], "waves": tiles[1],
+                      "chosen_by": "tomo_batch_autotune_tiles on other fields, untimed",
+                      "candidates_ms": {"%dx%d" % (r["rows"], r["waves"]): r["ms"]
+                                        for r in tile_rows}},
             "launched_iteration": {"grad_evals_per_s": 64 / loops[False][0],
                                    "cg_loop_ms": loops[False][1]},
             "persistent_iteration": {"grad_evals_per_s": 64 / loops[True][0],
                                      "cg_loop_ms": loops[True][1], "ctas": pctas,
-                                     "phases": pphases}}
+                                     "phases": pphases, "tiles": "8x%d" % tiles[1]}}
     finally:
         for gg in grids:
             gg.close()

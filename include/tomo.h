@@ -404,6 +404,30 @@ tomo_status tomo_batch_persistent_info(const tomo_batch* batch, int32_t* ctas, i
  * grids) reports 0, its time counted with the continuation.  Synchronises the device. */
 tomo_status tomo_batch_persistent_phase_ns(tomo_batch* batch, int64_t* ns, int32_t* kinds,
                                            int32_t cap, int32_t* count, int64_t* launches);
+/* Tiles of the lockstep loop's batched products: tile_rows thread rows per CTA (8: tiles of
+ * 30 x 14 nodes, as a grid alone; 4: 30 x 6 nodes, which fit small grids' y extent better at
+ * more halo per node) and the waves of resident CTAs (1..16) that the z-chunk length aims
+ * at; default 8 and 4.  Only the order of the fused dots' block partials depends on them
+ * (results agree to rounding).  The persistent iteration takes 8-row tiles (with 4 the
+ * launched iteration runs).  TOMO_EINVAL for other values; the next call recaptures the
+ * loop.  tomo_batch_autotune_tiles: on the designs z[i] (dcdz[i] receives the gradients) it
+ * runs tomo_batch_gradient for each of the 6 candidates (8, 4 rows x 2, 4, 8 waves): one
+ * untimed call, then reps (1..16) calls timed by the device time of the batched phase (the
+ * first V-cycle and the CG loop), the median kept; the fastest becomes the batch's setting.
+ * results[k] (may be NULL, room for 6): rows, waves, status and median ms (-1 if the call
+ * failed); *best (may be NULL) its index.  Needs a batch that runs in lockstep (else
+ * TOMO_EINVAL); if no candidate runs, the previous setting is kept and TOMO_ENOCONV is
+ * returned (TOMO_ECUDA, and the search stops, after a CUDA error). */
+typedef struct {
+  int32_t tile_rows, waves;
+  int32_t status, reserved;
+  double ms;
+} tomo_batch_tune_result;
+tomo_status tomo_batch_set_tiles(tomo_batch* batch, int32_t tile_rows, int32_t waves);
+tomo_status tomo_batch_get_tiles(const tomo_batch* batch, int32_t* tile_rows, int32_t* waves);
+tomo_status tomo_batch_autotune_tiles(tomo_batch* batch, const float* const* z,
+                                      float* const* dcdz, int32_t reps,
+                                      tomo_batch_tune_result* results, int32_t* best);
 tomo_status tomo_batch_gradient(tomo_batch* batch, const float* const* z, double* compliance,
                                 float* const* dcdz, float* const* dvdz, tomo_solve_info* info);
 tomo_status tomo_batch_destroy(tomo_batch* batch);

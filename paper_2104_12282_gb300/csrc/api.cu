@@ -2241,6 +2241,10 @@ struct tomo_batch {
   // loop, and of the scalar read-back (events on the batch stream)
   cudaEvent_t tev[4] = {};
   double phase_ms[5] = {};
+  // tiles of the batched products: thread rows per CTA (8 or 4) and the waves of resident
+  // CTAs the z-chunking aims at (tomo_batch_set_tiles / tomo_batch_autotune_tiles)
+  int tile_ty = 8;
+  int waves = 4;
   // persistent lockstep iteration: requested, and whether the captured loop uses it
   bool persistent = false;
   bool persist_used = false;
@@ -2324,21 +2328,24 @@ bool lockstep_compatible(const std::vector<tomo_grid*>& Gs) {
 }
 
 // z-chunk length (node planes per CTA) for the grids P of a batched product on `level`:
-// the shortest chunks whose CTAs across the batch fit in four waves of resident CTAs (2 per
-// SM).  A grid alone chunks for the GPU it fills by itself; in a batch the grids together
-// fill it.  One wave of whole columns leaves the tallest grid's column as the makespan,
-// very short chunks add halo layers and waves; measured on 64 uneven cantilevers, the CG
-// loop took 6.79 / 6.88 / 6.63 ms with one / two / four waves.
-constexpr int kLockstepWaves = 4;
-int lockstep_kz(const std::vector<tomo_grid*>& Gs, const std::vector<int>& P, int level) {
-  const int target = kLockstepWaves * 2 * (Gs[0]->num_sms > 0 ? Gs[0]->num_sms : 152);
+// the shortest chunks whose CTAs across the batch fit in `waves` waves of resident CTAs
+// (2 per SM at 8 thread rows, 4 at 4).  A grid alone chunks for the GPU it fills by itself;
+// in a batch the grids together fill it.  One wave of whole columns leaves the tallest
+// grid's column as the makespan, very short chunks add halo layers and waves; measured on
+// 64 uneven cantilevers at 8 rows, the CG loop took 6.79 / 6.88 / 6.63 ms with one / two /
+// four waves (the default; tomo_batch_autotune_tiles measures the choice per batch).
+int lockstep_kz(const std::vector<tomo_grid*>& Gs, const std::vector<int>& P, int level,
+                int ty, int waves) {
+  const int per_sm = ty == 4 ? 4 : 2;
+  const int target = waves * per_sm * (Gs[0]->num_sms > 0 ? Gs[0]->num_sms : 152);
   int kmax = 1;
   for (int q : P) kmax = std::max(kmax, Gs[q]->L[level].g.nzn);
   for (int kz = 1; kz < kmax; ++kz) {
     long long ctas = 0;
     for (int q : P) {
       const Geom& g = Gs[q]->L[level].g;
-      const long long tiles = (long long)((g.nxn + 29) / 30) * ((g.nyn + 13) / 14);
+      const long long tiles =
+          (long long)((g.nxn + 29) / 30) * ((g.nyn + 2 * ty - 3) / (2 * ty - 2));
       ctas += tiles * ((g.nzn + kz - 1) / kz);
     }
     if (ctas <= target) return kz;
@@ -2408,13 +2415,13 @@ tomo_status batch_vcycle(tomo_batch* B, cudaStream_t st, const std::vector<tomo_
   auto cheb_step = [&](int l, int s, const std::vector<std::vector<ChebCoef>>& cf,
                        bool zero_start, int dk) -> tomo_status {
     ma.clear();
-    const int kz = lockstep_kz(Gs, P, l);
+    const int kz = lockstep_kz(Gs, P, l, B->tile_ty, B->waves);
     for (int q : P) {
       ma.push_back(march2_args(Gs[q], l, X[q][l], rhs(q, l), Y[q][l], nullptr, cf[q][s].c1,
                                cf[q][s].c2, dk, (s == 1 && zero_start) ? 1 : 0));
       ma.back().kz = kz;
     }
-    BK(launch_march2_batch(st, M_CHEB, ma.data(), (int)ma.size(), kc, num_sms));
+    BK(launch_march2_batch(st, M_CHEB, ma.data(), (int)ma.size(), kc, num_sms, B->tile_ty));
     *launches += 1;
     for (int q : P) std::swap(X[q][l], Y[q][l]);
     return TOMO_OK;
@@ -2446,13 +2453,13 @@ tomo_status batch_vcycle(tomo_batch* B, cudaStream_t st, const std::vector<tomo_
       TRY(cheb_step(l, s, cf, true, 0));
     }
     ma.clear();
-    const int kz = lockstep_kz(Gs, P, l);
+    const int kz = lockstep_kz(Gs, P, l, B->tile_ty, B->waves);
     for (int q : P) {
       ma.push_back(march2_args(Gs[q], l, X[q][l], rhs(q, l), nullptr,
                                (float*)Gs[q]->L[l].t, 0.0f, 0.0f, 0, 0));
       ma.back().kz = kz;
     }
-    BK(launch_march2_batch(st, M_RESID, ma.data(), (int)ma.size(), kc, num_sms));
+    BK(launch_march2_batch(st, M_RESID, ma.data(), (int)ma.size(), kc, num_sms, B->tile_ty));
     *launches += 1;
     std::vector<RestrictItem> ra;
     for (int q : P) {
@@ -2523,13 +2530,14 @@ tomo_status batch_iteration(tomo_batch* B, cudaStream_t st, const std::vector<to
   std::vector<March2Args> ma;
   std::vector<int> all(n);
   for (int q = 0; q < n; ++q) all[q] = q;
-  const int kz = lockstep_kz(Gs, all, 0);
+  const int kz = lockstep_kz(Gs, all, 0, B->tile_ty, B->waves);
   for (auto* G : Gs) {
     ma.push_back(march2_args(G, 0, (const float*)G->p, nullptr, nullptr, (float*)G->q, 0.0f,
                              0.0f, 1, 0));
     ma.back().kz = kz;
   }
-  BK(launch_march2_batch(st, M_APPLY, ma.data(), n, march2_const(G0), G0->num_sms));
+  BK(launch_march2_batch(st, M_APPLY, ma.data(), n, march2_const(G0), G0->num_sms,
+                         B->tile_ty));
   *launches += 1;
   // every lockstep grid is an FP32 multigrid grid, so all have the fused first step
   std::vector<CgXrItem> xa;
@@ -2576,6 +2584,7 @@ tomo_status batch_iteration(tomo_batch* B, cudaStream_t st, const std::vector<to
 // kernel's CTAs co-resident (the caller keeps the launched iteration).
 tomo_status batch_record_persist(tomo_batch* B, const std::vector<tomo_grid*>& Gs, bool* ok) {
   *ok = false;
+  if (B->tile_ty != 8) return TOMO_OK;  // the persistent units are 8-row product tiles
   std::vector<PhaseRec> rec;
   int64_t unused = 0;
   g_phase_rec = &rec;
@@ -3104,6 +3113,89 @@ tomo_status tomo_batch_gradient(tomo_batch* B, const float* const* z, double* co
     }
   });
   return batch_first_error(B, st);
+}
+
+tomo_status tomo_batch_set_tiles(tomo_batch* B, int32_t tile_rows, int32_t waves) {
+  if (!B || (tile_rows != 8 && tile_rows != 4) || waves < 1 || waves > 16) return TOMO_EINVAL;
+  if (tile_rows != B->tile_ty || waves != B->waves) B->plan.clear();  // recapture the loop
+  B->tile_ty = tile_rows;
+  B->waves = waves;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_get_tiles(const tomo_batch* B, int32_t* tile_rows, int32_t* waves) {
+  if (!B) return TOMO_EINVAL;
+  if (tile_rows) *tile_rows = B->tile_ty;
+  if (waves) *waves = B->waves;
+  return TOMO_OK;
+}
+
+tomo_status tomo_batch_autotune_tiles(tomo_batch* B, const float* const* z, float* const* dcdz,
+                                      int32_t reps, tomo_batch_tune_result* res,
+                                      int32_t* best) {
+  if (!B || !z || !dcdz || reps < 1 || reps > 16) return TOMO_EINVAL;
+  B->err.clear();
+  const int n = (int)B->grids.size();
+  for (int i = 0; i < n; ++i)
+    if (B->grids[i]->prec != TOMO_FP32 || !z[i] || !dcdz[i]) {
+      B->err = "tile autotune: FP32 grids and one z and dcdz array per grid";
+      return TOMO_EINVAL;
+    }
+  if (!B->lockstep || !lockstep_compatible(B->grids)) {
+    B->err = "tile autotune: the batch does not run in lockstep";
+    return TOMO_EINVAL;
+  }
+  // candidates: thread rows per CTA x waves of resident CTAs; each timed by the device time
+  // of the batched phase (first V-cycle and CG loop, CUDA events on the batch stream) after
+  // one untimed call that captures its loop; the median of reps calls
+  static const int kRows[] = {8, 4};
+  static const int kWaves[] = {2, 4, 8};
+  const int ty0 = B->tile_ty, w0 = B->waves;
+  std::vector<double> c(n);
+  int bi = -1, k = 0;
+  double bms = 0.0;
+  tomo_status st = TOMO_OK;
+  for (int ty : kRows)
+    for (int w : kWaves) {
+      if (st == TOMO_ECUDA) break;
+      tomo_batch_set_tiles(B, ty, w);
+      tomo_status sk = batch_lockstep(B, z, c.data(), dcdz, nullptr, nullptr);
+      std::vector<double> ms;
+      for (int r = 0; r < reps && sk == TOMO_OK; ++r) {
+        sk = batch_lockstep(B, z, c.data(), dcdz, nullptr, nullptr);
+        ms.push_back(B->phase_ms[1] + B->phase_ms[2]);
+      }
+      double med = -1.0;
+      if (sk == TOMO_OK) {
+        std::sort(ms.begin(), ms.end());
+        med = ms[ms.size() / 2];
+        if (bi < 0 || med < bms) {
+          bi = k;
+          bms = med;
+        }
+      } else if (sk == TOMO_ECUDA) {
+        st = sk;
+      }
+      if (res) {
+        res[k].tile_rows = ty;
+        res[k].waves = w;
+        res[k].status = sk;
+        res[k].reserved = 0;
+        res[k].ms = med;
+      }
+      ++k;
+    }
+  if (st == TOMO_OK && bi < 0) {
+    st = TOMO_ENOCONV;
+    B->err = "tile autotune: no candidate ran";
+  }
+  if (st != TOMO_OK) {
+    tomo_batch_set_tiles(B, ty0, w0);
+    return st;
+  }
+  tomo_batch_set_tiles(B, kRows[bi / 3], kWaves[bi % 3]);
+  if (best) *best = bi;
+  return TOMO_OK;
 }
 
 tomo_status tomo_batch_size(const tomo_batch* B, int32_t* count) {

@@ -225,9 +225,10 @@ struct March2Batch {
 // The same k_march2 operation on n grids (all with the same mode and dot flag) in
 // ceil(n / kBatchMax) launches; each grid gets the tiles of its own launch and z-chunks of
 // a[q].kz node planes (kz <= 0: the chunks of its own launch).  Only the fused dot depends
-// on the chunking (its per-block partials); the products themselves do not.
+// on the chunking (its per-block partials); the products themselves do not.  ty: thread
+// rows per CTA, 8 (the tiles of k_march2) or 4 (tiles of 6 element rows).
 cudaError_t launch_march2_batch(cudaStream_t st, int mode, const March2Args* a, int n,
-                                const March2Const& c, int num_sms);
+                                const March2Const& c, int num_sms, int ty = 8);
 cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const March2Const& c,
                           int num_sms);
 

@@ -1,6 +1,7 @@
-// The body of the FP32 product kernel (k_march2): one CTA of 32 x 8 threads, thread (l, t)
-// = lane l of thread row t.  Shared by the launched kernels (matvec2.cu) and the persistent
-// lockstep iteration (persist.cu), which runs the same CTA work as one unit of its phases.
+// The body of the FP32 product kernel (k_march2): one CTA of 32 x TY threads (TY = 8 thread
+// rows, or 4 for batches of small grids), thread (l, t) = lane l of thread row t.  Shared by
+// the launched kernels (matvec2.cu) and the persistent lockstep iteration (vec.cu), which
+// runs the same CTA work as one unit of its phases.
 #pragma once
 
 #include "common.cuh"
@@ -39,7 +40,7 @@ __device__ __forceinline__ float2 shup2(float2 v) {
 
 // One CTA of the product: tile (bx, by) of gx tiles along x, z-chunk bz; blin / nblk are the
 // CTA's linear index and the CTA count of this grid's launch (for the fused dot).
-template <int MODE, bool DOT, bool NC = true>
+template <int MODE, bool DOT, bool NC = true, int TY = TYP>
 __device__ __forceinline__ void march2_body(const March2Args& A, const March2Const& K, int bx,
                                             int by, int bz, int gx, unsigned blin,
                                             unsigned nblk, int l, int t) {
@@ -50,7 +51,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
   const int stop = A.skip != nullptr ? *A.skip : 0;
   const Geom g = A.g;
   const int i = bx * 30 - 1 + l;
-  const int j0 = by * (2 * TYP - 2) - 1 + 2 * t;
+  const int j0 = by * (2 * TY - 2) - 1 + 2 * t;
   const int j1 = j0 + 1;
   const int kb = bz * A.kz;
   const int ke = min(kb + A.kz, g.nzn);
@@ -60,15 +61,15 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
   const bool c1 = col_i && j1 >= 0 && j1 < g.nyn;
   const bool el_i = i >= 0 && i < g.nx && l < 31;
   const bool e0 = el_i && j0 >= 0 && j0 < g.ny;
-  const bool e1 = el_i && j1 >= 0 && j1 < g.ny && t < TYP - 1;
+  const bool e1 = el_i && j1 >= 0 && j1 < g.ny && t < TY - 1;
   const bool lane_out = l >= 1 && l <= 30;
   const bool o0 = lane_out && c0 && t >= 1;
-  const bool o1 = lane_out && c1 && t <= TYP - 2;
+  const bool o1 = lane_out && c1 && t <= TY - 2;
   const int nb0 = c0 ? i + g.nxn * j0 : 0, nb1 = c1 ? i + g.nxn * j1 : 0;
   const int eb0 = e0 ? i + g.nx * j0 : 0, eb1 = e1 ? i + g.nx * j1 : 0;
 
-  __shared__ float sN[3][TYP][32];  // node row j0 of each thread row, plane k+1
-  __shared__ float sV[6][TYP][32];  // sy = 1 half of the upper element, for the next row
+  __shared__ float sN[3][TY][32];  // node row j0 of each thread row, plane k+1
+  __shared__ float sV[6][TY][32];  // sy = 1 half of the upper element, for the next row
 
   auto load_plane = [&](int k, float2 (&v)[3]) {
     const bool in = k >= 0 && k < g.nzn;
@@ -99,7 +100,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
   __syncthreads();
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    N0[c] = (t + 1 < TYP) ? sN[c][t + 1][l] : 0.0f;
+    N0[c] = (t + 1 < TY) ? sN[c][t + 1][l] : 0.0f;
     C0[c] = shdn2(A0[c]);
     DN0[c] = __shfl_down_sync(FULL, N0[c], 1);
   }
@@ -160,7 +161,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
     float2 C1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      N1[c] = (t + 1 < TYP) ? sN[c][t + 1][l] : 0.0f;
+      N1[c] = (t + 1 < TY) ? sN[c][t + 1][l] : 0.0f;
       C1[c] = shdn2(A1[c]);
       DN1[c] = __shfl_down_sync(FULL, N1[c], 1);
     }

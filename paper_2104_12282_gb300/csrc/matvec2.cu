@@ -38,15 +38,34 @@ __global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
 // cta0[q] <= b < cta0[q+1] and is that grid's block b - cta0[q] in the order of k_march2's
 // (x, y, z) grid, so each grid sees exactly the blocks (and the dot partials) of its own
 // launch.
-template <int MODE, bool DOT>
-__global__ void __launch_bounds__(32 * TYP, TOMO_MARCH2_MIN_BLOCKS)
+// TY thread rows per CTA: 8 as k_march2, or 4 (tiles of 6 element rows, for batches of
+// small grids whose y extent the 14-row tile covers poorly; chosen by measurement).
+template <int MODE, bool DOT, int TY>
+__global__ void __launch_bounds__(32 * TY, TOMO_MARCH2_MIN_BLOCKS * TYP / TY)
     k_march2_batch(const __grid_constant__ March2Batch B, const __grid_constant__ March2Const K) {
   const int q = batch_owner(B.cta0, B.n, (int)blockIdx.x);
   const int loc = (int)blockIdx.x - B.cta0[q];
   const int gx = B.gx[q], gy = B.gy[q];
-  march2_body<MODE, DOT>(B.a[q], K, loc % gx, (loc / gx) % gy, loc / (gx * gy), gx,
-                         (unsigned)loc, (unsigned)(B.cta0[q + 1] - B.cta0[q]), threadIdx.x,
-                         threadIdx.y);
+  march2_body<MODE, DOT, true, TY>(B.a[q], K, loc % gx, (loc / gx) % gy, loc / (gx * gy), gx,
+                                   (unsigned)loc, (unsigned)(B.cta0[q + 1] - B.cta0[q]),
+                                   threadIdx.x, threadIdx.y);
+}
+
+template <int TY>
+cudaError_t launch_march2_batch_ty(cudaStream_t st, int mode, bool dot, int ctas,
+                                   const March2Batch& B, const March2Const& c) {
+  dim3 grid(ctas), block(32, TY);
+  if (mode == M_APPLY) {
+    if (dot) pdl_launch(k_march2_batch<M_APPLY, true, TY>, grid, block, 0, st, B, c);
+    else pdl_launch(k_march2_batch<M_APPLY, false, TY>, grid, block, 0, st, B, c);
+  } else if (mode == M_RESID) {
+    if (dot) return cudaErrorInvalidValue;
+    pdl_launch(k_march2_batch<M_RESID, false, TY>, grid, block, 0, st, B, c);
+  } else {
+    if (dot) pdl_launch(k_march2_batch<M_CHEB, true, TY>, grid, block, 0, st, B, c);
+    else pdl_launch(k_march2_batch<M_CHEB, false, TY>, grid, block, 0, st, B, c);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -111,8 +130,9 @@ March2Shape march2_shape(int mode, bool dot, const Geom& g, int num_sms) {
 }  // namespace
 
 cudaError_t launch_march2_batch(cudaStream_t st, int mode, const March2Args* a, int n,
-                                const March2Const& c, int num_sms) {
+                                const March2Const& c, int num_sms, int ty) {
   if (n <= 0) return cudaSuccess;
+  if (ty != TYP && ty != 4) return cudaErrorInvalidValue;
   const bool dot = a[0].dot_kind != 0;
   for (int q = 0; q < n; ++q)
     if ((a[q].dot_kind != 0) != dot) return cudaErrorInvalidValue;
@@ -128,32 +148,26 @@ cudaError_t launch_march2_batch(cudaStream_t st, int mode, const March2Args* a, 
       }
       B.a[q] = a[q0 + q];
       B.a[q].kz = m.kz;
+      if (ty != TYP) {
+        m.gy = (a[q0 + q].g.nyn + 2 * ty - 3) / (2 * ty - 2);
+        B.a[q].tile_fixed = nullptr;  // the flags are per TYP-row tile: test every mask
+      }
       B.gx[q] = m.gx;
       B.gy[q] = m.gy;
       B.cta0[q] = ctas;
       ctas += m.gx * m.gy * m.nzc;
     }
     B.cta0[B.n] = ctas;
-    if (g_phase_rec) {  // recorded for the persistent lockstep iteration
-      if (mode == M_RESID && dot) return cudaErrorInvalidValue;
+    if (g_phase_rec) {  // recorded for the persistent lockstep iteration (TYP rows)
+      if ((mode == M_RESID && dot) || ty != TYP) return cudaErrorInvalidValue;
       const int kind = mode == M_APPLY ? (dot ? PH_M2_APPLY_DOT : PH_M2_APPLY)
                        : mode == M_RESID ? PH_M2_RESID
                                          : (dot ? PH_M2_CHEB_DOT : PH_M2_CHEB);
       record_phase(kind, ctas, B, q0 > 0);
       continue;
     }
-    dim3 grid(ctas), block(32, TYP);
-    if (mode == M_APPLY) {
-      if (dot) pdl_launch(k_march2_batch<M_APPLY, true>, grid, block, 0, st, B, c);
-      else pdl_launch(k_march2_batch<M_APPLY, false>, grid, block, 0, st, B, c);
-    } else if (mode == M_RESID) {
-      if (dot) return cudaErrorInvalidValue;
-      pdl_launch(k_march2_batch<M_RESID, false>, grid, block, 0, st, B, c);
-    } else {
-      if (dot) pdl_launch(k_march2_batch<M_CHEB, true>, grid, block, 0, st, B, c);
-      else pdl_launch(k_march2_batch<M_CHEB, false>, grid, block, 0, st, B, c);
-    }
-    cudaError_t e = cudaGetLastError();
+    const cudaError_t e = ty == TYP ? launch_march2_batch_ty<TYP>(st, mode, dot, ctas, B, c)
+                                    : launch_march2_batch_ty<4>(st, mode, dot, ctas, B, c);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

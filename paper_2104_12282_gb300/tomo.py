@@ -62,6 +62,12 @@ class Result(ctypes.Structure):
                 ("message_len", ctypes.c_int32), ("message", ctypes.c_char * 256)]
 
 
+class BatchTuneResult(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("grids_created", ctypes.c_int64), ("evictions", ctypes.c_int64),
@@ -121,6 +127,11 @@ def _load():
         "tomo_batch_phase_times": (st, [P, P]),
         "tomo_inject_fault": (st, [ctypes.c_char_p, ctypes.c_int32]),
         "tomo_batch_set_persistent": (st, [P, ctypes.c_int32]),
+        "tomo_batch_set_tiles": (st, [P, ctypes.c_int32, ctypes.c_int32]),
+        "tomo_batch_get_tiles": (st, [P, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+        "tomo_batch_autotune_tiles": (st, [P, P, P, ctypes.c_int32, P,
+                                           ctypes.POINTER(ctypes.c_int32)]),
         "tomo_batch_set_wait_limit": (st, [P, ctypes.c_int64]),
         "tomo_batch_persistent_phase_ns": (st, [P, P, P, ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_int32),
@@ -209,6 +220,7 @@ def exported_symbols():
             "tomo_batch_set_lockstep", "tomo_batch_lockstep_runs", "tomo_batch_phase_times",
             "tomo_batch_set_persistent", "tomo_batch_set_wait_limit", "tomo_inject_fault",
             "tomo_batch_persistent_info", "tomo_batch_persistent_phase_ns",
+            "tomo_batch_set_tiles", "tomo_batch_get_tiles", "tomo_batch_autotune_tiles",
             "tomo_batch_gradient", "tomo_batch_destroy", "tomo_batch_last_error",
             "tomo_filter", "tomo_filter_d", "tomo_coarse_grain", "tomo_coarse_grain_d",
             "tomo_adjoint_gradient", "tomo_adjoint_gradient_d",
@@ -593,6 +605,39 @@ class Batch:
         self.grids = []
         lib().tomo_batch_set_lockstep(self._h, int(bool(lockstep)))
         lib().tomo_batch_set_persistent(self._h, int(bool(persistent)))
+
+    def set_tiles(self, tile_rows=8, waves=4):
+        """Tiles of the batched products (tomo_batch_set_tiles): thread rows per CTA (8 or
+        4) and waves of resident CTAs for the z-chunking."""
+        st = lib().tomo_batch_set_tiles(self._h, int(tile_rows), int(waves))
+        if st != 0:
+            raise TomoError(st, "tile rows must be 8 or 4 and waves 1..16")
+
+    def tiles(self):
+        r, w = ctypes.c_int32(), ctypes.c_int32()
+        lib().tomo_batch_get_tiles(self._h, ctypes.byref(r), ctypes.byref(w))
+        return r.value, w.value
+
+    def autotune_tiles(self, zs, dcdzs, reps=2):
+        """tomo_batch_autotune_tiles: returns (best (tile_rows, waves), list of dicts with
+        rows, waves, status, ms per candidate); the best becomes the batch's setting."""
+        n = len(self.grids)
+        if len(zs) != n or len(dcdzs) != n:
+            raise ValueError("one array per grid")
+        arr = ctypes.c_void_p * n
+        z = arr(*[g._e(a, "z") for g, a in zip(self.grids, zs)])
+        dc = arr(*[g._e(a, "dcdz") for g, a in zip(self.grids, dcdzs)])
+        res = (BatchTuneResult * 6)()
+        best = ctypes.c_int32(-1)
+        st = lib().tomo_batch_autotune_tiles(self._h, ctypes.cast(z, ctypes.c_void_p),
+                                             ctypes.cast(dc, ctypes.c_void_p), int(reps),
+                                             ctypes.cast(res, ctypes.c_void_p),
+                                             ctypes.byref(best))
+        if st != 0:
+            raise TomoError(st, lib().tomo_batch_last_error(self._h).decode())
+        rows = [dict(rows=r.tile_rows, waves=r.waves, status=r.status, ms=r.ms) for r in res]
+        b = rows[best.value]
+        return (b["rows"], b["waves"]), rows
 
     def set_persistent(self, on=True):
         """Each lockstep CG iteration as one cooperative launch (tomo_batch_set_persistent);
