@@ -517,7 +517,9 @@ const char* tomo_last_error(const tomo_grid* grid);
  * would: "alloc" (a device allocation of a grid: TOMO_ENOMEM), "sync" (a synchronisation
  * of a grid's stream, reported after the real one completed: TOMO_ECUDA), "graph" (the
  * launch of a captured CG loop, one grid's or a lockstep batch's: TOMO_ECUDA, nothing
- * launched).  nth = 0 disarms.  TOMO_FAULT="site:n[,site:n...]" in the environment arms
+ * launched), "nan_input" (a gradient's material gets one NaN modulus: the solve reports
+ * TOMO_ENAN), "slow_request" (a served request waits 200 ms on the host before it runs; the
+ * other workers go on).  nth = 0 disarms.  TOMO_FAULT="site:n[,site:n...]" in the environment arms
  * sites at the first check.  Process-wide; TOMO_EINVAL for an unknown site or nth < 0. */
 tomo_status tomo_inject_fault(const char* site, int32_t nth);
 

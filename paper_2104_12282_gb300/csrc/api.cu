@@ -101,11 +101,10 @@ void pool_init_once() {
 // ---------------------------------------------------------------------------------------
 // Host-side fault injection (error-path tests without a GPU fault): site k fails its n-th
 // pass after arming, once, with the status the real call's failure gives.  Armed by
-// tomo_inject_fault or, at the first check, by TOMO_FAULT="site:n[,site:n...]" (sites
-// alloc, sync, graph).
+// tomo_inject_fault or, at the first check, by TOMO_FAULT="site:n[,site:n...]".
 // ---------------------------------------------------------------------------------------
-enum FaultSite { FAULT_ALLOC = 0, FAULT_SYNC = 1, FAULT_GRAPH = 2, FAULT_SITES = 3 };
-const char* const kFaultNames[FAULT_SITES] = {"alloc", "sync", "graph"};
+const char* const kFaultNames[FAULT_SITES] = {"alloc", "sync", "graph", "nan_input",
+                                              "slow_request"};
 std::atomic<long long> g_fault_left[FAULT_SITES];  // passes until the failure, 0 = disarmed
 
 int fault_site(const char* name, size_t len) {
@@ -131,7 +130,9 @@ void fault_env_once() {
   });
 }
 
-bool fault_hit(FaultSite k) {
+}  // namespace
+
+bool tomo::fault_hit(FaultSite k) {
   fault_env_once();
   long long v = g_fault_left[k].load(std::memory_order_relaxed);
   while (v > 0) {
@@ -139,6 +140,8 @@ bool fault_hit(FaultSite k) {
   }
   return false;
 }
+
+namespace {
 
 tomo_status dalloc(tomo_grid* G, void** p, size_t bytes) {
   *p = nullptr;
@@ -1180,6 +1183,8 @@ tomo_status gradient_begin(tomo_grid* G, const T* z, T* dcdz, T* dvdz, GradIO* i
                       (const T*)G->Hs, rho, 0, 1, (T)d.E0, (T)d.Emin, (T)d.penal, (T)d.h,
                       (T*)G->L[0].s));
   G->launches += 1;
+  if (fault_hit(FAULT_NAN))  // injected: element 0's modulus becomes NaN (all bits set)
+    CK(cudaMemsetAsync(G->L[0].s, 0xFF, sizeof(T), G->stream));
   TRY(pmark(G, 1));
   // S2: coarse moduli, coarsest factorisation
   TRY(setup_levels<T>(G));

@@ -14,6 +14,18 @@
 
 namespace tomo {
 
+// Host-side fault injection sites (tomo_inject_fault / TOMO_FAULT); fault_hit(k) is true on
+// the armed pass of site k (once per arming).
+enum FaultSite {
+  FAULT_ALLOC = 0,    // a device allocation of a grid reports TOMO_ENOMEM
+  FAULT_SYNC = 1,     // a grid's stream synchronisation reports TOMO_ECUDA (after the real one)
+  FAULT_GRAPH = 2,    // a CG-loop graph launch is skipped and reports TOMO_ECUDA
+  FAULT_NAN = 3,      // a NaN modulus enters a gradient's material (the solve reports ENAN)
+  FAULT_SLOW = 4,     // a served request waits 200 ms on the host before it runs
+  FAULT_SITES = 5
+};
+bool fault_hit(FaultSite k);
+
 // Named host range around a step of the path, visible to NVTX-aware profilers (a no-op
 // unless a tool is attached).
 struct NvtxRange {

@@ -33,6 +33,7 @@
 
 #include "../../include/tomo.h"
 #include "admission.h"
+#include "host.h"
 
 namespace {
 
@@ -148,6 +149,8 @@ struct tomo_server {
   tomo_status run_one(Request* r, tomo_grid* g, cudaStream_t st) {
     nvtxRangePushA(r->iters > 0 ? "tomo server: optimisation request"
                                 : "tomo server: gradient request");
+    if (tomo::fault_hit(tomo::FAULT_SLOW))  // injected: a slow request (host wait)
+      std::this_thread::sleep_for(std::chrono::milliseconds(200));
     tomo_status s;
     if (r->iters > 0) {
       s = optimise(g, st, *r);

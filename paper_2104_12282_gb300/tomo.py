@@ -265,7 +265,8 @@ def _ptr(a, dtype, count, name):
 
 def inject_fault(site, nth=1):
     """Arm host-side fault injection (tomo_inject_fault): the nth pass through site
-    ("alloc", "sync" or "graph") fails once; nth = 0 disarms."""
+    ("alloc", "sync", "graph", "nan_input" or "slow_request") fails once; nth = 0
+    disarms."""
     st = lib().tomo_inject_fault(str(site).encode(), int(nth))
     if st != 0:
         raise TomoError(st, f"unknown fault site {site!r} or nth < 0")

@@ -2,7 +2,8 @@
 status and message, the handle stays usable and the next call gives the clean result.  No
 GPU fault is made: the host reports an error in place of the real call's result (a device
 allocation, a stream synchronisation after the real one, a CG-loop graph launch that is
-not made)."""
+not made), writes a NaN modulus into the material (a valid value the solve must report),
+or delays a served request on the host."""
 import os
 import subprocess
 import sys
@@ -20,7 +21,7 @@ torch = pytest.importorskip("torch")
 from paper_2104_12282_gb300 import tomo  # noqa: E402
 
 DEV = torch.device("cuda:0")
-ENOMEM, ECUDA = 2, 6
+ENOMEM, ENAN, ECUDA = 2, 4, 6
 
 
 def _field(p, seed):
@@ -67,6 +68,32 @@ def test_injected_sync_and_graph_failures_leave_the_grid_usable():
             again = _grad(g, z)
             assert again[0] == ref[0] and again[1] == ref[1]
             assert np.array_equal(again[2], ref[2])
+
+
+def test_injected_nan_modulus_is_reported_and_the_grid_recovers():
+    p = P.cantilever(16, 8, 8)
+    z = _field(p, 3)
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        ref = _grad(g, z)
+        tomo.inject_fault("nan_input", 1)
+        with pytest.raises(tomo.TomoError) as ei:
+            _grad(g, z)
+        assert ei.value.status == ENAN
+        again = _grad(g, z)
+    assert again[0] == ref[0] and again[1] == ref[1] and np.array_equal(again[2], ref[2])
+
+
+def test_a_slow_request_does_not_hold_up_the_others():
+    reqs = [P.served_request(9, i, (6, 10)) for i in range(4)]
+    with tomo.Server(workers=2, budget_bytes=1 << 30) as srv:
+        tomo.inject_fault("slow_request", 1)
+        tickets = [srv.submit(p) for p in reqs]
+        res = [srv.wait(t) for t in tickets]
+    assert all(r.status == 0 for r, _, _ in res)
+    slow = [r for r, _, _ in res if r.run_ms >= 200.0]
+    fast = [r for r, _, _ in res if r.run_ms < 200.0]
+    assert len(slow) == 1 and len(fast) == 3
+    assert max(r.queue_ms + r.run_ms for r in fast) < slow[0].queue_ms + slow[0].run_ms
 
 
 def test_injected_graph_failure_in_a_lockstep_batch():
