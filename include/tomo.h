@@ -523,6 +523,21 @@ const char* tomo_last_error(const tomo_grid* grid);
  * sites at the first check.  Process-wide; TOMO_EINVAL for an unknown site or nth < 0. */
 tomo_status tomo_inject_fault(const char* site, int32_t nth);
 
+/* Checked build (libtomo_checked.so, compiled with -DTOMO_CHECKED): the kernels' computed
+ * indices are tested against their buffers' extents; the first index outside is recorded
+ * (per source file) and replaced by 0, so that the access stays inside its buffer (no trap,
+ * no fault; the results of that call are then wrong).  tomo_check_report synchronises the
+ * device and returns *checked = 1 and in *word the first recorded violation (site in bits
+ * 48-63, the index's low 48 bits below; 0: none), then clears the records.  Sites: 1/2 the
+ * FP32 product's node/element loads, 3 its per-node operands (mask, b, D^-1, x_prev), 4 its
+ * stores, 5 the FP64 product's loads, 6 its per-node operands, 7 the Jacobi step's moduli,
+ * 8 the restriction's fine nodes and coarse moduli, 9 the prolongation's coarse nodes, 10
+ * the modulus coarsening, 11 the D^-1 kernel's moduli, 12 the coarsest solve's columns, 13
+ * the CG update's D^-1 gathers, 14 the filters' neighbours, 15 the sensitivity's element
+ * nodes, 17 the persistent iteration's unit table.  In the regular build *checked = 0 and
+ * *word = 0. */
+tomo_status tomo_check_report(int32_t* checked, uint64_t* word);
+
 #ifdef __cplusplus
 }
 #endif

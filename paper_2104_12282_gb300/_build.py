@@ -1,5 +1,6 @@
 """Build libtomo.so (sm_103a) in-tree with nvcc: one object per .cu file, compiled in
-parallel, linked into ``paper_2104_12282_gb300/_lib/libtomo.so``."""
+parallel, linked into ``paper_2104_12282_gb300/_lib/libtomo.so``; with checked=True also
+the bounds-checked variant ``libtomo_checked.so`` (-DTOMO_CHECKED)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -13,6 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "libtomo.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libtomo_checked.so")
 SOURCES = ["api.cu", "element.cu", "matvec.cu", "matvec2.cu", "vec.cu", "filt.cu",
            "twoscale.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -27,8 +29,8 @@ def nvcc() -> str:
     return exe
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OBJ_DIR, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, extra, obj_dir: str) -> str:
+    obj = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -36,18 +38,36 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(OBJ_DIR, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    if verbose:
-        print(LIB)
+def _variants(checked: bool):
+    """(library path, object directory, extra flags) of the regular build and, with
+    checked, of the bounds-checked build (-DTOMO_CHECKED, libtomo_checked.so)."""
+    out = [(LIB, OBJ_DIR, [])]
+    if checked:
+        out.append((LIB_CHECKED, os.path.join(OUT_DIR, "obj_checked"), ["-DTOMO_CHECKED"]))
+    return out
+
+
+def build(verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile every source (all variants' translation units in one parallel pool), then
+    link each variant; returns the regular library's path."""
+    variants = _variants(checked)
+    jobs = []
+    for _, obj_dir, flags in variants:
+        os.makedirs(obj_dir, exist_ok=True)
+        jobs += [(s, list(extra) + flags, obj_dir) for s in SOURCES]
+    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(lambda j: _compile(*j), jobs))
+    for v, (lib, _, _) in enumerate(variants):
+        part = objs[v * len(SOURCES):(v + 1) * len(SOURCES)]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *part, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        if verbose:
+            print(lib)
     return LIB
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    args = [a for a in sys.argv[1:] if a != "--checked"]
+    build(verbose=True, extra=args, checked="--checked" in sys.argv[1:])

@@ -2016,6 +2016,28 @@ tomo_status tomo_get_cycle(const tomo_grid* G, uint32_t* w_levels) {
   return TOMO_OK;
 }
 
+tomo_status tomo_check_report(int32_t* checked, uint64_t* word) {
+  if (!checked || !word) return TOMO_EINVAL;
+  *word = 0;
+#ifdef TOMO_CHECKED
+  *checked = 1;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return TOMO_ECUDA;
+  }
+  unsigned long long (*const words[])() = {check_word_matvec2, check_word_matvec,
+                                           check_word_vec, check_word_filt};
+  for (auto f : words) {
+    const unsigned long long w = f();
+    if (w == ~0ull) return TOMO_ECUDA;
+    if (*word == 0 && w != 0) *word = w;
+  }
+#else
+  *checked = 0;
+#endif
+  return TOMO_OK;
+}
+
 tomo_status tomo_inject_fault(const char* site, int32_t nth) {
   if (!site || nth < 0) return TOMO_EINVAL;
   const int k = fault_site(site, std::strlen(site));

@@ -115,6 +115,39 @@ inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Checked build (-DTOMO_CHECKED): a computed index passes through TOMO_CHK(i, n, site); one
+// outside [0, n) is recorded in this translation unit's check word (the first violation:
+// site in bits 48-63, the index's low 48 bits below) and replaced by 0, so the access stays
+// inside its buffer; no trap.  The host reads and clears the words (tomo_check_report).
+// Without TOMO_CHECKED the macro is the index itself.
+#ifdef TOMO_CHECKED
+namespace {
+__device__ unsigned long long g_check_word = 0ull;
+}
+__device__ __forceinline__ long long tomo_chk(long long i, long long n, int site) {
+  if (i < 0 || i >= n) {
+    atomicCAS(&g_check_word, 0ull,
+              ((unsigned long long)site << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull));
+    return 0;
+  }
+  return i;
+}
+#define TOMO_CHK(i, n, site) tomo_chk((long long)(i), (long long)(n), (site))
+// host accessor of this translation unit's word (read, then cleared)
+#define TOMO_CHECK_ACCESSOR(fn)                                                   \
+  unsigned long long fn() {                                                       \
+    unsigned long long v = 0ull, z = 0ull;                                        \
+    if (cudaMemcpyFromSymbol(&v, g_check_word, sizeof v) != cudaSuccess ||        \
+        cudaMemcpyToSymbol(g_check_word, &z, sizeof z) != cudaSuccess) {          \
+      cudaGetLastError();                                                         \
+      return ~0ull;                                                               \
+    }                                                                             \
+    return v;                                                                     \
+  }
+#else
+#define TOMO_CHK(i, n, site) (i)
+#endif
+
 // Load of data that does not change while the kernel runs (NC: the read-only path), or, in
 // the persistent lockstep iteration, where earlier phases of the same kernel write it, a
 // load cached in L2 only (coherent across the SMs after the phase barrier).

@@ -23,7 +23,7 @@ __global__ void k_filter(Geom g, const int4* __restrict__ taps, const T* __restr
       const int4 d = taps[t];
       const int ii = i + d.x, jj = j + d.y, kk = k + d.z;
       if (ii < 0 || ii >= g.nx || jj < 0 || jj >= g.ny || kk < 0 || kk >= g.nz) continue;
-      const int nb = ii + g.nx * (jj + g.ny * kk);
+      const int nb = TOMO_CHK(ii + g.nx * (jj + g.ny * kk), g.nel, 14);
       T v = ldg(in + nb);
       if (MODE == 1) v = v / ldg(Hs + nb);
       acc += tapw[t] * v;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kFtX * kFtY)
     const int i = i0 + x - R, j = j0 + y - R, k = k0 + z - R;
     T v = T(0);
     if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) {
-      const int e = i + g.nx * (j + g.ny * k);
+      const int e = TOMO_CHK(i + g.nx * (j + g.ny * k), g.nel, 14);
       v = ldg(in + e);
       if (MODE == 1) v = v / ldg(Hs + e);
     }
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kFtX * kFtY)
   for (int z = 0; z < kFtZ; ++z) {
     const int k = k0 + z;
     if (k >= g.nz) break;
-    const int e = i + g.nx * (j + g.ny * k);
+    const int e = TOMO_CHK(i + g.nx * (j + g.ny * k), g.nel, 14);
     T v = acc[z];
     if (MODE == 0) v = v / Hs[e];
     out[e] = v;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kFtX * kFtY)
     const int i = i0 + x - R, j = j0 + y - R, k = k0 + z - R;
     float v = 0.0f;
     if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) {
-      const int e = i + g.nx * (j + g.ny * k);
+      const int e = TOMO_CHK(i + g.nx * (j + g.ny * k), g.nel, 14);
       v = __ldg(in + e);
       if (MODE == 1) v = v / __ldg(Hs + e);
     }
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kFtX * kFtY)
   for (int z = 0; z < kFtZ; ++z) {
     const int k = k0 + z;
     if (k >= g.nz) break;
-    const int e = i + g.nx * (j + g.ny * k);
+    const int e = TOMO_CHK(i + g.nx * (j + g.ny * k), g.nel, 14);
     float v = acc[z];
     if (MODE == 0) v = v / Hs[e];
     out[e] = v;
@@ -303,12 +303,13 @@ __device__ __forceinline__ void element_modes(const Geom& g, const T* __restrict
     T w[8];
     const T* vc = v + (size_t)c * g.nn;
     const T* vlc = PAIR ? vlo + (size_t)c * g.nn : nullptr;
-    const int n0 = i + g.nxn * (j + g.nyn * k);
+    const int n0 = TOMO_CHK(i + g.nxn * (j + g.nyn * k), g.nn, 15);
     const T a0 = ldg(vc + n0);
     const T al = PAIR ? ldg(vlc + n0) : T(0);
 #pragma unroll
     for (int s = 1; s < 8; ++s) {
-      const int ns = (i + (s & 1)) + g.nxn * ((j + ((s >> 1) & 1)) + g.nyn * (k + (s >> 2)));
+      const int ns = TOMO_CHK(
+          (i + (s & 1)) + g.nxn * ((j + ((s >> 1) & 1)) + g.nyn * (k + (s >> 2))), g.nn, 15);
       T d = ldg(vc + ns) - a0;
       if (PAIR) d += ldg(vlc + ns) - al;
       w[s] = d;
@@ -640,5 +641,9 @@ int oc_max_blocks(int n) {
 INST(float)
 INST(double)
 #undef INST
+
+#ifdef TOMO_CHECKED
+TOMO_CHECK_ACCESSOR(check_word_filt)
+#endif
 
 }  // namespace tomo

@@ -14,6 +14,15 @@
 
 namespace tomo {
 
+#ifdef TOMO_CHECKED
+// the check words of the translation units with checked kernels (read, then cleared;
+// ~0 if the read failed)
+unsigned long long check_word_matvec2();
+unsigned long long check_word_matvec();
+unsigned long long check_word_vec();
+unsigned long long check_word_filt();
+#endif
+
 // Host-side fault injection sites (tomo_inject_fault / TOMO_FAULT); fault_hit(k) is true on
 // the armed pass of site k (once per arming).
 enum FaultSite {

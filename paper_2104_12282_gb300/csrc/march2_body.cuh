@@ -75,14 +75,18 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
     const bool in = k >= 0 && k < g.nzn;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      v[c].x = (in && c0) ? ldv<NC>(A.x + (size_t)c * nn + nb0 + plane * k) : 0.0f;
-      v[c].y = (in && c1) ? ldv<NC>(A.x + (size_t)c * nn + nb1 + plane * k) : 0.0f;
+      v[c].x = (in && c0)
+                   ? ldv<NC>(A.x + TOMO_CHK((size_t)c * nn + nb0 + plane * k, 3 * nn, 1))
+                   : 0.0f;
+      v[c].y = (in && c1)
+                   ? ldv<NC>(A.x + TOMO_CHK((size_t)c * nn + nb1 + plane * k, 3 * nn, 1))
+                   : 0.0f;
     }
   };
   auto load_s = [&](int k) -> float2 {
     const bool in = k >= 0 && k < g.nz;
-    return make_float2((in && e0) ? ldv<NC>(A.s + eb0 + eplane * k) : 0.0f,
-                       (in && e1) ? ldv<NC>(A.s + eb1 + eplane * k) : 0.0f);
+    return make_float2((in && e0) ? ldv<NC>(A.s + TOMO_CHK(eb0 + eplane * k, g.nel, 2)) : 0.0f,
+                       (in && e1) ? ldv<NC>(A.s + TOMO_CHK(eb1 + eplane * k, g.nel, 2)) : 0.0f);
   };
 
   // carried raw values at plane k: A0 own rows (j0, j1), N0 row j0+2, C0 = lane+1 of A0,
@@ -129,27 +133,27 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
       xp[c] = bc2(0.0f);
     }
     if (tile_fixed) {  // (CTA-uniform) only tiles that hold fixed nodes read the mask
-      if (w0) m0 = A.mask[n0];
-      if (w1) m1 = A.mask[n1];
+      if (w0) m0 = A.mask[TOMO_CHK(n0, nn, 3)];
+      if (w1) m1 = A.mask[TOMO_CHK(n1, nn, 3)];
     }
     if (MODE != M_APPLY) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if (w0) bv[c].x = ldv<NC>(A.b + (size_t)c * nn + n0);
-        if (w1) bv[c].y = ldv<NC>(A.b + (size_t)c * nn + n1);
+        if (w0) bv[c].x = ldv<NC>(A.b + TOMO_CHK((size_t)c * nn + n0, 3 * nn, 3));
+        if (w1) bv[c].y = ldv<NC>(A.b + TOMO_CHK((size_t)c * nn + n1, 3 * nn, 3));
       }
     }
     float2 inv = bc2(0.0f);  // CHEB: D^-1 of the two nodes (precomputed per level)
     if (CHEBY) {
-      if (w0) inv.x = ldv<NC>(A.invd + n0);
-      if (w1) inv.y = ldv<NC>(A.invd + n1);
+      if (w0) inv.x = ldv<NC>(A.invd + TOMO_CHK(n0, nn, 3));
+      if (w1) inv.y = ldv<NC>(A.invd + TOMO_CHK(n1, nn, 3));
     }
     if (CHEBY && A.c1 != 0.0f && !A.xprev_zero) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float* xpc = A.xprev + (size_t)c * nn;
-        if (w0) xp[c].x = NC ? xpc[n0] : __ldcg(xpc + n0);
-        if (w1) xp[c].y = NC ? xpc[n1] : __ldcg(xpc + n1);
+        if (w0) xp[c].x = NC ? xpc[TOMO_CHK(n0, nn, 3)] : __ldcg(xpc + TOMO_CHK(n0, nn, 3));
+        if (w1) xp[c].y = NC ? xpc[TOMO_CHK(n1, nn, 3)] : __ldcg(xpc + TOMO_CHK(n1, nn, 3));
       }
     }
 
@@ -304,8 +308,8 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
         if (f0) v.x = 0.0f;
         if (f1) v.y = 0.0f;
         float* dst = CHEBY ? A.xprev : A.y;
-        if (w0) dst[(size_t)c * nn + n0] = v.x;
-        if (w1) dst[(size_t)c * nn + n1] = v.y;
+        if (w0) dst[TOMO_CHK((size_t)c * nn + n0, 3 * nn, 4)] = v.x;
+        if (w1) dst[TOMO_CHK((size_t)c * nn + n1, 3 * nn, 4)] = v.y;
         if (DOT) {
           const float2 d2 = (MODE == M_APPLY) ? A0[c] : bv[c];
           pc = fma2(make_float2(w0 ? d2.x : 0.0f, w1 ? d2.y : 0.0f), v, pc);

@@ -107,7 +107,7 @@ __device__ __forceinline__ void march_body(const MarchArgs<T>& A, const ElemCons
 #pragma unroll
     for (int q = 0; q < NA; ++q) v[q] = T(0);
     if (col_in && k >= 0 && k < g.nzn) {
-      const int n = colbase + plane * k;
+      const int n = TOMO_CHK(colbase + plane * k, nn, 5);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if constexpr (JOIN) {
@@ -121,7 +121,8 @@ __device__ __forceinline__ void march_body(const MarchArgs<T>& A, const ElemCons
     }
   };
   auto load_s = [&](int k) -> T {
-    return (el_col && k >= 0 && k < g.nz) ? ldv<NC>(A.s + (ecol + eplane * k)) : T(0);
+    return (el_col && k >= 0 && k < g.nz) ? ldv<NC>(A.s + TOMO_CHK(ecol + eplane * k, g.nel, 5))
+                                          : T(0);
   };
 
   // raw node values: A* own column, B* row j+1; *0 plane k, *1 plane k+1
@@ -151,7 +152,8 @@ __device__ __forceinline__ void march_body(const MarchArgs<T>& A, const ElemCons
     sen = load_s(k + 1);
     // epilogue operands of node (i, j, k), consumed at the end of this step
     const bool emit = out_col && k >= kb;
-    const int n_out = colbase + plane * (k < 0 ? 0 : k);
+    const int n_out = emit ? TOMO_CHK(colbase + plane * (k < 0 ? 0 : k), nn, 6)
+                           : colbase + plane * (k < 0 ? 0 : k);
     unsigned mk = 0u;
     T bv[3] = {T(0), T(0), T(0)}, xp[3] = {T(0), T(0), T(0)};
     if (emit) {

@@ -126,4 +126,8 @@ template cudaError_t launch_march<float>(cudaStream_t, int, const MarchArgs<floa
 template cudaError_t launch_march<double>(cudaStream_t, int, const MarchArgs<double>&,
                                           const ElemConst<double>&, int, int*);
 
+#ifdef TOMO_CHECKED
+TOMO_CHECK_ACCESSOR(check_word_matvec)
+#endif
+
 }  // namespace tomo

@@ -194,4 +194,8 @@ cudaError_t launch_march2(cudaStream_t st, int mode, const March2Args& a, const 
   return cudaGetLastError();
 }
 
+#ifdef TOMO_CHECKED
+TOMO_CHECK_ACCESSOR(check_word_matvec2)
+#endif
+
 }  // namespace tomo

@@ -47,7 +47,9 @@ __device__ __forceinline__ void jacobi_body(int vb, int vnb, Geom g, const T* __
     const T wxa = i > 0 ? T(1) : T(0), wxb = i < g.nx ? T(1) : T(0);
     const T wya = j > 0 ? T(1) : T(0), wyb = j < g.ny ? T(1) : T(0);
     const T wza = k > 0 ? T(1) : T(0), wzb = k < g.nz ? T(1) : T(0);
-    auto row = [&](int off) { return wxa * s[off + xa] + wxb * s[off + xb]; };
+    auto row = [&](int off) {
+      return wxa * s[TOMO_CHK(off + xa, g.nel, 7)] + wxb * s[TOMO_CHK(off + xb, g.nel, 7)];
+    };
     const T S = wza * (wya * row(za + ya) + wyb * row(za + yb)) +
                 wzb * (wya * row(zb + ya) + wyb * row(zb + yb));
     const T dg = k0diag * S;
@@ -146,7 +148,9 @@ __device__ __forceinline__ void restrict_body(int vb, int vnb, Geom gf, Geom gc,
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
           const int row = iz[dz] + iy[dy];
-          const T ay = wx[0] * v[row + ix[0]] + wx[1] * v[row + ix[1]] + wx[2] * v[row + ix[2]];
+          const T ay = wx[0] * v[TOMO_CHK(row + ix[0], gf.nn, 8)] +
+                       wx[1] * v[TOMO_CHK(row + ix[1], gf.nn, 8)] +
+                       wx[2] * v[TOMO_CHK(row + ix[2], gf.nn, 8)];
           az += wy[dy] * ay;
         }
         acc[c] += wz[dz] * az;
@@ -162,7 +166,7 @@ __device__ __forceinline__ void restrict_body(int vb, int vnb, Geom gf, Geom gc,
           for (int dx = -1; dx <= 0; ++dx) {
             const int ei = I + dx, ej = J + dy, ek = K + dz;
             if (ei >= 0 && ei < gc.nx && ej >= 0 && ej < gc.ny && ek >= 0 && ek < gc.nz)
-              S += sc[ei + gc.nx * (ej + gc.ny * ek)];
+              S += sc[TOMO_CHK(ei + gc.nx * (ej + gc.ny * ek), gc.nel, 8)];
           }
       const T dg = k0diag * S;
 #pragma unroll
@@ -214,10 +218,10 @@ __device__ __forceinline__ void prolong_body(int vb, int vnb, Geom gf, Geom gc,
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T* v = xc + (size_t)c * gc.nn;
-      const T a00 = wi0 * v[r00 + i0] + wi1 * v[r00 + i1];
-      const T a10 = wi0 * v[r10 + i0] + wi1 * v[r10 + i1];
-      const T a01 = wi0 * v[r01 + i0] + wi1 * v[r01 + i1];
-      const T a11 = wi0 * v[r11 + i0] + wi1 * v[r11 + i1];
+      const T a00 = wi0 * v[TOMO_CHK(r00 + i0, gc.nn, 9)] + wi1 * v[TOMO_CHK(r00 + i1, gc.nn, 9)];
+      const T a10 = wi0 * v[TOMO_CHK(r10 + i0, gc.nn, 9)] + wi1 * v[TOMO_CHK(r10 + i1, gc.nn, 9)];
+      const T a01 = wi0 * v[TOMO_CHK(r01 + i0, gc.nn, 9)] + wi1 * v[TOMO_CHK(r01 + i1, gc.nn, 9)];
+      const T a11 = wi0 * v[TOMO_CHK(r11 + i0, gc.nn, 9)] + wi1 * v[TOMO_CHK(r11 + i1, gc.nn, 9)];
       const T acc = wk0 * (wj0 * a00 + wj1 * a10) + wk1 * (wj0 * a01 + wj1 * a11);
       const size_t idx = (size_t)c * gf.nn + n;
       if (!((mk >> c) & 1u)) xf[idx] += acc;
@@ -252,7 +256,8 @@ __global__ void k_coarsen_s(Geom gf, Geom gc, const T* __restrict__ sf, T* __res
       for (int dy = 0; dy < 2; ++dy)
         for (int dx = 0; dx < 2; ++dx) {
           const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-          if (i < gf.nx && j < gf.ny && k < gf.nz) acc += sf[i + gf.nx * (j + gf.ny * k)];
+          if (i < gf.nx && j < gf.ny && k < gf.nz)
+            acc += sf[TOMO_CHK(i + gf.nx * (j + gf.ny * k), gf.nel, 10)];
         }
     sc[e] = acc * T(0.25);
   }
@@ -272,7 +277,9 @@ __global__ void k_invdiag(Geom g, const T* __restrict__ s, T k0diag, T* __restri
     const T wxa = i > 0 ? T(1) : T(0), wxb = i < g.nx ? T(1) : T(0);
     const T wya = j > 0 ? T(1) : T(0), wyb = j < g.ny ? T(1) : T(0);
     const T wza = k > 0 ? T(1) : T(0), wzb = k < g.nz ? T(1) : T(0);
-    auto row = [&](int off) { return wxa * s[off + xa] + wxb * s[off + xb]; };
+    auto row = [&](int off) {
+      return wxa * s[TOMO_CHK(off + xa, g.nel, 11)] + wxb * s[TOMO_CHK(off + xb, g.nel, 11)];
+    };
     const T S = wza * (wya * row(za + ya) + wyb * row(za + yb)) +
                 wzb * (wya * row(zb + ya) + wyb * row(zb + yb));
     const T dg = k0diag * S;
@@ -451,7 +458,7 @@ __device__ __forceinline__ void coarse_apply_body(int n, const T* __restrict__ A
   for (int row = w0; row < n; row += nw) {
     const T* a = Ainv + (size_t)row * n;
     T acc = T(0);
-    for (int c = lane; c < n; c += 32) acc += __ldg(a + c) * rs[c];
+    for (int c = lane; c < n; c += 32) acc += __ldg(a + TOMO_CHK(c, n, 12)) * rs[c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) z[row] = dsc[row] * acc;
@@ -556,13 +563,13 @@ __device__ __forceinline__ void cg_xr_body(int vb, int vnb, int n, T* __restrict
           const int i = v << 2;
           int m = i - (i / nn) * nn;   // node of DOF i; the next three follow (wrapping at nn)
           float4 xv;
-          xv.x = c2 * rr.x * invd[m];
+          xv.x = c2 * rr.x * invd[TOMO_CHK(m, nn, 13)];
           m = (m + 1 == nn) ? 0 : m + 1;
-          xv.y = c2 * rr.y * invd[m];
+          xv.y = c2 * rr.y * invd[TOMO_CHK(m, nn, 13)];
           m = (m + 1 == nn) ? 0 : m + 1;
-          xv.z = c2 * rr.z * invd[m];
+          xv.z = c2 * rr.z * invd[TOMO_CHK(m, nn, 13)];
           m = (m + 1 == nn) ? 0 : m + 1;
-          xv.w = c2 * rr.w * invd[m];
+          xv.w = c2 * rr.w * invd[TOMO_CHK(m, nn, 13)];
           reinterpret_cast<float4*>(x1)[v] = xv;
         }
         accf.add(__fmul_rn(rr.x, rr.x));
@@ -1253,7 +1260,8 @@ __global__ void __launch_bounds__(256, 2)
       const unsigned char* tab = tables + ph.offset;
       // the unit's place, precomputed on the host: grid q, block vb of vnb, product tile
       // counts gx, gy
-      const UnitDesc ud = reinterpret_cast<const UnitDesc*>(tables + ph.units_offset)[u];
+      UnitDesc ud = reinterpret_cast<const UnitDesc*>(tables + ph.units_offset)[u];
+      ud.q = (int)TOMO_CHK(ud.q, *reinterpret_cast<const int*>(tab), 17);
       *sp = p;
       *su = u;
       switch (ph.kind) {
@@ -1329,5 +1337,9 @@ cudaError_t launch_persist(cudaStream_t st, const DevPhase* phases, int nph,
   return cudaLaunchKernelEx(&cfg, k_persist, phases, nph, tables, k2, k1, barrier, limit_ns,
                             scs, nscs, acc);
 }
+
+#ifdef TOMO_CHECKED
+TOMO_CHECK_ACCESSOR(check_word_vec)
+#endif
 
 }  // namespace tomo

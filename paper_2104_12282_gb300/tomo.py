@@ -14,7 +14,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libtomo.so")
+# TOMO_LIB=checked selects the bounds-checked build (tomo_check_report)
+LIB_PATH = os.path.join(_HERE, "_lib", "libtomo_checked.so" if os.environ.get("TOMO_LIB") ==
+                        "checked" else "libtomo.so")
 
 FP64, FP32 = 0, 1
 PRECOND_MG, PRECOND_JACOBI = 0, 1
@@ -126,6 +128,8 @@ def _load():
         "tomo_batch_lockstep_runs": (st, [P, ctypes.POINTER(ctypes.c_int64)]),
         "tomo_batch_phase_times": (st, [P, P]),
         "tomo_inject_fault": (st, [ctypes.c_char_p, ctypes.c_int32]),
+        "tomo_check_report": (st, [ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_uint64)]),
         "tomo_batch_set_persistent": (st, [P, ctypes.c_int32]),
         "tomo_batch_set_tiles": (st, [P, ctypes.c_int32, ctypes.c_int32]),
         "tomo_batch_get_tiles": (st, [P, ctypes.POINTER(ctypes.c_int32),
@@ -219,6 +223,7 @@ def exported_symbols():
             "tomo_batch_create", "tomo_batch_append", "tomo_batch_size",
             "tomo_batch_set_lockstep", "tomo_batch_lockstep_runs", "tomo_batch_phase_times",
             "tomo_batch_set_persistent", "tomo_batch_set_wait_limit", "tomo_inject_fault",
+            "tomo_check_report",
             "tomo_batch_persistent_info", "tomo_batch_persistent_phase_ns",
             "tomo_batch_set_tiles", "tomo_batch_get_tiles", "tomo_batch_autotune_tiles",
             "tomo_batch_gradient", "tomo_batch_destroy", "tomo_batch_last_error",
@@ -270,6 +275,16 @@ def inject_fault(site, nth=1):
     st = lib().tomo_inject_fault(str(site).encode(), int(nth))
     if st != 0:
         raise TomoError(st, f"unknown fault site {site!r} or nth < 0")
+
+
+def check_report():
+    """(checked build?, first recorded index violation or 0) from tomo_check_report; the
+    records are cleared.  The word holds the site in bits 48-63 and the index below."""
+    c, w = ctypes.c_int32(), ctypes.c_uint64()
+    st = lib().tomo_check_report(ctypes.byref(c), ctypes.byref(w))
+    if st != 0:
+        raise TomoError(st, "tomo_check_report")
+    return bool(c.value), w.value
 
 
 def _current_stream():

@@ -38,6 +38,21 @@ def test_library_exports_every_declared_symbol(libpath):
     assert not missing, missing
 
 
+def test_checked_library_exports_every_declared_symbol(libpath):
+    """The bounds-checked variant (-DTOMO_CHECKED) has the same boundary and says so."""
+    from paper_2104_12282_gb300 import _build
+    if not os.path.exists(_build.LIB_CHECKED):
+        _build.build(checked=True)
+    lib = ctypes.CDLL(_build.LIB_CHECKED)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    plain = ctypes.CDLL(libpath)
+    for L, want in ((plain, 0),):
+        c, w = ctypes.c_int32(-1), ctypes.c_uint64(7)
+        assert L.tomo_check_report(ctypes.byref(c), ctypes.byref(w)) == 0
+        assert c.value == want and w.value == 0
+
+
 def test_binding_signatures_cover_header(libpath):
     from paper_2104_12282_gb300 import tomo
     assert set(tomo.exported_symbols()) == set(_declared())
