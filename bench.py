@@ -375,7 +375,7 @@ def extras(args, dev, stream):
         best, _ = g.autotune(z)    # smoother autotuner on the evolved design
         g.gradient(z, dc, dv)
         ms_t, (c_t, info_t) = timed(lambda: g.gradient(z, dc, dv), 3)
-        g.set_smoother(2, 2)
+        g.set_smoother(2, 2, 20.0)
         g.set_smoother_bound(0.0)
         g.set_cycle(0)
         out["evolved_field"] = {
@@ -386,6 +386,7 @@ def extras(args, dev, stream):
             "warm_cg_iters_mean": statistics.mean(warm_its),
             "autotuned": {"fine_degree": best[0], "coarse_degree": best[1],
                           "smoothing_bound": best[2], "w_cycle_levels": best[3],
+                          "interval_ratio": best[4],
                           "cold_ms_per_grad": ms_t, "cold_cg_iters": info_t.iters}}
         # two-scale step of Algorithm 1 at N_B = 4 on the bumpy field
         nb = 4
@@ -497,10 +498,11 @@ def run_ours(args):
     # ---------------- mixed path: timed steps ----------------
     g = make(tomo.FP32, 1e-6)
     zs = [torch.tensor(f, dtype=torch.float32, device=dev) for f in fields]
-    # the smoother (Chebyshev degrees and interval) chosen by the library's autotuner on a
-    # third field of the same recipe, before and outside the timed region
-    ztune = torch.tensor(P.bumpy_field(p.dims, args.seed + 2), dtype=torch.float32,
-                         device=dev)
+    # the smoother (Chebyshev degrees, interval and cycle) chosen by the library's autotuner
+    # on three other fields of the same recipe (seeds 2-4), before and outside the timed
+    # region
+    ztune = [torch.tensor(P.bumpy_field(p.dims, args.seed + 2 + k), dtype=torch.float32,
+                          device=dev) for k in range(3)]
     tuned, _ = g.autotune(ztune, reps=2)
     del ztune
     dc = torch.empty_like(zs[0])
@@ -536,7 +538,7 @@ def run_ours(args):
     fallbacks = g.smoother_bound()[2]
 
     # the same steps with the default smoother (degrees 2, 2 on the element bound)
-    g.set_smoother(2, 2)
+    g.set_smoother(2, 2, 20.0)
     g.set_smoother_bound(0.0)
     g.set_cycle(0)
     for w in range(2):
@@ -554,7 +556,7 @@ def run_ours(args):
     barrier()
     ms_def = [a.elapsed_time(b) for a, b in ev_def]
     value_def = whole_job_rate(world, args.steps, slowest(sum(ms_def)))
-    g.set_smoother(tuned[0], tuned[1])
+    g.set_smoother(tuned[0], tuned[1], tuned[4])
     g.set_smoother_bound(tuned[2])
     g.set_cycle(tuned[3])
 
@@ -659,9 +661,10 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}", "cg_iters": iters[0],
                    "smoother": {"fine_degree": tuned[0], "coarse_degree": tuned[1],
                                 "bound": tuned[2], "w_cycle_levels": tuned[3],
+                                "interval_ratio": tuned[4],
                                 "bound_fallbacks": fallbacks,
-                                "chosen_by": "tomo_autotune_smoother on the seed-2 field of "
-                                             "the same recipe, untimed"}},
+                                "chosen_by": "tomo_autotune_smoother_multi on the seed 2-4 "
+                                             "fields of the same recipe, untimed"}},
         "default_smoother": {"value": value_def, "unit": UNIT,
                              "ms_per_step": statistics.mean(ms_def), "cg_iters": it_def[0],
                              "setting": "degrees 2, 2 on the element bound"},

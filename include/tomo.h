@@ -273,19 +273,23 @@ tomo_status tomo_get_smoother_bound(const tomo_grid* grid, double* lam, double* 
 /* Smoother autotuner.  On the design z (N_el, host or device; filtered and turned into the
  * material as tomo_gradient does) it times the state solve from a zero start for each
  * candidate (pairs[2k], pairs[2k+1]) = (fine_degree, coarse_degree), k < n (1..64), at the
- * grid's current ratio and bound: one untimed solve (skipped when the grid kept that
+ * grid's current ratio, bound and cycle: one untimed solve (skipped when the grid kept that
  * candidate's captured loop from an earlier use: a grid keeps the loops of up to 8 smoother
  * settings), then reps (1..16) solves timed with CUDA events on the grid's stream, the
- * median kept.  pairs == NULL: the built-in list (2,2) (2,3) (2,4) (1,3) (1,4) (1,6), each at
- * 1, 0.75 and 0.68 times the element bound, as V-cycles (18 candidates), then the fastest
- * of these with a W-cycle at level 1 and at levels 1 and 2 (tomo_set_cycle masks 2 and 6):
- * 20 candidates, n ignored, results needs room for 20.  A caller's list keeps the grid's
- * bound and cycle.  Candidates are timed without the bound fallback of the solves (a
- * candidate that fails is only marked failed).  The fastest candidate that converges
- * becomes the grid's smoother and cycle; results[k] (may be NULL) holds each candidate's
- * median milliseconds (-1 when it failed), iterations, status, bound and cycle mask; *best
- * (may be NULL) its index.  If no candidate converges the grid keeps its previous setting
- * and ENOCONV is returned.  The grid's displacement is left as the last trial's. */
+ * median kept.  pairs == NULL: the built-in stages, 23 candidates (n ignored; results needs
+ * room for 23): the degree pairs (2,2) (2,3) (2,4) (1,3) (1,4) (1,6), each at 1, 0.75 and
+ * 0.68 times the element bound, as V-cycles (18); the fastest of these with a W-cycle at
+ * level 1 and at levels 1 and 2 (tomo_set_cycle masks 2 and 6); the fastest so far with the
+ * smoothing interval [lam/ratio, lam] at ratios 12, 30 and 50.  Candidates are timed
+ * without the bound fallback of the solves (a candidate that fails is only marked failed).
+ * The fastest candidate that converges becomes the grid's smoother and cycle; results[k]
+ * (may be NULL) holds each candidate's median milliseconds (-1 when it failed or its stage
+ * did not run), iterations, status, bound, cycle mask and ratio; *best (may be NULL) its
+ * index.  If no candidate converges the grid keeps its previous setting and ENOCONV is
+ * returned.  The grid's displacement is left as the last trial's.
+ * tomo_autotune_smoother_multi: the same on nz (1..16) designs z[0..nz): a candidate's time
+ * is the sum of its medians over the designs, its iterations the largest count, and it
+ * fails if it fails on any design (a setting for a family of designs rather than one). */
 typedef struct {
   int32_t fine_degree, coarse_degree;
   int32_t iters;
@@ -294,6 +298,7 @@ typedef struct {
   double lam;         /* upper end of the smoothing interval the candidate used */
   uint32_t w_levels;  /* the candidate's cycle (tomo_set_cycle mask) */
   uint32_t reserved;
+  double ratio;       /* the candidate's interval ratio (lam / lower end) */
 } tomo_tune_result;
 tomo_status tomo_autotune_smoother(tomo_grid* grid, const float* z, const int32_t* pairs,
                                    int32_t n, int32_t reps, tomo_tune_result* results,
@@ -301,6 +306,13 @@ tomo_status tomo_autotune_smoother(tomo_grid* grid, const float* z, const int32_
 tomo_status tomo_autotune_smoother_d(tomo_grid* grid, const double* z, const int32_t* pairs,
                                      int32_t n, int32_t reps, tomo_tune_result* results,
                                      int32_t* best);
+tomo_status tomo_autotune_smoother_multi(tomo_grid* grid, const float* const* z, int32_t nz,
+                                         const int32_t* pairs, int32_t n, int32_t reps,
+                                         tomo_tune_result* results, int32_t* best);
+tomo_status tomo_autotune_smoother_multi_d(tomo_grid* grid, const double* const* z,
+                                           int32_t nz, const int32_t* pairs, int32_t n,
+                                           int32_t reps, tomo_tune_result* results,
+                                           int32_t* best);
 
 /* Copy the displacement of the last tomo_gradient / tomo_solve on this grid to u
  * (3*N_n, host or device). */
@@ -320,8 +332,11 @@ tomo_status tomo_get_launch_count(const tomo_grid* grid, int64_t* launches);
  * the grid's stream and accumulates their count, total milliseconds and algorithmic DRAM
  * bytes (inputs read once plus outputs written once); the CG loop is then issued from the
  * host (same kernels, same order) because event records cannot sit inside the device-side
- * loop.  tomo_profile_read waits for the stream, returns the totals since the last reset
- * and resets them.  enable bit 1: events at phase boundaries only (device-side loop kept);
+ * loop; the host issues iterations four at a time, so the launches enqueued after the
+ * solve stopped (the rest of the last iteration after its convergence test, and up to
+ * three further iterations) return at once on the device flag: they are left out of the
+ * totals and the level tables.  tomo_profile_read waits for the stream, returns the totals
+ * since the last reset and resets them.  enable bit 1: events at phase boundaries only (device-side loop kept);
  * tomo_profile_phases returns the accumulated milliseconds of ms[0] filter + material,
  * ms[1] multigrid level setup, ms[2] CG solve, ms[3] compliance + sensitivity, ms[4] filter
  * adjoints, ms[6] OC step (ms[5] unused) and the number of gradient calls, then resets. */

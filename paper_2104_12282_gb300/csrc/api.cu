@@ -295,13 +295,26 @@ tomo_status prof_end(tomo_grid* G, double bytes, int tag = -1) {
   if (!G->prof) return TOMO_OK;
   CK(cudaEventRecord(G->ev[G->ev_used + 1], G->stream));
   G->ev_used += 2;
-  if ((int)G->ev_tag.size() < (int)G->ev_used / 2) G->ev_tag.resize(G->ev_used / 2);
-  G->ev_tag[G->ev_used / 2 - 1] = tag;
-  if (tag < 0) {
-    G->prof_launches += 1;
-    G->prof_bytes += bytes;
+  const size_t rec = G->ev_used / 2 - 1;
+  if (G->ev_tag.size() <= rec) {
+    G->ev_tag.resize(rec + 1);
+    G->ev_bytes.resize(rec + 1);
+    G->ev_iter.resize(rec + 1);
+    G->ev_post.resize(rec + 1);
   }
+  G->ev_tag[rec] = tag;
+  G->ev_bytes[rec] = bytes;
+  G->ev_iter[rec] = G->prof_iter;
+  G->ev_post[rec] = G->prof_post ? 1 : 0;
   return TOMO_OK;
+}
+
+// After a host-issued solve that stopped at iteration itf: the launches it enqueued after
+// the stop (the rest of iteration itf after its x/r update, and the iterations after it)
+// returned at once on the device flag and did no work; they are left out of the timing.
+void prof_drop_idle(tomo_grid* G, size_t rec0, int itf) {
+  for (size_t q = rec0; q < G->ev_used / 2 && q < G->ev_tag.size(); ++q)
+    if (G->ev_iter[q] > itf || (G->ev_iter[q] == itf && G->ev_post[q])) G->ev_tag[q] = -2;
 }
 
 // Level timing of one launch (kernel-timing mode): tag = level + 1.
@@ -631,6 +644,7 @@ tomo_status enqueue_iteration(tomo_grid* G) {
   CK(launch_cg_xr<T>(G->stream, n, xhi, xlo, r, p, q, G->partials, G->counter, G->sc, x1,
                      (const T*)G->invd, c2));
   G->launches += 1;
+  G->prof_post = true;  // the convergence test of this iteration is enqueued
   if (G->d.rr_every > 0) {
     // residual replacement r = f - K x on iterations it % rr_every == 0 (device gate), in
     // FP64 for both precisions
@@ -868,13 +882,24 @@ tomo_status pcg_once(tomo_grid* G, bool warm, tomo_solve_info* info) {
     const int batch = 4;
     int it = 0;
     bool done = false;
+    const size_t rec0 = G->ev_used / 2;
     while (!done) {
-      for (int b2 = 0; b2 < batch; ++b2, ++it) TRY(enqueue_iteration<T>(G));
+      for (int b2 = 0; b2 < batch; ++b2, ++it) {
+        G->prof_iter = it + 1;
+        G->prof_post = false;
+        const tomo_status se = enqueue_iteration<T>(G);
+        if (se != TOMO_OK) {
+          G->prof_iter = 0;
+          return se;
+        }
+      }
+      G->prof_iter = 0;
       CK(cudaMemcpyAsync(G->h_sc, G->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, G->stream));
       TRY(sync(G));
       done = G->h_sc->done != 0;
       if (it > G->d.maxit + batch) done = true;
     }
+    if (G->prof) prof_drop_idle(G, rec0, G->h_sc->it);
   }
   return pcg_result(G, info);
 }
@@ -1696,12 +1721,13 @@ tomo_status set_smoother(tomo_grid* G, int fine, int coarse, double ratio, doubl
 }
 
 // The smoother autotuner: the state solve K(P z) u = f (cold start) timed with CUDA events
-// on the grid's stream for each candidate (fine, coarse) degree pair, reps times after one
-// untimed solve (which also captures that candidate's loop); the fastest candidate that
-// converges is kept.
+// on the grid's stream for each candidate setting, on each of the nz designs (one untimed
+// solve, which also captures the candidate's loop unless the grid kept it, then the median
+// of reps), the medians summed over the designs; the fastest candidate that converges on
+// every design is kept.
 template <typename T>
-tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, int reps,
-                        tomo_tune_result* res, int32_t* best) {
+tomo_status do_autotune(tomo_grid* G, const T* const* zs, int nz, const int32_t* pairs, int n,
+                        int reps, tomo_tune_result* res, int32_t* best) {
   // (fine, coarse) degrees: (2, 2) is fastest on random fields, (1, 4) on OC-evolved
   // designs (near 0/1 densities), measured on the 192x96x76 MBB-type block; with the
   // built-in list each pair is also tried at 0.75 and 0.68 of the element bound of the
@@ -1709,118 +1735,149 @@ tomo_status do_autotune(tomo_grid* G, const T* z, const int32_t* pairs, int n, i
   // the bound of 5.3, which only isolated elements reach)
   static const int32_t kDefault[] = {2, 2, 2, 3, 2, 4, 1, 3, 1, 4, 1, 6};
   static const double kBoundScale[] = {1.0, 0.75, 0.68};
-  if (!z) return fail(G, TOMO_EINVAL, "null array");
   // after the V-cycle candidates of the built-in list, the best of them is tried with a
-  // W-cycle at level 1 and at levels 1 and 2 (bit masks 2 and 6)
+  // W-cycle at level 1 and at levels 1 and 2 (bit masks 2 and 6); then the best so far with
+  // the interval [lam/ratio, lam] at ratios 12, 30 and 50 instead of the grid's
   static const uint32_t kWStage[] = {2u, 6u};
+  static const double kRatioStage[] = {12.0, 30.0, 50.0};
+  if (!zs || nz < 1 || nz > 16) return fail(G, TOMO_EINVAL, "autotune: 1..16 designs");
+  for (int d = 0; d < nz; ++d)
+    if (!zs[d]) return fail(G, TOMO_EINVAL, "null array");
   struct Cand {
     int fine, coarse;
-    double lam;
+    double lam, ratio;
     uint32_t w;
   };
+  const double ratio0 = G->cheb_ratio;
   std::vector<Cand> cands;
-  int n_v = 0;  // candidates before the W stage (all of them with a caller's list)
+  std::vector<int> stage_end;  // candidates [stage_end[s-1], stage_end[s]) form stage s
   if (!pairs) {
     for (double f : kBoundScale)
       for (size_t k = 0; k + 1 < sizeof(kDefault) / sizeof(kDefault[0]); k += 2)
-        cands.push_back(Cand{kDefault[k], kDefault[k + 1], f * G->lam_bound, 0u});
-    n_v = (int)cands.size();
-    n = n_v + (int)(sizeof(kWStage) / sizeof(kWStage[0]));
+        cands.push_back(Cand{kDefault[k], kDefault[k + 1], f * G->lam_bound, ratio0, 0u});
+    const int nv = (int)cands.size();
+    stage_end = {nv, nv + 2, nv + 5};
   } else {
     if (n < 1 || n > 64)
       return fail(G, TOMO_EINVAL, "autotune: 1..64 candidates and 1..16 repetitions");
     for (int k = 0; k < n; ++k)
-      cands.push_back(Cand{pairs[2 * k], pairs[2 * k + 1], G->lam_hi, G->wlevels});
-    n_v = n;
+      cands.push_back(Cand{pairs[2 * k], pairs[2 * k + 1], G->lam_hi, ratio0, G->wlevels});
+    stage_end = {n};
   }
+  const int ntot = stage_end.back();
   if (reps < 1 || reps > 16)
     return fail(G, TOMO_EINVAL, "autotune: 1..64 candidates and 1..16 repetitions");
   if (G->d.precond != TOMO_PRECOND_MG)
     return fail(G, TOMO_EINVAL, "autotune: the grid has no multigrid smoother");
-  for (int k = 0; k < n_v; ++k)
+  for (int k = 0; k < stage_end[0]; ++k)
     if (cands[k].fine < 1 || cands[k].fine > 16 || cands[k].coarse < 1 || cands[k].coarse > 16)
       return fail(G, TOMO_EINVAL, "autotune: candidate %d has a degree outside 1..16", k);
   const int fine0 = G->d.smoother_degree, coarse0 = G->d.coarse_degree;
-  const double ratio = G->cheb_ratio, lam0 = G->lam_hi;
+  const double lam0 = G->lam_hi;
   const uint32_t w0 = G->wlevels;
   const size_t be = sizeof(T) * (size_t)G->g.nel;
-  const void* dz;
-  bool h1;
-  TRY(stage_in(G, z, be, 0, &dz, &h1));
   const tomo_grid_desc& d = G->d;
-  CK(launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
-                      G->filter_radius, (const T*)dz, (const T*)G->Hs, (T*)G->rho, 0, 1,
-                      (T)d.E0, (T)d.Emin, (T)d.penal, (T)d.h, (T*)G->L[0].s));
-  G->launches += 1;
-  TRY(setup_levels<T>(G));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     CK(cudaGetLastError());
   }
+  std::vector<double> sum(ntot, 0.0);
+  std::vector<int> iters(ntot, 0), status(ntot, TOMO_OK);
   int bi = -1;
-  double bms = 0.0;
   tomo_status st = TOMO_OK;
-  for (int k = 0; k < n && st == TOMO_OK; ++k) {
-    if (k == n_v) {  // the W stage, from the best V candidate
+  int k0 = 0;
+  for (size_t sg = 0; sg < stage_end.size() && st == TOMO_OK; ++sg) {
+    if (sg > 0) {  // the next stage starts from the best candidate so far
       if (bi < 0) break;
       const Cand b = cands[bi];
-      for (uint32_t w : kWStage) cands.push_back(Cand{b.fine, b.coarse, b.lam, w});
+      if (sg == 1)
+        for (uint32_t w : kWStage) cands.push_back(Cand{b.fine, b.coarse, b.lam, b.ratio, w});
+      else
+        for (double r : kRatioStage) cands.push_back(Cand{b.fine, b.coarse, b.lam, r, b.w});
     }
-    st = set_smoother(G, cands[k].fine, cands[k].coarse, ratio, cands[k].lam, cands[k].w);
-    if (st != TOMO_OK) break;
-    tomo_solve_info info{};
-    // untimed solve, which captures this candidate's loop, unless the grid kept it; a
-    // candidate is timed as it is, without the fallback to the element bound
-    tomo_status sk = TOMO_OK;
-    if (!G->loop_exec || G->prof) sk = pcg<T>(G, false, &info, false);
-    std::vector<double> ms;
-    for (int r = 0; r < reps && sk == TOMO_OK; ++r) {
-      float t = 0.0f;
-      if (cudaEventRecord(e0, G->stream) != cudaSuccess) sk = TOMO_ECUDA;
-      if (sk == TOMO_OK) sk = pcg<T>(G, false, &info, false);
-      if (sk == TOMO_OK && (cudaEventRecord(e1, G->stream) != cudaSuccess ||
-                            cudaEventSynchronize(e1) != cudaSuccess ||
-                            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
-        sk = TOMO_ECUDA;
-      ms.push_back(t);
-    }
-    if (sk == TOMO_ECUDA) {
-      cudaGetLastError();
-      st = fail(G, TOMO_ECUDA, "autotune: CUDA error while timing candidate %d", k);
-      break;
-    }
-    double med = 0.0;
-    if (sk == TOMO_OK) {
-      std::sort(ms.begin(), ms.end());
-      med = ms[ms.size() / 2];
-      if (bi < 0 || med < bms) {
-        bi = k;
-        bms = med;
+    const int k1 = stage_end[sg];
+    for (int dsg = 0; dsg < nz && st == TOMO_OK; ++dsg) {
+      // the material of design dsg
+      const void* dz;
+      bool h1;
+      st = stage_in(G, zs[dsg], be, 0, &dz, &h1);
+      if (st != TOMO_OK) break;
+      if (launch_filter<T>(G->stream, G->g, G->d_taps, (const T*)G->d_tapw, G->ntaps,
+                           G->filter_radius, (const T*)dz, (const T*)G->Hs, (T*)G->rho, 0, 1,
+                           (T)d.E0, (T)d.Emin, (T)d.penal, (T)d.h, (T*)G->L[0].s) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        st = fail(G, TOMO_ECUDA, "autotune: filter launch failed");
+        break;
+      }
+      G->launches += 1;
+      st = setup_levels<T>(G);
+      if (st != TOMO_OK) break;
+      for (int k = k0; k < k1 && st == TOMO_OK; ++k) {
+        if (status[k] != TOMO_OK) continue;  // failed on an earlier design
+        st = set_smoother(G, cands[k].fine, cands[k].coarse, cands[k].ratio, cands[k].lam,
+                          cands[k].w);
+        if (st != TOMO_OK) break;
+        tomo_solve_info info{};
+        // untimed solve, which captures this candidate's loop, unless the grid kept it; a
+        // candidate is timed as it is, without the fallback to the element bound
+        tomo_status sk = TOMO_OK;
+        if (!G->loop_exec || G->prof) sk = pcg<T>(G, false, &info, false);
+        std::vector<double> ms;
+        for (int r = 0; r < reps && sk == TOMO_OK; ++r) {
+          float t = 0.0f;
+          if (cudaEventRecord(e0, G->stream) != cudaSuccess) sk = TOMO_ECUDA;
+          if (sk == TOMO_OK) sk = pcg<T>(G, false, &info, false);
+          if (sk == TOMO_OK && (cudaEventRecord(e1, G->stream) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+            sk = TOMO_ECUDA;
+          ms.push_back(t);
+        }
+        if (sk == TOMO_ECUDA) {
+          cudaGetLastError();
+          st = fail(G, TOMO_ECUDA, "autotune: CUDA error while timing candidate %d", k);
+          break;
+        }
+        status[k] = sk;
+        iters[k] = std::max(iters[k], (int)info.iters);
+        if (sk == TOMO_OK) {
+          std::sort(ms.begin(), ms.end());
+          sum[k] += ms[ms.size() / 2];
+        }
       }
     }
-    if (res) {
-      res[k].fine_degree = cands[k].fine;
-      res[k].coarse_degree = cands[k].coarse;
-      res[k].iters = info.iters;
-      res[k].status = sk;
-      res[k].ms = sk == TOMO_OK ? med : -1.0;
-      res[k].lam = cands[k].lam;
-      res[k].w_levels = cands[k].w;
-    }
+    for (int k = k0; k < k1; ++k)
+      if (status[k] == TOMO_OK && (bi < 0 || sum[k] < sum[bi])) bi = k;
+    k0 = k1;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (res)
+    for (int k = 0; k < ntot; ++k) {
+      const bool ran = k < (int)cands.size();
+      res[k].fine_degree = ran ? cands[k].fine : 0;
+      res[k].coarse_degree = ran ? cands[k].coarse : 0;
+      res[k].iters = iters[k];
+      res[k].status = ran ? status[k] : TOMO_ENOCONV;
+      res[k].ms = (ran && status[k] == TOMO_OK && k < k0) ? sum[k] : -1.0;
+      res[k].lam = ran ? cands[k].lam : 0.0;
+      res[k].w_levels = ran ? cands[k].w : 0u;
+      res[k].reserved = 0u;
+      res[k].ratio = ran ? cands[k].ratio : 0.0;
+    }
   if (st == TOMO_OK && bi < 0)
     st = fail(G, TOMO_ENOCONV, "autotune: no candidate converged");
   if (st != TOMO_OK) {
     std::string why = G->err;
-    set_smoother(G, fine0, coarse0, ratio, lam0, w0);
+    set_smoother(G, fine0, coarse0, ratio0, lam0, w0);
     G->err = why;
     return st;
   }
-  TRY(set_smoother(G, cands[bi].fine, cands[bi].coarse, ratio, cands[bi].lam, cands[bi].w));
+  TRY(set_smoother(G, cands[bi].fine, cands[bi].coarse, cands[bi].ratio, cands[bi].lam,
+                   cands[bi].w));
   if (best) *best = bi;
   return TOMO_OK;
 }
@@ -1988,7 +2045,8 @@ tomo_status tomo_autotune_smoother(tomo_grid* G, const float* z, const int32_t* 
   if (!G) return TOMO_EINVAL;
   g_cur_err = &G->err;
   TRY(check_prec(G, false));
-  return do_autotune<float>(G, z, pairs, n, reps, results, best);
+  const float* zs[1] = {z};
+  return do_autotune<float>(G, zs, 1, pairs, n, reps, results, best);
 }
 
 tomo_status tomo_autotune_smoother_d(tomo_grid* G, const double* z, const int32_t* pairs,
@@ -1997,7 +2055,26 @@ tomo_status tomo_autotune_smoother_d(tomo_grid* G, const double* z, const int32_
   if (!G) return TOMO_EINVAL;
   g_cur_err = &G->err;
   TRY(check_prec(G, true));
-  return do_autotune<double>(G, z, pairs, n, reps, results, best);
+  const double* zs[1] = {z};
+  return do_autotune<double>(G, zs, 1, pairs, n, reps, results, best);
+}
+
+tomo_status tomo_autotune_smoother_multi(tomo_grid* G, const float* const* z, int32_t nz,
+                                         const int32_t* pairs, int32_t n, int32_t reps,
+                                         tomo_tune_result* results, int32_t* best) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  TRY(check_prec(G, false));
+  return do_autotune<float>(G, z, nz, pairs, n, reps, results, best);
+}
+
+tomo_status tomo_autotune_smoother_multi_d(tomo_grid* G, const double* const* z, int32_t nz,
+                                           const int32_t* pairs, int32_t n, int32_t reps,
+                                           tomo_tune_result* results, int32_t* best) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  TRY(check_prec(G, true));
+  return do_autotune<double>(G, z, nz, pairs, n, reps, results, best);
 }
 
 tomo_status tomo_set_cycle(tomo_grid* G, uint32_t w_levels) {
@@ -2210,8 +2287,11 @@ tomo_status tomo_profile_read(tomo_grid* G, int64_t* launches, double* total_ms,
     float t = 0.0f;
     CK(cudaEventElapsedTime(&t, G->ev[q], G->ev[q + 1]));
     const int tag = (q / 2 < G->ev_tag.size()) ? G->ev_tag[q / 2] : -1;
+    if (tag == -2) continue;  // enqueued after the solve stopped: no work
     if (tag < 0) {
       ms += t;
+      G->prof_launches += 1;
+      G->prof_bytes += G->ev_bytes[q / 2];
       G->level_ms[0] += t;
       G->level_n[0] += 1;
     } else if (tag - 1 < 16) {

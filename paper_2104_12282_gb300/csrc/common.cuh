@@ -118,8 +118,9 @@ __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 // Checked build (-DTOMO_CHECKED): a computed index passes through TOMO_CHK(i, n, site); one
 // outside [0, n) is recorded in this translation unit's check word (the first violation:
 // site in bits 48-63, the index's low 48 bits below) and replaced by 0, so the access stays
-// inside its buffer; no trap.  The host reads and clears the words (tomo_check_report).
-// Without TOMO_CHECKED the macro is the index itself.
+// inside its buffer; no trap.  TOMO_AT(base, off, n, site) is the checked address base + off.
+// The host reads and clears the words (tomo_check_report).  Without TOMO_CHECKED the macros
+// are the index and the address themselves.
 #ifdef TOMO_CHECKED
 namespace {
 __device__ unsigned long long g_check_word = 0ull;
@@ -133,6 +134,7 @@ __device__ __forceinline__ long long tomo_chk(long long i, long long n, int site
   return i;
 }
 #define TOMO_CHK(i, n, site) tomo_chk((long long)(i), (long long)(n), (site))
+#define TOMO_AT(base, off, n, site) ((base) + tomo_chk((long long)(off), (long long)(n), (site)))
 // host accessor of this translation unit's word (read, then cleared)
 #define TOMO_CHECK_ACCESSOR(fn)                                                   \
   unsigned long long fn() {                                                       \
@@ -146,6 +148,8 @@ __device__ __forceinline__ long long tomo_chk(long long i, long long n, int site
   }
 #else
 #define TOMO_CHK(i, n, site) (i)
+// base + off with the tokens as written (the regular build's address arithmetic unchanged)
+#define TOMO_AT(base, off, n, site) base + off
 #endif
 
 // Load of data that does not change while the kernel runs (NC: the read-only path), or, in

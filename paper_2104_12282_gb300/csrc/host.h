@@ -457,7 +457,13 @@ struct tomo_grid {
   size_t ev_used = 0;
   int64_t prof_launches = 0;
   double prof_bytes = 0.0;
-  std::vector<int> ev_tag;          // per event pair: -1 fine-level product, else level + 1
+  std::vector<int> ev_tag;          // per event pair: -1 fine-level product, else level + 1;
+                                    // -2: a launch that found the solve stopped (no work)
+  std::vector<double> ev_bytes;     // per event pair: algorithmic bytes of a product launch
+  std::vector<int> ev_iter;         // per event pair: CG iteration that enqueued it (0: none)
+  std::vector<char> ev_post;        // ... after that iteration's x/r update
+  int prof_iter = 0;                // the CG iteration being enqueued (host-issued loop)
+  bool prof_post = false;
   double level_ms[16] = {};         // eager V-cycle time per level (all kernels), level 0..15
   int64_t level_n[16] = {};
   size_t dev_bytes = 0;        // device memory held by this grid (cudaMalloc through dalloc)

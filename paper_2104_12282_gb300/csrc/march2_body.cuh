@@ -76,17 +76,17 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       v[c].x = (in && c0)
-                   ? ldv<NC>(A.x + TOMO_CHK((size_t)c * nn + nb0 + plane * k, 3 * nn, 1))
+                   ? ldv<NC>(TOMO_AT(A.x, (size_t)c * nn + nb0 + plane * k, 3 * nn, 1))
                    : 0.0f;
       v[c].y = (in && c1)
-                   ? ldv<NC>(A.x + TOMO_CHK((size_t)c * nn + nb1 + plane * k, 3 * nn, 1))
+                   ? ldv<NC>(TOMO_AT(A.x, (size_t)c * nn + nb1 + plane * k, 3 * nn, 1))
                    : 0.0f;
     }
   };
   auto load_s = [&](int k) -> float2 {
     const bool in = k >= 0 && k < g.nz;
-    return make_float2((in && e0) ? ldv<NC>(A.s + TOMO_CHK(eb0 + eplane * k, g.nel, 2)) : 0.0f,
-                       (in && e1) ? ldv<NC>(A.s + TOMO_CHK(eb1 + eplane * k, g.nel, 2)) : 0.0f);
+    return make_float2((in && e0) ? ldv<NC>(TOMO_AT(A.s, eb0 + eplane * k, g.nel, 2)) : 0.0f,
+                       (in && e1) ? ldv<NC>(TOMO_AT(A.s, eb1 + eplane * k, g.nel, 2)) : 0.0f);
   };
 
   // carried raw values at plane k: A0 own rows (j0, j1), N0 row j0+2, C0 = lane+1 of A0,
@@ -139,8 +139,8 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
     if (MODE != M_APPLY) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if (w0) bv[c].x = ldv<NC>(A.b + TOMO_CHK((size_t)c * nn + n0, 3 * nn, 3));
-        if (w1) bv[c].y = ldv<NC>(A.b + TOMO_CHK((size_t)c * nn + n1, 3 * nn, 3));
+        if (w0) bv[c].x = ldv<NC>(TOMO_AT(A.b, (size_t)c * nn + n0, 3 * nn, 3));
+        if (w1) bv[c].y = ldv<NC>(TOMO_AT(A.b, (size_t)c * nn + n1, 3 * nn, 3));
       }
     }
     float2 inv = bc2(0.0f);  // CHEB: D^-1 of the two nodes (precomputed per level)

@@ -36,18 +36,35 @@ def paper_cantilever(mesh: int, volfrac: float = 0.12, radius: float = 0.08) -> 
 
 def save_checkpoint(path: str, k: int, z, hist, smoother) -> None:
     """State of an OC run after its iteration k-1 (the design z, the history so far and the
-    smoother setting), written atomically (temporary file, then rename)."""
+    smoother setting (fine, coarse, ratio[, bound, W-cycle mask])), written atomically
+    (temporary file, then rename)."""
     tmp = path + ".tmp.npz"
-    np.savez(tmp, next_it=np.int64(k), z=np.asarray(z), smoother=np.asarray(smoother, np.int64),
+    np.savez(tmp, next_it=np.int64(k), z=np.asarray(z),
+             smoother=np.asarray(smoother, np.float64),
              hist=np.frombuffer(json.dumps(hist).encode(), dtype=np.uint8))
     os.replace(tmp, path)
 
 
 def load_checkpoint(path: str):
-    """(next iteration, z, history, smoother) from save_checkpoint."""
+    """(next iteration, z, history, smoother) from save_checkpoint; the smoother as
+    (fine, coarse[, ratio, bound, W-cycle mask])."""
     with np.load(path) as f:
-        return (int(f["next_it"]), f["z"], json.loads(bytes(f["hist"]).decode()),
-                tuple(int(v) for v in f["smoother"]))
+        sm = [float(v) for v in f["smoother"]]
+        smoother = tuple([int(sm[0]), int(sm[1])] + sm[2:4] + [int(v) for v in sm[4:5]])
+        return (int(f["next_it"]), f["z"], json.loads(bytes(f["hist"]).decode()), smoother)
+
+
+def smoother_state(g) -> tuple:
+    """(fine, coarse, ratio, bound, W-cycle mask): the grid's full smoother setting."""
+    fine, coarse, ratio = g.smoother()
+    return (fine, coarse, ratio, g.smoother_bound()[0], g.cycle())
+
+
+def set_smoother_state(g, sm) -> None:
+    g.set_smoother(sm[0], sm[1], *sm[2:3])
+    if len(sm) > 3:
+        g.set_smoother_bound(sm[3])
+        g.set_cycle(sm[4])
 
 
 def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo.FP32,
@@ -89,7 +106,7 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
     with tomo.Grid.from_problem(problem, precision=precision, rtol=rtol, maxit=maxit) as g:
         g.set_warm_start(warm)
         if resumed_smoother is not None:
-            g.set_smoother(*resumed_smoother)
+            set_smoother_state(g, resumed_smoother)
         gc = None
         if block:
             q = P.coarse_problem(problem, block)
@@ -137,7 +154,7 @@ def run(problem: P.Problem, iters: int, *, block: int = 0, precision: int = tomo
                 if checkpoint and ((checkpoint_every > 0 and (k + 1) % checkpoint_every == 0)
                                    or k + 1 == iters):
                     save_checkpoint(checkpoint, k + 1, z.cpu().numpy(), hist,
-                                    g.smoother()[:2])
+                                    smoother_state(g))
         finally:
             if gc is not None:
                 gc.close()

@@ -49,7 +49,7 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("fine_degree", ctypes.c_int32), ("coarse_degree", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("ms", ctypes.c_double),
                 ("lam", ctypes.c_double), ("w_levels", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("reserved", ctypes.c_uint32), ("ratio", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -106,6 +106,12 @@ def _load():
                                         ctypes.POINTER(ctypes.c_int32)]),
         "tomo_autotune_smoother_d": (st, [G, P, P, ctypes.c_int32, ctypes.c_int32, P,
                                           ctypes.POINTER(ctypes.c_int32)]),
+        "tomo_autotune_smoother_multi": (st, [G, P, ctypes.c_int32, P, ctypes.c_int32,
+                                              ctypes.c_int32, P,
+                                              ctypes.POINTER(ctypes.c_int32)]),
+        "tomo_autotune_smoother_multi_d": (st, [G, P, ctypes.c_int32, P, ctypes.c_int32,
+                                                ctypes.c_int32, P,
+                                                ctypes.POINTER(ctypes.c_int32)]),
         "tomo_server_create": (st, [ctypes.c_int32, ctypes.c_uint64,
                                     ctypes.POINTER(ctypes.c_void_p)]),
         "tomo_server_submit": (st, [P, ctypes.POINTER(GridDesc), ctypes.c_int64, P, P, P,
@@ -215,6 +221,7 @@ def exported_symbols():
             "tomo_set_smoother_bound", "tomo_get_smoother_bound",
             "tomo_server_submit_optimize",
             "tomo_autotune_smoother", "tomo_autotune_smoother_d", "tomo_set_cycle",
+            "tomo_autotune_smoother_multi", "tomo_autotune_smoother_multi_d",
             "tomo_get_cycle",
             "tomo_server_create", "tomo_server_submit",
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
@@ -444,28 +451,35 @@ class Grid:
         return w.value
 
     def autotune(self, z, candidates=None, reps=2):
-        """Time the state solve on design z for each (fine, coarse) degree pair at the
-        current bound and cycle, or for the built-in list of pairs, bounds and cycles when
-        None, and keep the fastest (tomo_autotune_smoother); returns (best (fine, coarse,
-        lam, w_levels), list of dicts with fine, coarse, lam, w, ms, iters, status per
-        candidate)."""
+        """Time the state solve on design z (or on each design of a list: the medians are
+        summed, tomo_autotune_smoother_multi) for each (fine, coarse) degree pair at the
+        current bound, cycle and ratio, or for the built-in stages when None, and keep the
+        fastest (tomo_autotune_smoother); returns (best (fine, coarse, lam, w_levels, ratio),
+        list of dicts with fine, coarse, lam, w, ratio, ms, iters, status per candidate)."""
         if candidates is None:
-            pairs, n = None, 20
+            pairs, n = None, 23
         else:
             flat = [int(v) for pq in candidates for v in pq]
             pairs = (ctypes.c_int32 * len(flat))(*flat)
             n = len(candidates)
         res = (TuneResult * n)()
         best = ctypes.c_int32(-1)
-        st = getattr(lib(), "tomo_autotune_smoother" + self._sfx)(
-            self._h, self._e(z, "z"), ctypes.cast(pairs, ctypes.c_void_p) if pairs else None,
-            n, int(reps), ctypes.cast(res, ctypes.c_void_p), ctypes.byref(best))
+        pp = ctypes.cast(pairs, ctypes.c_void_p) if pairs else None
+        if isinstance(z, (list, tuple)):
+            zs = (ctypes.c_void_p * len(z))(*[self._e(a, "z") for a in z])
+            st = getattr(lib(), "tomo_autotune_smoother_multi" + self._sfx)(
+                self._h, ctypes.cast(zs, ctypes.c_void_p), len(z), pp, n, int(reps),
+                ctypes.cast(res, ctypes.c_void_p), ctypes.byref(best))
+        else:
+            st = getattr(lib(), "tomo_autotune_smoother" + self._sfx)(
+                self._h, self._e(z, "z"), pp, n, int(reps), ctypes.cast(res, ctypes.c_void_p),
+                ctypes.byref(best))
         if st != 0:
             raise TomoError(st, lib().tomo_last_error(self._h).decode())
         rows = [dict(fine=r.fine_degree, coarse=r.coarse_degree, lam=r.lam, w=r.w_levels,
-                     ms=r.ms, iters=r.iters, status=r.status) for r in res]
+                     ratio=r.ratio, ms=r.ms, iters=r.iters, status=r.status) for r in res]
         b = rows[best.value]
-        return (b["fine"], b["coarse"], b["lam"], b["w"]), rows
+        return (b["fine"], b["coarse"], b["lam"], b["w"], b["ratio"]), rows
 
     def filter(self, x, out, transpose=False):
         self._call("tomo_filter", self._e(x, "in"), self._e(out, "out"), int(bool(transpose)))

@@ -19,3 +19,8 @@ def test_checkpoint_round_trip(tmp_path):
     O.save_checkpoint(path, 3, z[::-1].copy(), hist + [{"it": 2}], (2, 2))   # overwrite
     k, z3, h3, sm = O.load_checkpoint(path)
     assert k == 3 and sm == (2, 2) and len(h3) == 3 and np.array_equal(z3, z[::-1])
+    # the full setting: degrees, interval ratio, bound and W-cycle mask
+    O.save_checkpoint(path, 4, z, hist, (1, 3, 30.0, 3.6163636363636376, 2))
+    k, _, _, sm = O.load_checkpoint(path)
+    assert k == 4 and sm == (1, 3, 30.0, 3.6163636363636376, 2)
+    assert isinstance(sm[0], int) and isinstance(sm[4], int)

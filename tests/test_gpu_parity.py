@@ -308,6 +308,12 @@ def test_device_loop_and_host_loop_agree(prec):
     assert i1.iters == i2.iters and i1.iters > 3
     assert c1 == c2 and torch.equal(dc1, dc2)
     assert n > 0 and ms > 0 and b > 0
+    if prec == tomo.FP32:
+        # the fine-level products that did work: four in the first V-cycle (degree 2: one
+        # Chebyshev step after the Jacobi start, the residual, two post-smoothing steps),
+        # then per iteration the CG product, and for every iteration but the last (which
+        # stops at its convergence test) another V-cycle's four: 5 per iteration
+        assert n == 5 * i2.iters
 
 
 def test_gradient_host_buffers_equal_device_buffers():

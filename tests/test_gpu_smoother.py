@@ -75,7 +75,7 @@ def test_autotune_keeps_the_fastest_converging_candidate():
         ok = [r for r in rows if r["status"] == 0]
         assert ok and all(r["ms"] > 0 for r in ok)
         fastest = min(ok, key=lambda r: r["ms"])
-        assert best == (fastest["fine"], fastest["coarse"], fastest["lam"], 0)
+        assert best == (fastest["fine"], fastest["coarse"], fastest["lam"], 0, 20.0)
         assert g.smoother()[:2] == best[:2] and g.smoother_bound()[0] == best[2]
         dc = torch.empty_like(zt)
         c, info = g.gradient(zt, dc)
@@ -88,18 +88,41 @@ def test_autotune_keeps_the_fastest_converging_candidate():
     with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
         best, rows = g.autotune(zt)
         lam_b = g.smoother_bound()[1]
-        assert len(rows) == 20
-        assert best in [(r["fine"], r["coarse"], r["lam"], r["w"]) for r in rows]
+        assert len(rows) == 23
+        assert best in [(r["fine"], r["coarse"], r["lam"], r["w"], r["ratio"]) for r in rows]
         assert sorted({round(r["lam"] / lam_b, 6) for r in rows}) == [0.68, 0.75, 1.0]
-        assert [r["w"] for r in rows] == [0] * 18 + [2, 6]
+        assert [r["w"] for r in rows[:20]] == [0] * 18 + [2, 6]
+        assert [r["ratio"] for r in rows[20:]] == [12.0, 30.0, 50.0]
         v = [r for r in rows[:18] if r["status"] == 0]
         vbest = min(v, key=lambda r: r["ms"])       # the W stage starts from the best V row
         assert all((r["fine"], r["coarse"], r["lam"]) == (vbest["fine"], vbest["coarse"],
-                                                          vbest["lam"]) for r in rows[18:])
+                                                          vbest["lam"]) for r in rows[18:20])
+        wbest = min([r for r in rows[:20] if r["status"] == 0], key=lambda r: r["ms"])
+        assert all((r["fine"], r["coarse"], r["lam"], r["w"]) ==
+                   (wbest["fine"], wbest["coarse"], wbest["lam"], wbest["w"])
+                   for r in rows[20:])                # the ratio stage from the best so far
         assert g.smoother_bound()[0] == best[2] and g.cycle() == best[3]
+        assert g.smoother()[2] == best[4]
         dc = torch.empty_like(zt)
         c2, _ = g.gradient(zt, dc)
     assert abs(c2 / c0 - 1.0) <= 1e-5
+
+
+def test_autotune_over_several_designs_sums_their_times():
+    p = P.mbb_block(48, 24, 19, volfrac=0.12, rmin=2.5)
+    zs = [_field(p, 40 + k)[1] for k in range(3)]
+    cands = [(2, 2), (1, 4)]
+    with tomo.Grid.from_problem(p, precision=tomo.FP32) as g:
+        best, rows = g.autotune(zs, cands, reps=2)
+        assert len(rows) == 2 and all(r["status"] == 0 and r["ms"] > 0 for r in rows)
+        fastest = min(rows, key=lambda r: r["ms"])
+        assert best[:2] == (fastest["fine"], fastest["coarse"])
+        one = [g.autotune(z, cands, reps=2)[1] for z in zs]
+        for k in range(2):    # the sum of three medians: larger than any one of them
+            assert rows[k]["ms"] > max(o[k]["ms"] for o in one) * 1.5
+            assert rows[k]["iters"] == max(o[k]["iters"] for o in one)
+        with pytest.raises(tomo.TomoError):
+            g.autotune([], cands)
 
 
 def test_autotune_without_a_converging_candidate_keeps_the_smoother():
