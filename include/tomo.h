@@ -267,6 +267,18 @@ tomo_status tomo_set_smoother_bound(tomo_grid* grid, double lam);
  * stream and sets the captured loop aside.  tomo_get_cycle reads the mask. */
 tomo_status tomo_set_cycle(tomo_grid* grid, uint32_t w_levels);
 tomo_status tomo_get_cycle(const tomo_grid* grid, uint32_t* w_levels);
+/* Coarse tail (FP32 multigrid grids): with on != 0 the V-cycle runs its levels from the
+ * first one below the finest with at most 4096 elements down to the coarsest and back
+ * (smoothing, residual, transfers, coarsest solve) as ONE launch of a thread-block cluster,
+ * its passes separated by cluster barriers, instead of about six launches per level.  The
+ * operator is the same (the launched levels' definitions); only the order in which a
+ * node's element contributions are added differs, so results agree to rounding.  Levels
+ * with W-cycle bits at or below the entry level keep the launched form.  No effect on grids
+ * without such a level (tomo_get_coarse_tail reports 0) or on lockstep batches.  Like
+ * tomo_set_smoother it waits for the grid's stream and drops the captured loops.
+ * tomo_get_coarse_tail: the entry level in use, 0 when off. */
+tomo_status tomo_set_coarse_tail(tomo_grid* grid, int32_t on);
+tomo_status tomo_get_coarse_tail(const tomo_grid* grid, int32_t* level);
 tomo_status tomo_get_smoother_bound(const tomo_grid* grid, double* lam, double* element_bound,
                                     int64_t* fallbacks);
 
@@ -549,8 +561,8 @@ tomo_status tomo_inject_fault(const char* site, int32_t nth);
  * 8 the restriction's fine nodes and coarse moduli, 9 the prolongation's coarse nodes, 10
  * the modulus coarsening, 11 the D^-1 kernel's moduli, 12 the coarsest solve's columns, 13
  * the CG update's D^-1 gathers, 14 the filters' neighbours, 15 the sensitivity's element
- * nodes, 17 the persistent iteration's unit table.  In the regular build *checked = 0 and
- * *word = 0. */
+ * nodes, 17 the persistent iteration's unit table, 18 the coarse tail's element, node and
+ * transfer indices.  In the regular build *checked = 0 and *word = 0. */
 tomo_status tomo_check_report(int32_t* checked, uint64_t* word);
 
 #ifdef __cplusplus

@@ -16,7 +16,7 @@ OBJ_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "libtomo.so")
 LIB_CHECKED = os.path.join(OUT_DIR, "libtomo_checked.so")
 SOURCES = ["api.cu", "element.cu", "matvec.cu", "matvec2.cu", "vec.cu", "filt.cu",
-           "twoscale.cu", "server.cu", "noalloc.cu"]
+           "twoscale.cu", "server.cu", "noalloc.cu", "vtail.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

@@ -532,6 +532,53 @@ tomo_status smooth(tomo_grid* G, int l, const T* b, T** X, T** Y, bool zero_star
   return TOMO_OK;
 }
 
+// Levels l .. coarsest of the V-cycle on b (level l's right-hand side) in one cluster
+// launch (vtail.cu); first_done: level l's x already holds the zero-start step.
+tomo_status vtail(tomo_grid* G, int l, const float* b, const int* skip, bool first_done) {
+  TRY(join_factor(G));
+  VTailArgs A{};
+  const int nl = (int)G->L.size();
+  A.nlev = nl - l;
+  A.first_done = first_done ? 1 : 0;
+  A.nc = G->coarse_n;
+  A.ld = G->vt_ld;
+  A.Ainv = (const float*)G->coarseA;
+  A.dsc = (const float*)G->coarseD;
+  A.eb = (float*)G->vt_eb;
+  A.skip = skip;
+  const Cheb cb = cheb(G);
+  for (int q = 0; q < A.nlev; ++q) {
+    const tomo_level& Lv = G->L[l + q];
+    VTailLevel& V = A.L[q];
+    V.g = Lv.g;
+    V.s = (const float*)Lv.s;
+    V.mask = Lv.mask;
+    V.invd = (const float*)Lv.invd;
+    V.x = (float*)Lv.x;
+    V.xp = (float*)Lv.xp;
+    V.b = q == 0 ? const_cast<float*>(b) : (float*)Lv.b;
+    V.t = (float*)Lv.t;
+    V.K = level_degree(G, l + q);
+    if (V.K > kVtMaxDeg) return fail(G, TOMO_EINVAL, "coarse tail: degree above %d", kVtMaxDeg);
+    double rho_prev = 1.0 / cb.sigma;
+    for (int s = 0; s < V.K; ++s) {  // the coefficients smooth() uses
+      if (s == 0) {
+        V.c1[s] = 0.0f;
+        V.c2[s] = (float)(1.0 / cb.theta);
+      } else {
+        const double rho = 1.0 / (2.0 * cb.sigma - rho_prev);
+        V.c1[s] = (float)(rho * rho_prev);
+        V.c2[s] = (float)(2.0 * rho / cb.delta);
+        rho_prev = rho;
+      }
+    }
+  }
+  LevelTimer lt(G, l);
+  CK(launch_vtail(G->stream, A, elem_const<float>(G)));
+  G->launches += 1;
+  return TOMO_OK;
+}
+
 // z = V-cycle(b) on level l; *out receives the buffer holding z.
 template <typename T>
 tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int* skip,
@@ -546,6 +593,15 @@ tomo_status vcycle(tomo_grid* G, int l, const T* b, T** out, bool dot, const int
     G->launches += 1;
     *out = (T*)Lv.x;
     return TOMO_OK;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (G->vt_on && l == G->vt_level && l > 0 && (G->wlevels >> l) == 0u) {
+      // levels l .. coarsest in one cluster launch (the same operator as the launched
+      // levels below; ping-pong as smooth(): 2K - 1 swaps leave the result in xp)
+      TRY(vtail(G, l, b, skip, first_done));
+      *out = (T*)((2 * level_degree(G, l) - 1) % 2 ? Lv.xp : Lv.x);
+      return TOMO_OK;
+    }
   }
   T* X = (T*)Lv.x;
   T* Y = (T*)Lv.xp;
@@ -676,7 +732,10 @@ tomo_status enqueue_iteration(tomo_grid* G) {
   }
   T* z = nullptr;
   TRY(precond<T>(G, r, &z, G->fuse_j0));
-  CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
+  if (G->cond_capture)  // the device-side loop: this launch also decides the next iteration
+    CK(launch_cg_p_cond<T>(G->stream, n, p, z, G->sc, G->cond_handle, G->counter + 3));
+  else
+    CK(launch_cg_p<T>(G->stream, n, p, z, G->sc));
   G->launches += 1;
   return TOMO_OK;
 }
@@ -712,13 +771,11 @@ tomo_status build_loop_graph(tomo_grid* G, cudaGraphExec_t* out) {
   tomo_status st = TOMO_OK;
   const int64_t before = G->launches;
   if (e == cudaSuccess) {
+    // the iteration's last kernel (the p update) also runs the loop test
+    G->cond_capture = true;
+    G->cond_handle = h;
     st = enqueue_iteration<T>(G);
-    if (st == TOMO_OK) {
-      cudaError_t e2 = launch_loop_cond(G->stream, h, G->sc);
-      G->launches += 1;
-      if (e2 != cudaSuccess) st = fail(G, TOMO_ECUDA, "loop control launch failed: %s",
-                                       cudaGetErrorString(e2));
-    }
+    G->cond_capture = false;
     cudaGraph_t captured = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(G->stream, &captured);
     if (st == TOMO_OK && e3 != cudaSuccess) e = e3;
@@ -1441,6 +1498,7 @@ void free_grid(tomo_grid* G) {
   F(G->s64);
   F(G->partials);
   F(G->counter);
+  F(G->vt_eb);
   F(G->sc);
   F(G->dscal);
   pinned_put(G->h_sc);
@@ -1571,6 +1629,16 @@ tomo_status create_impl(tomo_grid* G) {
       TRY(dalloc(G, &G->L[l].invd, sizeof(T) * (size_t)G->L[l].g.nn));
     G->invd = G->L[0].invd;
     G->fuse_j0 = true;
+    // the coarse tail in one cluster launch: from the first level (below the finest and
+    // above the coarsest) with few enough elements for the cluster's threads
+    const int nl = (int)G->L.size();
+    for (int l = 1; l + 1 < nl; ++l)
+      if (G->L[l].g.nel <= kVtMaxTailElements && nl - l <= kVtMaxLevels && vtail_ctas() > 0) {
+        G->vt_level = l;
+        G->vt_ld = G->L[l].g.nel;
+        TRY(dalloc(G, &G->vt_eb, sizeof(float) * 24 * (size_t)G->vt_ld));
+        break;
+      }
   }
   if (G->coarse_n > 0) {
     TRY(dalloc(G, &G->coarseA, sizeof(T) * (size_t)G->coarse_n * G->coarse_n));
@@ -2077,6 +2145,30 @@ tomo_status tomo_autotune_smoother_multi_d(tomo_grid* G, const double* const* z,
   return do_autotune<double>(G, z, nz, pairs, n, reps, results, best);
 }
 
+tomo_status tomo_set_coarse_tail(tomo_grid* G, int32_t on) {
+  if (!G) return TOMO_EINVAL;
+  g_cur_err = &G->err;
+  G->err.clear();
+  const bool want = on != 0 && G->vt_level > 0;
+  if (want == G->vt_on) return TOMO_OK;
+  TRY(sync(G));  // no captured loop of this grid is still running
+  // the captured loops hold the other V-cycle form: drop them all
+  if (G->loop_exec) cudaGraphExecDestroy(G->loop_exec);
+  if (G->loop_exec_adj) cudaGraphExecDestroy(G->loop_exec_adj);
+  G->loop_exec = G->loop_exec_adj = nullptr;
+  for (auto& e : G->loop_cache) cudaGraphExecDestroy(e.exec);
+  G->loop_cache.clear();
+  G->vt_on = want;
+  G->gen += 1;
+  return TOMO_OK;
+}
+
+tomo_status tomo_get_coarse_tail(const tomo_grid* G, int32_t* level) {
+  if (!G || !level) return TOMO_EINVAL;
+  *level = G->vt_on ? G->vt_level : 0;
+  return TOMO_OK;
+}
+
 tomo_status tomo_set_cycle(tomo_grid* G, uint32_t w_levels) {
   if (!G) return TOMO_EINVAL;
   g_cur_err = &G->err;
@@ -2103,7 +2195,7 @@ tomo_status tomo_check_report(int32_t* checked, uint64_t* word) {
     return TOMO_ECUDA;
   }
   unsigned long long (*const words[])() = {check_word_matvec2, check_word_matvec,
-                                           check_word_vec, check_word_filt};
+                                           check_word_vec, check_word_filt, check_word_vtail};
   for (auto f : words) {
     const unsigned long long w = f();
     if (w == ~0ull) return TOMO_ECUDA;

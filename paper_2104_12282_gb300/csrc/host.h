@@ -21,7 +21,43 @@ unsigned long long check_word_matvec2();
 unsigned long long check_word_matvec();
 unsigned long long check_word_vec();
 unsigned long long check_word_filt();
+unsigned long long check_word_vtail();
 #endif
+
+// ---------------------------------------------------------------------------------------
+// Coarse tail of the V-cycle in one thread-block cluster (vtail.cu): levels [l0, coarsest]
+// of one FP32 grid, every pass (element forces, node update, transfers, coarsest solve)
+// separated by cluster barriers instead of kernel boundaries.
+// ---------------------------------------------------------------------------------------
+constexpr int kVtMaxLevels = 8;
+constexpr int kVtMaxTailElements = 4096;  // the entry level's elements (about one per thread)
+constexpr int kVtMaxDeg = 8;
+struct VTailLevel {
+  Geom g;
+  const float* s;         // element moduli
+  const uint8_t* mask;    // fixed-DOF bits per node
+  const float* invd;      // D^-1 per node (not for the coarsest)
+  float* x;               // iterate (holds the zero-start step on entry when first_done)
+  float* xp;              // second smoother buffer
+  float* b;               // right-hand side (restricted residual)
+  float* t;               // residual
+  int K;                  // smoothing degree
+  float c1[kVtMaxDeg], c2[kVtMaxDeg];  // Chebyshev coefficients of steps 0..K-1
+};
+struct VTailArgs {
+  int nlev;               // levels of the tail, the last one the dense coarsest
+  int first_done;         // the entry level's x already holds the zero-start step
+  int nc;                 // coarsest DOFs
+  int ld;                 // element-buffer stride (>= the largest level's element count)
+  const float* Ainv;      // coarsest: D^-1/2 K^-1 D^-1/2 scaled inverse, row-major
+  const float* dsc;       // coarsest: D^-1/2
+  float* eb;              // element forces, 24 x ld floats
+  const int* skip;        // CG stop flag
+  VTailLevel L[kVtMaxLevels];
+};
+// CTAs of the cluster that runs the tail, 0 if this device cannot launch it
+int vtail_ctas();
+cudaError_t launch_vtail(cudaStream_t st, const VTailArgs& A, const ElemConst<float>& C);
 
 // Host-side fault injection sites (tomo_inject_fault / TOMO_FAULT); fault_hit(k) is true on
 // the armed pass of site k (once per arming).
@@ -342,7 +378,11 @@ cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* 
                          const T* invd = nullptr, T c2 = T(0));
 template <typename T>
 cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc);
-cudaError_t launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, CgScalars* sc);
+// p = z + beta p with the device-side loop's test in its last block (counter: a zeroed word
+// it resets)
+template <typename T>
+cudaError_t launch_cg_p_cond(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc,
+                             cudaGraphConditionalHandle h, unsigned* counter);
 int march_blocks_per_sm(int tsize, int mode, bool pair, bool dot);
 
 // Dots and vector helpers.
@@ -494,6 +534,10 @@ struct tomo_grid {
   // Jacobi step x1 = c2 D^-1 r (D^-1 per node in invd, from the first V-cycle of the solve),
   // so the V-cycles inside the loop skip that launch
   bool fuse_j0 = false;
+  // while capturing the device-side loop: the loop's condition handle, set by the last
+  // kernel of the iteration (the p update)
+  bool cond_capture = false;
+  cudaGraphConditionalHandle cond_handle = 0;
   void* invd = nullptr;
   int64_t gen = 0;  // bumped when settings baked into captured loops change (smoother)
   // captured loops (load slot) of smoother settings used before: (fine, coarse, ratio)
@@ -505,6 +549,12 @@ struct tomo_grid {
   };
   // bit l: the V-cycle makes two coarse-grid corrections at level l (a W-cycle there)
   uint32_t wlevels = 0;
+  // coarse tail in one cluster launch (vtail.cu): entry level (-1: none fits), whether the
+  // V-cycle uses it, and its element-force buffer
+  int vt_level = -1;
+  bool vt_on = false;
+  void* vt_eb = nullptr;
+  int vt_ld = 0;
   double lam_bound = 0.0;       // the element bound of lambda_max(D^-1 K), always safe
   int64_t bound_fallbacks = 0;  // solves redone at lam_bound after failing at a lower lam_hi
   std::vector<CachedLoop> loop_cache;

@@ -1,6 +1,6 @@
 // The body of the generic product kernel (k_march, FP64 grids and the FP64 residual of the
 // float-pair iterate): one CTA of 32 lanes x TY thread rows, thread (l, r).  Shared by the
-// launched kernels (matvec.cu) and the persistent lockstep iteration (persist.cu).
+// launched kernels (matvec.cu) and the persistent lockstep iteration (vec.cu).
 #pragma once
 
 #include "common.cuh"

@@ -642,20 +642,6 @@ cudaError_t launch_cg_xr(cudaStream_t st, int n, T* xhi, T* xlo, T* r, const T* 
   return cudaGetLastError();
 }
 
-// Device-side loop control of the conditional-while graph: continue while CG has not
-// stopped; the launch counter bounds the loop even if a reduction never reported.
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc) {
-  PDL_ENTER();
-  sc->loops += 1;
-  const bool go = !sc->done && sc->loops < sc->maxit + 8;
-  if (!go) sc->done = 1;
-  cudaGraphSetConditional(h, go ? 1u : 0u);
-}
-
-cudaError_t launch_loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, CgScalars* sc) {
-  pdl_launch(k_loop_cond, 1, 1, 0, st, h, sc);
-  return cudaGetLastError();
-}
 
 // p = z + beta p
 template <typename T>
@@ -702,6 +688,36 @@ cudaError_t launch_cg_p(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc)
   int blocks = (n + 255) / 256;
   if (blocks > 8 * 152) blocks = 8 * 152;
   pdl_launch(k_cg_p<T>, blocks, 256, 0, st, n, p, z, sc);
+  return cudaGetLastError();
+}
+
+// The p update as the last kernel of the device-side loop's iteration, with the loop's
+// control in its last block (no launch of its own): continue while CG has not stopped; the
+// iteration counter bounds the loop even if a reduction never reported.  counter: a zeroed
+// word, reset by the last block.
+template <typename T>
+__global__ void k_cg_p_cond(int n, T* __restrict__ p, const T* __restrict__ z, CgScalars* sc,
+                            cudaGraphConditionalHandle h, unsigned* counter) {
+  cg_p_body<T>(blockIdx.x, gridDim.x, n, p, z, sc);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(counter, 1u) == gridDim.x - 1) {
+      *counter = 0u;
+      sc->loops += 1;
+      const bool go = !sc->done && sc->loops < sc->maxit + 8;
+      if (!go) sc->done = 1;
+      cudaGraphSetConditional(h, go ? 1u : 0u);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_cg_p_cond(cudaStream_t st, int n, T* p, const T* z, CgScalars* sc,
+                             cudaGraphConditionalHandle h, unsigned* counter) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 8 * 152) blocks = 8 * 152;
+  pdl_launch(k_cg_p_cond<T>, blocks, 256, 0, st, n, p, z, sc, h, counter);
   return cudaGetLastError();
 }
 
@@ -1104,6 +1120,8 @@ cudaError_t launch_convert(cudaStream_t st, int n, const TI* in, const TI* inlo,
   template cudaError_t launch_cg_xr<T>(cudaStream_t, int, T*, T*, T*, const T*, const T*,     \
                                        double*, unsigned*, CgScalars*, T*, const T*, T);     \
   template cudaError_t launch_cg_p<T>(cudaStream_t, int, T*, const T*, CgScalars*);           \
+  template cudaError_t launch_cg_p_cond<T>(cudaStream_t, int, T*, const T*, CgScalars*,       \
+                                           cudaGraphConditionalHandle, unsigned*);            \
   template cudaError_t launch_mask_copy<T>(cudaStream_t, Geom, const T*, const uint8_t*, T*);
 INST(float)
 INST(double)

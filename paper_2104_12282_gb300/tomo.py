@@ -98,6 +98,8 @@ def _load():
                                    ctypes.POINTER(ctypes.c_double)]),
         "tomo_set_smoother_bound": (st, [G, ctypes.c_double]),
         "tomo_set_cycle": (st, [G, ctypes.c_uint32]),
+        "tomo_set_coarse_tail": (st, [G, ctypes.c_int32]),
+        "tomo_get_coarse_tail": (st, [G, ctypes.POINTER(ctypes.c_int32)]),
         "tomo_get_cycle": (st, [G, ctypes.POINTER(ctypes.c_uint32)]),
         "tomo_get_smoother_bound": (st, [G, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double),
@@ -222,6 +224,7 @@ def exported_symbols():
             "tomo_server_submit_optimize",
             "tomo_autotune_smoother", "tomo_autotune_smoother_d", "tomo_set_cycle",
             "tomo_autotune_smoother_multi", "tomo_autotune_smoother_multi_d",
+            "tomo_set_coarse_tail", "tomo_get_coarse_tail",
             "tomo_get_cycle",
             "tomo_server_create", "tomo_server_submit",
             "tomo_server_wait", "tomo_server_get_stats", "tomo_server_destroy",
@@ -443,6 +446,18 @@ class Grid:
         st = lib().tomo_set_cycle(self._h, int(w_levels))
         if st != 0:
             raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def set_coarse_tail(self, on=True):
+        """Coarse levels of the V-cycle in one cluster launch (tomo_set_coarse_tail)."""
+        st = lib().tomo_set_coarse_tail(self._h, int(bool(on)))
+        if st != 0:
+            raise TomoError(st, lib().tomo_last_error(self._h).decode())
+
+    def coarse_tail(self):
+        """Entry level of the coarse tail in use (0: off) (tomo_get_coarse_tail)."""
+        l = ctypes.c_int32()
+        lib().tomo_get_coarse_tail(self._h, ctypes.byref(l))
+        return l.value
 
     def cycle(self):
         """The W-cycle level mask (tomo_get_cycle)."""

@@ -1,8 +1,8 @@
 """Workload run against one build of the library (the regular or, with TOMO_LIB=checked,
 the bounds-checked one) by tests/test_gpu_checked.py: products, gradients and OC steps on
 small and odd grids in both precisions, a wide filter, the general adjoint, the two-scale
-coarse-graining, lockstep batches (8- and 4-row tiles, the persistent iteration), a W-cycle
-and a served request.  Prints one JSON object: the results and the check report."""
+coarse-graining, lockstep batches (8- and 4-row tiles, the persistent iteration), a W-cycle,
+the coarse tail in one cluster launch and a served request.  Prints one JSON object: the results and the check report."""
 import json
 import os
 import sys
@@ -56,8 +56,11 @@ def run():
         g.coarse_grain(z, 4, zc)
         g.set_cycle(2)
         c2, _ = g.gradient(z, dc)
+        g.set_cycle(0)
+        g.set_coarse_tail(True)
+        c3, _ = g.gradient(z, dc)
         torch.cuda.synchronize()
-        out["wide_adjoint_twoscale_w"] = [c, J, float(dj.sum()), float(zc.sum()), c2]
+        out["wide_adjoint_twoscale_w_tail"] = [c, J, float(dj.sum()), float(zc.sum()), c2, c3]
     # lockstep batches
     ps = P.uneven_cantilever_batch(5, 6)
     zs = [t(P.random_field(q.dims, 10 + i, 0.05, 1.0)) for i, q in enumerate(ps)]
