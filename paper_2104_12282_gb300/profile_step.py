@@ -3,7 +3,7 @@ with every kernel issued from the host, for profilers: ncu does not profile kern
 of graphs with conditional nodes, so the CG loop normally hidden in such a graph is issued
 as separate launches here (bitwise the same results).  Single host thread, one grid.
 
-    python -m paper_2104_12282_gb300.profile_step --steps 2
+    python -m paper_2104_12282_gb300.profile_step --steps 2 [--degrees 2,2 --bound-scale 0.68]
 """
 from __future__ import annotations
 
@@ -19,6 +19,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--degrees", default="2,2", help="fine,coarse Chebyshev degrees")
+    ap.add_argument("--bound-scale", type=float, default=1.0,
+                    help="smoothing-interval bound as a fraction of the element bound")
+    ap.add_argument("--ratio", type=float, default=20.0, help="smoothing-interval ratio")
     a = ap.parse_args(argv)
     import torch
 
@@ -29,6 +33,9 @@ def main(argv=None):
     z = torch.tensor(P.bumpy_field(p.dims, a.seed), dtype=dt, device=dev)
     dc, dv, zn = torch.empty_like(z), torch.empty_like(z), torch.empty_like(z)
     with tomo.Grid.from_problem(p, precision=prec, maxit=5000) as g:
+        fine, coarse = (int(v) for v in a.degrees.split(","))
+        g.set_smoother(fine, coarse, a.ratio)
+        g.set_smoother_bound(a.bound_scale * g.smoother_bound()[1])
         g.profile_enable(True)   # host-issued CG iterations, events around the products
         for _ in range(a.steps):
             c, info = g.gradient(z, dc, dv)
