@@ -68,8 +68,19 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
   const int nb0 = c0 ? i + g.nxn * j0 : 0, nb1 = c1 ? i + g.nxn * j1 : 0;
   const int eb0 = e0 ? i + g.nx * j0 : 0, eb1 = e1 ? i + g.nx * j1 : 0;
 
-  __shared__ float sN[3][TY][32];  // node row j0 of each thread row, plane k+1
-  __shared__ float sV[6][TY][32];  // sy = 1 half of the upper element, for the next row
+  // sN: node row j0 of each thread row, plane k+1, and a zero row TY (the row above the
+  // last thread row); sV: the sy = 1 half of each thread row's upper element in rows 1..TY,
+  // for the thread row above, and a zero row 0 (below the first): no selects on the reads
+  __shared__ float sN[3][TY + 1][32];
+  __shared__ float sV[6][TY + 1][32];
+  if (t == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sN[c][TY][l] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sV[q][0][l] = 0.0f;
+  }
+  // lane 0 has no left neighbour: its shuffled-in value is weighted 0 (an FMA, not a select)
+  const float2 wleft = bc2(l > 0 ? 1.0f : 0.0f), nwleft = bc2(l > 0 ? -1.0f : 0.0f);
 
   auto load_plane = [&](int k, float2 (&v)[3]) {
     const bool in = k >= 0 && k < g.nzn;
@@ -104,7 +115,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
   __syncthreads();
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    N0[c] = (t + 1 < TY) ? sN[c][t + 1][l] : 0.0f;
+    N0[c] = sN[c][t + 1][l];
     C0[c] = shdn2(A0[c]);
     DN0[c] = __shfl_down_sync(FULL, N0[c], 1);
   }
@@ -165,7 +176,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
     float2 C1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      N1[c] = (t + 1 < TY) ? sN[c][t + 1][l] : 0.0f;
+      N1[c] = sN[c][t + 1][l];
       C1[c] = shdn2(A1[c]);
       DN1[c] = __shfl_down_sync(FULL, N1[c], 1);
     }
@@ -249,7 +260,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
       {
         const float2 w1 = W[c][1];  // q = 0: W[0] = 0, so U0 = w1, U1 = -w1
         const float2 fromleft = shup2(w1);
-        G[0] = (l > 0) ? sub2(w1, fromleft) : w1;
+        G[0] = fma2(fromleft, nwleft, w1);
       }
 #pragma unroll
       for (int q = 1; q < 4; ++q) {
@@ -257,7 +268,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
         const float2 u0 = add2(W[c][m0i], W[c][m0i + 1]);
         const float2 u1 = sub2(W[c][m0i], W[c][m0i + 1]);
         const float2 fromleft = shup2(u1);
-        G[q] = (l > 0) ? add2(u0, fromleft) : u0;
+        G[q] = fma2(fromleft, wleft, u0);
       }
 #pragma unroll
       for (int mz = 0; mz < 2; ++mz) {
@@ -265,7 +276,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
         const float2 v1 = sub2(G[2 * mz], G[2 * mz + 1]);  // sy = 1
         T[c][mz] = v0;
         V1keep[c][mz] = v1;
-        sV[2 * c + mz][t][l] = v1.y;  // upper element's sy = 1 half -> node row j0 + 2
+        sV[2 * c + mz][t + 1][l] = v1.y;  // upper element's sy = 1 half -> node row j0 + 2
       }
     }
     __syncthreads();
@@ -273,7 +284,7 @@ __device__ __forceinline__ void march2_body(const March2Args& A, const March2Con
     for (int c = 0; c < 3; ++c) {
 #pragma unroll
       for (int mz = 0; mz < 2; ++mz) {
-        const float prev = (t > 0) ? sV[2 * c + mz][t - 1][l] : 0.0f;
+        const float prev = sV[2 * c + mz][t][l];
         // node row j0 gets the element row below (previous thread row); row j1 gets the
         // lower element of this pair
         T[c][mz] = add2(T[c][mz], make_float2(prev, V1keep[c][mz].x));
