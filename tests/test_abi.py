@@ -97,3 +97,62 @@ def test_device_footprint_estimate_without_gpu(libpath):
     d.nx = 0
     out = ctypes.c_size_t()
     assert L.tomo_estimate_device_bytes(ctypes.byref(d), ctypes.byref(out)) == 1
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("nx", 0, b"dimensions"),
+    ("nz", -3, b"dimensions"),
+    ("nx", 1290, b"32-bit"),          # 3 (nx+1)^3 >= 2^31 - 1 with ny = nz = 1290
+    ("nu", 0.5, b"material"),
+    ("nu", -1.0, b"material"),
+    ("h", 0.0, b"material"),
+    ("Emin", -1e-9, b"material"),
+    ("E0", 0.0, b"material"),         # E0 <= Emin
+    ("penal", 0.5, b"material"),
+    ("rmin", 0.0, b"material"),
+    ("rmin", 16.5, b"material"),
+    ("precision", 7, b"precision"),
+    ("precond", 9, b"preconditioner"),
+])
+def test_create_rejects_each_bad_field_without_gpu(libpath, field, value, msg):
+    """Every descriptor check runs before any device call and names the problem."""
+    from paper_2104_12282_gb300 import tomo
+    L = tomo.lib()
+    d = tomo.GridDesc()
+    L.tomo_default_desc(ctypes.byref(d))
+    d.nx, d.ny, d.nz = 4, 2, 2
+    if field == "nx" and value == 1290:
+        d.ny = d.nz = 1290
+    fixed = (ctypes.c_uint8 * 3)()
+    f = (ctypes.c_double * 3)()
+    d.fixed_dof = ctypes.cast(fixed, ctypes.POINTER(ctypes.c_uint8))
+    d.f = ctypes.cast(f, ctypes.POINTER(ctypes.c_double))
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert L.tomo_create_grid(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert not h.value
+    assert msg in L.tomo_last_error(None)
+
+
+def test_create_needs_descriptor_and_arrays_without_gpu(libpath):
+    from paper_2104_12282_gb300 import tomo
+    L = tomo.lib()
+    h = ctypes.c_void_p()
+    assert L.tomo_create_grid(None, ctypes.byref(h)) == 1
+    d = tomo.GridDesc()
+    L.tomo_default_desc(ctypes.byref(d))
+    d.nx, d.ny, d.nz = 4, 2, 2
+    assert L.tomo_create_grid(ctypes.byref(d), ctypes.byref(h)) == 1   # no fixed_dof / f
+    assert b"required" in L.tomo_last_error(None)
+
+
+@pytest.mark.parametrize("n_el", [0, -5, (1 << 22) + 1])
+def test_no_alloc_oc_step_rejects_sizes_outside_its_scratch_without_gpu(libpath, n_el):
+    """The allocation-free OC step checks the size against its static scratch first."""
+    from paper_2104_12282_gb300 import tomo
+    L = tomo.lib()
+    one = (ctypes.c_float * 1)()
+    st = L.tomo_oc_step_noalloc(ctypes.c_int64(n_el), ctypes.c_double(1.0), one, one, one,
+                                ctypes.c_double(0.5), ctypes.c_double(0.2), one, None, None)
+    assert st == 1
+    assert b"4194304" in L.tomo_last_error(None)
