@@ -1157,7 +1157,7 @@ tomo_status compliance_and_sens(tomo_grid* G, const T* drho, const T* du, const 
     // f^T u: the load is sparse (point, line, face loads), so only its nonzero entries
     if (G->load_nnz <= (1 << 18)) {
       CK(launch_sparse_dot<T>(G->stream, G->load_nnz, G->load_idx, G->load_val, du, dulo,
-                              G->dscal));
+                              G->partials, G->counter, G->dscal));
     } else {
       CK(launch_dot<double, T>(G->stream, 3 * G->g.nn, G->f64, du, dulo, G->partials,
                                G->counter, G->dscal));

@@ -158,10 +158,12 @@ cudaError_t launch_fill(cudaStream_t st, int64_t n, T* p, T v);
 template <typename T>
 cudaError_t launch_scatter_load(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
                                 T* fT, double* f64);
-// f^T (u + ulo) over the nonzero load entries (FP64, one block); r = scatter of the entries
+// f^T (u + ulo) over the nonzero load entries (FP64; fixed-order reduction through
+// partials/counter); r = scatter of the entries
 template <typename T>
 cudaError_t launch_sparse_dot(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
-                              const T* u, const T* ulo, double* out);
+                              const T* u, const T* ulo, double* partials, unsigned* counter,
+                              double* out);
 template <typename T>
 cudaError_t launch_scatter_vec(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
                                T* r);

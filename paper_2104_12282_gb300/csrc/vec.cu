@@ -765,23 +765,24 @@ cudaError_t launch_scatter_load(cudaStream_t st, int nnz, const int64_t* idx, co
 // out = sum_k val[k] (u + ulo)[idx[k]] in FP64 (one block, fixed order): f^T u for a sparse
 // load f given by its nonzero entries.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_sparse_dot(int nnz, const int64_t* __restrict__ idx,
-                                                     const double* __restrict__ val,
-                                                     const T* __restrict__ u,
-                                                     const T* __restrict__ ulo, double* out) {
+__global__ void __launch_bounds__(256) k_sparse_dot(int nnz, const int64_t* __restrict__ idx,
+                                                    const double* __restrict__ val,
+                                                    const T* __restrict__ u,
+                                                    const T* __restrict__ ulo,
+                                                    double* partials, unsigned* counter,
+                                                    double* out) {
   PDL_ENTER();
-  __shared__ double red[32];
   double acc = 0.0;
-  // a thread's entries k = tid, tid + blockDim, ... in that order; kSpIlp of them have their
-  // index, value and u loads in flight together (one dependent round trip per group instead
-  // of one per entry: the load has ~2e4 entries on the benchmark grid, a single block)
-  constexpr int kSpIlp = 8;
-  for (int k0 = threadIdx.x; k0 < nnz; k0 += kSpIlp * blockDim.x) {
+  // a thread's entries k = t, t + nt, ... in that order, kSpIlp of them with their index,
+  // value and u loads in flight together (one dependent round trip per group)
+  constexpr int kSpIlp = 4;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int k0 = t; k0 < nnz; k0 += kSpIlp * nt) {
     int64_t ii[kSpIlp];
     double vv[kSpIlp], uu[kSpIlp];
 #pragma unroll
     for (int q = 0; q < kSpIlp; ++q) {
-      const int k = k0 + q * (int)blockDim.x;
+      const int k = k0 + q * nt;
       ii[q] = k < nnz ? idx[k] : -1;
       vv[q] = k < nnz ? val[k] : 0.0;
     }
@@ -797,20 +798,21 @@ __global__ void __launch_bounds__(1024) k_sparse_dot(int nnz, const int64_t* __r
     for (int q = 0; q < kSpIlp; ++q)
       if (ii[q] >= 0) acc += vv[q] * uu[q];
   }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    *out = t;
-  }
+  double v[1] = {acc};
+  grid_reduce_at<1>(v, partials, counter, [out](const double* tot) { *out = tot[0]; },
+                    blockIdx.x, gridDim.x);
 }
 
+// f^T u over the load's nonzero entries: blocks by the entry count alone (about 1024
+// entries each, at most 152), so the fixed-order block sum is the same on every call
 template <typename T>
 cudaError_t launch_sparse_dot(cudaStream_t st, int nnz, const int64_t* idx, const double* val,
-                              const T* u, const T* ulo, double* out) {
-  pdl_launch(k_sparse_dot<T>, 1, 1024, 0, st, nnz, idx, val, u, ulo, out);
+                              const T* u, const T* ulo, double* partials, unsigned* counter,
+                              double* out) {
+  int blocks = (nnz + 1023) / 1024;
+  blocks = blocks < 1 ? 1 : (blocks > 152 ? 152 : blocks);
+  pdl_launch(k_sparse_dot<T>, blocks, 256, 0, st, nnz, idx, val, u, ulo, partials, counter,
+             out);
   return cudaGetLastError();
 }
 
@@ -835,9 +837,11 @@ cudaError_t launch_scatter_vec(cudaStream_t st, int nnz, const int64_t* idx, con
 }
 
 template cudaError_t launch_sparse_dot<float>(cudaStream_t, int, const int64_t*, const double*,
-                                              const float*, const float*, double*);
+                                              const float*, const float*, double*, unsigned*,
+                                              double*);
 template cudaError_t launch_sparse_dot<double>(cudaStream_t, int, const int64_t*, const double*,
-                                               const double*, const double*, double*);
+                                               const double*, const double*, double*,
+                                               unsigned*, double*);
 template cudaError_t launch_scatter_vec<float>(cudaStream_t, int, const int64_t*, const double*,
                                                float*);
 template cudaError_t launch_scatter_vec<double>(cudaStream_t, int, const int64_t*,
